@@ -1,0 +1,383 @@
+"""Benchmark of the GEF rasterizer hot path on GB300.
+
+A step is one full pass of the hot path over one view: preprocess (projection, SH colour,
+extent), binning (depth sort, scan, keygen, tile sort, ranges), forward composite, backward
+composite and preprocess backward -- with a fixed synthetic upstream gradient.  The default
+workload is the scene-scale case: 1.5M clustered GEF primitives (SH degree 3, beta
+log-uniform [0.5, 8]) rendered at 1245x825 from 20 orbit cameras, cycled step by step.
+
+Printed (rank 0, one JSON line): Mpix/s of the fwd+bwd step (``value``), the forward-only
+rate, per-stage times, the dominant kernel's roofline, the end-to-end rate through the C-ABI
+with host buffers, the FP64 oracle timed on the host cores (``cpu_baseline``) and the SM clocks
+seen during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: independent replicas (each rank renders its own views; no collective), weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Mpix/s fwd & fwd+bwd at 1.5M GEF prims 1245×825; serving p50/p99 ms/frame"
+N_PRIMS = 1_500_000
+WIDTH, HEIGHT = 1245, 825
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.proc = None
+        self.lines = []
+        self.dev = device_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args, ws, rank):
+    """The oracle (FP64 CPU brute force, as it stands) on a bounded sample of the same workload."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2402_10128_gb300 import scenes
+    sc, cams = scenes.scene_scale_workload(N_PRIMS)
+    rng = np.random.default_rng(0)
+    cores = os.cpu_count() or 1
+    per_step = args.ref_pixels
+    times = []
+    for i in range(args.warmup + args.steps):
+        cam = cams[i % len(cams)]
+        pix = rng.choice(WIDTH * HEIGHT, per_step, replace=False)
+        g = rng.standard_normal((3, per_step))
+        t0 = time.perf_counter()
+        oracle.backward(sc, cam, g, pixels=pix, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = per_step * len(times) / tot / 1e6
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": "scene-scale: 1.5M clustered GEF primitives, SH3, 1245x825, "
+                                                       "20 orbit cameras; fwd+bwd", "sample_pixels_per_step": per_step},
+           "cpu_baseline": {"kind": "oracle", "value": value, "unit": "Mpix/s", "cores": cores,
+                            "sample": f"{per_step} uniformly random pixels per step of one 1245x825 view "
+                                      f"(fwd+bwd, FP64 brute force over all 1.5M primitives)"},
+           "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def cpu_baseline(sc, cams, pixels, cores):
+    import oracle
+    rng = np.random.default_rng(1)
+    cam = cams[0]
+    pix = rng.choice(cam.width * cam.height, pixels, replace=False)
+    g = rng.standard_normal((3, pixels))
+    t0 = time.perf_counter()
+    oracle.backward(sc, cam, g, pixels=pix, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": pixels / dt / 1e6, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+            "seconds": dt,
+            "sample": f"{pixels} uniformly random pixels of one 1245x825 view of the 1.5M-primitive scene, "
+                      f"fwd+bwd (FP64 brute force over all primitives); Mpix/s extrapolated from the sampled pixels"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-pixels", type=int, default=96)
+    ap.add_argument("--cpu-pixels", type=int, default=768)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n", type=int, default=N_PRIMS)
+    args = ap.parse_args()
+    assert args.warmup >= 3 or args.impl == "reference" or os.environ.get("GES_BENCH_ALLOW_SHORT")
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    from paper_2402_10128_gb300 import ges, render, scenes
+
+    sc, cams = scenes.scene_scale_workload(args.n)
+    # each rank renders its own views (replicas): rotate the camera sequence by rank
+    cams = cams[rank % len(cams):] + cams[:rank % len(cams)]
+    dev = torch.device("cuda", local)
+    t = render.scene_tensors(sc, dev)
+    stream = torch.cuda.current_stream()
+    ctx = render.default_context(local)
+
+    # key capacity: the largest K over the camera set, plus headroom (no host sync per frame)
+    probe = render.Frame(sc.n, WIDTH, HEIGHT, key_capacity=0, ctx=ctx)
+    Ks, Fs = [], []
+    for cam in cams:
+        probe.forward(t, sc.sh_degree, cam)
+        ev, inr, K = ges.ges_frame_count_work(probe.handle)
+        Ks.append(K)
+        Fs.append((ev, inr))
+    probe.close()
+    del probe
+    cap = int(max(Ks) * 1.05) + 4096
+    frame = render.Frame(sc.n, WIDTH, HEIGHT, key_capacity=cap, ctx=ctx)
+    gcam = [ges.make_camera(c) for c in cams]
+    params = ges.params_default()
+    img = torch.empty((3, HEIGHT, WIDTH), device=dev)
+    T = torch.empty((HEIGHT, WIDTH), device=dev)
+    nc = torch.empty((HEIGHT, WIDTH), dtype=torch.int32, device=dev)
+    gen = torch.Generator(device=dev).manual_seed(7)
+    dL = (torch.rand((3, HEIGHT, WIDTH), device=dev, generator=gen) - 0.5) * (2.0 / (WIDTH * HEIGHT))
+    grads = tuple(torch.empty_like(a) for a in t)
+    scene_c = ges.make_scene(*t, sc.sh_degree)
+    grads_c = ges.make_grads(*grads)
+    sp = stream.cuda_stream
+    nst = 5
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(nst)] for _ in range(args.steps)]
+
+    def step(i, events=None, bwd=True):
+        cam = gcam[i % len(gcam)]
+        if events:
+            events[0].record(stream)
+        ges.ges_preprocess(frame.handle, scene_c, cam, params, sp)
+        if events:
+            events[1].record(stream)
+        ges.ges_bin_sort(frame.handle, sp)
+        if events:
+            events[2].record(stream)
+        ges.ges_render_fwd(frame.handle, img, T, nc, sp)
+        if events:
+            events[3].record(stream)
+        if bwd:
+            ges.ges_render_bwd(frame.handle, scene_c, T, nc, dL, grads_c, sp)
+        if events:
+            events[4].record(stream)
+
+    def timed(fn_steps, bwd):
+        for i in range(args.warmup):
+            step(i, bwd=bwd)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        l0 = ges.ges_kernel_launches()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for i in range(args.steps):
+            step(i, ev[i] if bwd else None, bwd=bwd)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        launches = ges.ges_kernel_launches() - l0
+        ms = s0.elapsed_time(s1)
+        if dist:
+            x = torch.tensor([ms], device=dev)
+            dist.all_reduce(x, op=dist.ReduceOp.MAX)
+            ms = float(x.item())
+        return ms, launches
+
+    with ClockSampler(local) as clk:
+        ms_fb, launches = timed(args.steps, bwd=True)
+        stage = np.array([[ev[i][k].elapsed_time(ev[i][k + 1]) for k in range(nst - 1)] for i in range(args.steps)])
+        ms_f, _ = timed(args.steps, bwd=False)
+    clocks = clk.summary()
+    err = ges.ges_frame_status(frame.handle)[0]
+    assert err == ges.GES_OK, "key capacity overflowed during the timed region"
+
+    pix = WIDTH * HEIGHT
+    value = ws * pix * args.steps / (ms_fb / 1e3) / 1e6
+    fwd_rate = ws * pix * args.steps / (ms_f / 1e3) / 1e6
+    st_mean = stage.mean(0)
+
+    # roofline of the dominant kernel
+    peaks, src = _peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    stage_names = ["preprocess", "bin_sort", "render_fwd", "render_bwd+preprocess_bwd"]
+    dom = int(np.argmax(st_mean))
+    mean_eval = float(np.mean([f[0] for f in Fs]))
+    mean_inr = float(np.mean([f[1] for f in Fs]))
+    mean_K = float(np.mean(Ks))
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    # forward composite: 3 MUFU ops (lg2, ex2, ex2) per in-extent (fragment, pixel) pair; 16 MUFU lanes/SM/clk
+    mufu_peak = nsm * 16 * sm_mhz * 1e6 / 1e12  # Tops/s
+    fwd_ms = float(st_mean[2])
+    achieved_mufu = 3.0 * mean_inr / (fwd_ms / 1e3) / 1e12
+    roofline = {"kernel": "k_render_fwd (forward composite)", "bound": "alu", "achieved": achieved_mufu,
+                "peak": mufu_peak, "unit": "Tops/s (MUFU)", "frac": achieved_mufu / mufu_peak, "traffic": None,
+                "work": f"3 MUFU x {mean_inr:.3e} in-extent (fragment,pixel) pairs per frame",
+                "peak_source": f"{nsm} SMs x 16 MUFU/clk x {sm_mhz:.0f} MHz ({src} max clock)"}
+    # preprocess: HBM bytes per primitive (read 240 B at SH3, write 68 B)
+    pre_bytes = sc.n * (240 + 68)
+    pre_gbs = pre_bytes / (float(st_mean[0]) / 1e3) / 1e9
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+
+    out = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_fb / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "scene-scale: 1.5M clustered GEF primitives (64 clusters + 10% shell), SH3, "
+                                  "beta log-U[0.5,8], 1245x825, 20 orbit cameras; step = fwd+bwd of one view",
+                      "n_prims": sc.n, "width": WIDTH, "height": HEIGHT, "cameras": len(cams),
+                      "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                      "l2": "inputs larger than L2 (scene 360 MB, key lists ~%d MB)" % int(mean_K * 16 / 1e6)},
+           "fwd_mpix_s": fwd_rate, "fwd_ms_per_frame": ms_f / args.steps,
+           "stage_ms": dict(zip(stage_names, [float(x) for x in st_mean])),
+           "dominant_stage": stage_names[dom],
+           "frame_stats": {"K_mean": mean_K, "evaluated_pairs_mean": mean_eval, "in_extent_pairs_mean": mean_inr},
+           "roofline": roofline,
+           "preprocess_hbm": {"achieved_gbs": pre_gbs, "peak_gbs": hbm, "frac": pre_gbs / hbm,
+                              "bytes_per_prim": 308, "note": "includes the depth-key copy launch"},
+           "gpu_launches": int(launches), "clocks": clocks}
+
+    if not args.no_e2e:
+        out["e2e"] = e2e(args, sc, gcam, frame, params, dev, stream, ws, dist)
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(sc, cams, args.cpu_pixels, os.cpu_count() or 1)
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def e2e(args, sc, gcam, frame, params, dev, stream, ws, dist):
+    """Same fwd+bwd step through the C-ABI with the scene, upstream gradient, image and
+    gradients in pinned host memory: every step copies inputs in and results out."""
+    import torch
+    from paper_2402_10128_gb300 import ges
+    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in sc.arrays()]
+    dev_in = [torch.empty(h.shape, dtype=h.dtype, device=dev) for h in host]
+    gen = torch.Generator().manual_seed(3)
+    dL_h = ((torch.rand((3, HEIGHT, WIDTH), generator=gen) - 0.5) * (2.0 / (WIDTH * HEIGHT))).pin_memory()
+    dL_d = torch.empty_like(dL_h, device=dev)
+    img_h = torch.empty((3, HEIGHT, WIDTH)).pin_memory()
+    grads_h = [torch.empty(h.shape).pin_memory() for h in host]
+    img = torch.empty((3, HEIGHT, WIDTH), device=dev)
+    T = torch.empty((HEIGHT, WIDTH), device=dev)
+    nc = torch.empty((HEIGHT, WIDTH), dtype=torch.int32, device=dev)
+    grads = [torch.empty_like(a) for a in dev_in]
+    scene_c = ges.make_scene(*dev_in, sc.sh_degree)
+    grads_c = ges.make_grads(*grads)
+    sp = stream.cuda_stream
+    h2d = sum(h.numel() * 4 for h in host) + dL_h.numel() * 4
+    d2h = img_h.numel() * 4 + sum(h.numel() * 4 for h in grads_h)
+
+    def step(i):
+        for d, h in zip(dev_in, host):
+            d.copy_(h, non_blocking=True)
+        dL_d.copy_(dL_h, non_blocking=True)
+        cam = gcam[i % len(gcam)]
+        ges.ges_preprocess(frame.handle, scene_c, cam, params, sp)
+        ges.ges_bin_sort(frame.handle, sp)
+        ges.ges_render_fwd(frame.handle, img, T, nc, sp)
+        ges.ges_render_bwd(frame.handle, scene_c, T, nc, dL_d, grads_c, sp)
+        img_h.copy_(img, non_blocking=True)
+        for h, d in zip(grads_h, grads):
+            h.copy_(d, non_blocking=True)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for i in range(args.steps):
+        step(i)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    ms = s0.elapsed_time(s1)
+    if dist:
+        x = torch.tensor([ms], device=dev)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        ms = float(x.item())
+    return {"value": ws * WIDTH * HEIGHT * args.steps / (ms / 1e3) / 1e6, "unit": "Mpix/s",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": ms / args.steps}
+
+
+if __name__ == "__main__":
+    main()

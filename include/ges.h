@@ -1,0 +1,217 @@
+/*
+ * ges.h -- C ABI of libges, a GB300 (sm_103a) rasterizer for Generalized
+ * Exponential Splatting (Hamdi et al., "GES: Generalized Exponential Splatting
+ * for Efficient Radiance Field Rendering").
+ *
+ * The library renders a set of 3D primitives, each with mean mu, scale s,
+ * rotation quaternion q, shape parameter beta, opacity kappa and spherical
+ * harmonic (SH) colour coefficients (Sec. 3.1), to an image: projection of the
+ * beta-modified covariance to a 2D conic (Sec. 3.1, EWA; Sec. 3.2, Eq. approx),
+ * tile|depth keys and a radix sort, front-to-back compositing with the GEF
+ * falloff exp(-1/2 q^(beta/2)) (Sec. 3.1, Eq. ges; Sec. 3.2, Eq. transmittance),
+ * and the gradients of all primitive parameters (backward pass).
+ *
+ * Conventions shared by every entry point
+ *  - All functions are extern "C", never throw, and return ges_status.
+ *    On failure ges_last_error() returns a message for the calling thread.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is stream-ordered: a call returns once its kernels are enqueued,
+ *    unless its comment says it synchronises.
+ *  - Array arguments are caller-owned DEVICE pointers to contiguous fp32 (or
+ *    the stated type), row-major, unless stated otherwise.  Workspaces
+ *    (ges_ctx, ges_frame, ges_server) are library-owned.
+ *  - Parameters are physical values: scale > 0, opacity in (0,1), beta > 0.
+ *    (The paper trains beta shifted by -2 and scale/opacity through log/logit
+ *    activations, App. B.2; that reparameterisation is the caller's.)
+ *    Primitives with a non-finite or non-positive beta, a zero quaternion,
+ *    opacity <= alpha_min, depth <= znear, or a footprint off the image are
+ *    culled (contribute nothing, receive zero gradient).
+ *  - Quaternions are (w,x,y,z) and are normalised inside; their gradient is
+ *    with respect to the unnormalised input.
+ *  - Camera: OpenCV axes (+x right, +y down, +z forward); viewmat maps world
+ *    to camera; pixel (i,j) is sampled at (i+0.5, j+0.5).
+ *  - Images are planar [3, H, W]; per-pixel arrays are [H, W].
+ */
+#ifndef GES_H
+#define GES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ges_status {
+  GES_OK = 0,
+  GES_ERR_INVALID_ARG = 1,  /* a pointer, size or value is out of range; nothing was enqueued */
+  GES_ERR_OOM = 2,          /* a device allocation failed or the HBM budget would be exceeded */
+  GES_ERR_CUDA = 3,         /* a CUDA runtime call failed (message names it) */
+  GES_ERR_CAPACITY = 4,     /* the duplicate-key count exceeded the frame's key capacity */
+  GES_ERR_NOT_READY = 5,    /* serving: the request has not finished */
+  GES_ERR_TIMEOUT = 6,      /* serving: the wait ran out */
+  GES_ERR_BUSY = 7,         /* serving: the request queue is full */
+  GES_ERR_DEVICE_WAIT = 8   /* a bounded device-side wait gave up (status word set by a kernel) */
+} ges_status;
+
+typedef enum ges_falloff {
+  /* exp(-1/2 q^(beta/2)) on the phi_bar-scaled covariance (Eq. ges with Eq. approx); default */
+  GES_FALLOFF_GEF = 0,
+  /* exp(-1/2 q) on the phi_bar-scaled covariance: the paper's Gaussian-form
+     rasterizer that only rescales the splat (Sec. 3.2, "Approximate Rasterization") */
+  GES_FALLOFF_PAPER_APPROX = 1
+} ges_falloff;
+
+typedef struct ges_camera {
+  int32_t width, height;  /* pixels, 1..16384 each */
+  float fx, fy, cx, cy;   /* pinhole intrinsics in pixels */
+  float viewmat[16];      /* world -> camera, row-major 4x4 (last row 0,0,0,1) */
+  float campos[3];        /* camera centre in world space (SH view direction) */
+  float znear;            /* primitives with camera depth <= znear are culled */
+  float bg[3];            /* background colour composited with the final transmittance */
+} ges_camera;
+
+typedef struct ges_params {
+  float rho;              /* shape strength of phi_bar (App. B.2: 0.1) */
+  int32_t falloff;        /* ges_falloff */
+  float dilation;         /* added to the 2D covariance diagonal, px^2 (0.3) */
+  float alpha_max;        /* alpha clamp (0.99) */
+  float alpha_min;        /* fragments with alpha below this are skipped (1/255) */
+  float t_min;            /* stop before transmittance would drop below this (1e-4) */
+  float extent_margin_rel;/* relative safety margin on the tile extent (1e-3) */
+  float extent_margin_abs;/* absolute safety margin on the tile extent, px (1e-2) */
+  float clamp_fov;        /* tangent clamp of the EWA Jacobian, in half-image units (1.3) */
+} ges_params;
+
+typedef struct ges_scene {
+  int64_t n;              /* number of primitives, 0..2^31-1 */
+  int32_t sh_degree;      /* 0..3 */
+  const float* means;     /* [n,3] */
+  const float* scales;    /* [n,3], > 0 */
+  const float* quats;     /* [n,4] (w,x,y,z) */
+  const float* betas;     /* [n], > 0 */
+  const float* opacities; /* [n], in (0,1) */
+  const float* shs;       /* [n,(sh_degree+1)^2,3], l-major, m = -l..l, real SH with Condon-Shortley phase */
+} ges_scene;
+
+typedef struct ges_grads { /* same shapes as ges_scene; written (not accumulated) by ges_render_bwd */
+  float* means;
+  float* scales;
+  float* quats;
+  float* betas;
+  float* opacities;
+  float* shs;
+} ges_grads;
+
+typedef struct ges_ctx ges_ctx;
+typedef struct ges_frame ges_frame;
+typedef struct ges_server ges_server;
+
+/* Message for the last failed call on this thread ("" if none).  Owned by the library. */
+const char* ges_last_error(void);
+
+/* Defaults listed beside each ges_params field. */
+ges_status ges_params_default(ges_params* out);
+
+/* Library context on CUDA device `device`.  hbm_budget_bytes bounds the memory this
+   context may allocate (0 = no bound).  Destroy with ges_ctx_destroy. */
+ges_status ges_ctx_create(int device, size_t hbm_budget_bytes, ges_ctx** out);
+void ges_ctx_destroy(ges_ctx* ctx);
+
+/* Per-frame workspace for up to n_capacity primitives at width x height.
+   key_capacity: maximum number of (tile, primitive) duplicates K.  0 selects
+   automatic growth: ges_bin_sort then synchronises the stream once per call to read
+   K and reallocates when needed.  With key_capacity > 0 ges_bin_sort never
+   synchronises (the sequence is graph-capturable); when K exceeds it the frame is
+   marked overflowed, no keys are written, and ges_frame_status reports
+   GES_ERR_CAPACITY.  Destroy with ges_frame_destroy (synchronises the device). */
+ges_status ges_frame_create(ges_ctx* ctx, int64_t n_capacity, int32_t width, int32_t height,
+                            int64_t key_capacity, ges_frame** out);
+void ges_frame_destroy(ges_frame* frame);
+
+/* Preprocess (per primitive): scale modification phi_bar (Eq. approx), covariance from
+   scale and quaternion (Sec. 3.1), EWA projection to a 2D conic (Sec. 3.1), opacity-aware
+   beta-dependent tile extent, depth key, SH colour.  scene->n <= n_capacity; the camera's
+   size must equal the frame's.  The scene arrays must stay valid until ges_render_bwd
+   (if used) has been enqueued. */
+ges_status ges_preprocess(ges_frame* frame, const ges_scene* scene, const ges_camera* cam,
+                          const ges_params* params, void* stream);
+
+/* Binning: depth sort of the primitives (radix, 32-bit float keys), exclusive scan of
+   the tiles each touches, duplicate generation in depth order, stable radix sort by
+   tile id, and per-tile [start,end) ranges.  The result equals a stable sort of the
+   64-bit keys (tile << 32 | depth bits) with values = primitive index. */
+ges_status ges_bin_sort(ges_frame* frame, void* stream);
+
+/* Forward composite (Sec. 3.2): per pixel, front to back over its tile's list,
+   q = d^T conic d, G = exp(-1/2 q^(beta/2)) (or exp(-1/2 q)), alpha = min(alpha_max, kappa G),
+   skip alpha < alpha_min, stop before T drops below t_min.  Outputs (device, caller-owned):
+   img [3,H,W] = colour + T * bg, final_T [H,W], n_contrib [H,W] (1-based position, in the
+   tile's list, of the last fragment composited; 0 if none). */
+ges_status ges_render_fwd(ges_frame* frame, float* img, float* final_T, uint32_t* n_contrib, void* stream);
+
+/* Backward: gradients of L with respect to every scene parameter, given dL/dimg [3,H,W].
+   Recomputes back to front from final_T and n_contrib as returned by ges_render_fwd for
+   the same frame (no per-fragment state is stored), then chains through the projection.
+   `scene` must be the one passed to ges_preprocess.  All of out's arrays are overwritten. */
+ges_status ges_render_bwd(ges_frame* frame, const ges_scene* scene, const float* final_T,
+                          const uint32_t* n_contrib, const float* dL_dimg, const ges_grads* out,
+                          void* stream);
+
+/* Synchronises `stream` and reports GES_ERR_CAPACITY if the last ges_bin_sort overflowed,
+   else GES_OK.  *num_keys (optional) receives K. */
+ges_status ges_frame_status(ges_frame* frame, void* stream, int64_t* num_keys);
+
+/* Inspection (tests, tools).  Synchronises `stream`.  Copies to HOST buffers:
+   the sorted 64-bit keys (tile << 32 | depth bits) and values (primitive index) of the
+   last ges_bin_sort, max_keys entries at most; *num_keys receives K. */
+ges_status ges_frame_keys(ges_frame* frame, void* stream, uint64_t* keys, uint32_t* vals,
+                          int64_t max_keys, int64_t* num_keys);
+
+/* Inspection.  Synchronises `stream`.  Copies per-primitive results of the last
+   ges_preprocess to HOST buffers (any may be NULL): depth_key [n] (float bits of the camera
+   depth, 0xFFFFFFFF if culled), rect [n,4] int32 (x0,y0,x1,y1 tiles, end-exclusive),
+   record [n,12] fp32 (mean x, mean y, q limit, beta exponent, conic a, b, c, opacity,
+   r, g, b, 0), tile ranges [tiles,2] uint32.  Also the intermediate 2D gradients of the
+   last ges_render_bwd, grad2d [n,12] (mx, my, conic a, b, c, opacity, beta exponent, r, g, b). */
+ges_status ges_frame_inspect(ges_frame* frame, void* stream, uint32_t* depth_key, int32_t* rect,
+                             float* record, uint32_t* ranges, float* grad2d);
+
+/* Inspection.  Re-runs the forward composite of the last ges_bin_sort into internal scratch
+   buffers while counting work, then synchronises `stream`: *evaluated receives the number of
+   (fragment, pixel) pairs composited or tested before each pixel stopped, *in_extent those whose
+   q was within the primitive's extent (the pairs that evaluate the falloff), *num_keys K. */
+ges_status ges_frame_count_work(ges_frame* frame, void* stream, int64_t* evaluated, int64_t* in_extent,
+                                int64_t* num_keys);
+
+/* Number of CUDA kernels this process has launched through libges (all threads). */
+uint64_t ges_kernel_launches(void);
+
+/* ---------------------------------------------------------------------------------------
+ * Serving: several scenes resident on the device, render requests of mixed resolutions
+ * admitted by memory and batched into shared launches (continuous batching).
+ * --------------------------------------------------------------------------------------- */
+
+/* max_slots: requests that may be in flight on the device at once (1..64).
+   The server runs a scheduler thread; destroy with ges_serve_destroy. */
+ges_status ges_serve_create(ges_ctx* ctx, const ges_params* params, int32_t max_slots, ges_server** out);
+
+/* Copies a scene (HOST arrays) into library-owned device memory. */
+ges_status ges_serve_add_scene(ges_server* srv, const ges_scene* host_scene, int32_t* scene_id);
+
+/* Enqueues one render; never blocks.  out_img is a HOST buffer [3,H,W] that stays valid
+   until ges_serve_poll reports GES_OK for the ticket.  GES_ERR_BUSY if the queue is full. */
+ges_status ges_serve_submit(ges_server* srv, int32_t scene_id, const ges_camera* cam, float* out_img,
+                            uint64_t* ticket);
+
+/* Waits up to timeout_us (0 = just check) for a ticket.  GES_OK once out_img is written
+   (latency_ms, optional, receives submit-to-completion time), GES_ERR_NOT_READY when
+   timeout_us == 0 and not done, GES_ERR_TIMEOUT when the wait ran out. */
+ges_status ges_serve_poll(ges_server* srv, uint64_t ticket, int64_t timeout_us, float* latency_ms);
+
+ges_status ges_serve_destroy(ges_server* srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GES_H */

@@ -1,0 +1,76 @@
+// Host-side structures behind the opaque handles of ges.h (shared by api.cu and serve.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "../../include/ges.h"
+#include "common.cuh"
+#include "kernels.cuh"
+
+struct ges_ctx {
+  int device = 0;
+  size_t budget = 0;   // bytes this context may allocate (0 = unbounded)
+  size_t used = 0;
+  int num_sms = 0;
+  std::mutex mu;
+};
+
+struct ges_frame {
+  ges_ctx* ctx = nullptr;
+  int64_t n_cap = 0;
+  int32_t W = 0, H = 0, tiles_x = 0, tiles_y = 0;
+  int64_t n_tiles = 0;
+  int64_t key_cap = 0;
+  bool auto_cap = false;
+  // per primitive
+  uint32_t* depth_key = nullptr;  // float bits of the camera depth, kCulledKey if culled
+  uint32_t* dk[2] = {nullptr, nullptr};
+  uint32_t* pv[2] = {nullptr, nullptr};
+  ushort4* rect = nullptr;
+  ges::Rec* rec = nullptr;
+  uint32_t* touched = nullptr;
+  unsigned long long* offsets = nullptr;
+  float4* g2d = nullptr;
+  // per duplicate
+  uint32_t* tk[2] = {nullptr, nullptr};
+  uint32_t* tv[2] = {nullptr, nullptr};
+  uint32_t* hist = nullptr;
+  int64_t hist_cap = 0;
+  unsigned long long* keys64 = nullptr;
+  int64_t keys64_cap = 0;
+  ges::ScanScratch scan;
+  // per tile
+  uint2* ranges = nullptr;
+  // counters
+  unsigned long long* d_K = nullptr;
+  uint32_t* d_flags = nullptr;
+  unsigned long long* h_K = nullptr;  // pinned
+  // state of the current frame
+  ges::ViewTable<1> vt;
+  ges::Params P;
+  int64_t n = 0;
+  int32_t sh_degree = 0;
+  uint32_t* sorted_prims = nullptr;
+  uint32_t* tile_keys = nullptr;
+  uint32_t* tile_vals = nullptr;
+  bool have_pre = false, have_sort = false;
+  // scratch for ges_frame_count_work
+  float* work_img = nullptr;
+  unsigned long long* work_stats = nullptr;
+};
+
+namespace ges {
+ges_status fail(ges_status st, const char* fmt, ...);
+ges_status cuda_fail(cudaError_t e, const char* what);
+ges_status ctx_alloc(ges_ctx* ctx, void** p, size_t bytes);
+void ctx_free(ges_ctx* ctx, void* p, size_t bytes);
+ges_status use_device(int device);
+Params to_params(const ges_params& p);
+ges_status check_params(const ges_params* p);
+ges_status check_camera(const ges_camera* c);
+ges_status check_scene(const ges_scene* s);
+void fill_view(ViewDesc& v, const ges_camera& c, const ges_scene& s, int64_t prim_base, int32_t tile_base);
+int bits_for(int64_t count);
+}  // namespace ges

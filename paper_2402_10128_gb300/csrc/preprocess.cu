@@ -1,0 +1,458 @@
+// Per-primitive kernels: projection (forward) and its chain rule (backward).
+//
+// Forward, per primitive (Sec. 3.1, Sec. 3.2):
+//   phi_bar_rho(beta) = 2 / (1 + exp(-rho (beta - 2)))            Eq. approx (App. B.2: rho = 0.1)
+//   Sigma = R diag(phi_bar s)^2 R^T                                  Sec. 3.1 (scale vector modified by phi)
+//   Sigma' = J W Sigma W^T J^T + dilation I, conic = Sigma'^-1       Sec. 3.1 (EWA, Zwicker et al.)
+//   extent: alpha = kappa exp(-1/2 q^(beta/2)) >= alpha_min  <=>  q <= q* = (2 ln(kappa/alpha_min))^(2/beta)
+//   colour = max(0, sum_lm c_lm Y_lm(dir) + 1/2)                     Sec. 3.1 (SH as in Gaussian splatting)
+// Everything that decides an integer (visibility, depth key, tile rectangle) runs on the
+// fixed-order FP32 key path of common.cuh; the SH colour uses ordinary FP32 arithmetic.
+#include "common.cuh"
+#include "kernels.cuh"
+#include "keypath.cuh"
+
+namespace ges {
+
+namespace {
+
+// Real SH basis up to degree 3 at unit direction (x,y,z); returns (deg+1)^2 values.
+__device__ __forceinline__ void sh_eval(int deg, float x, float y, float z, float* Y) {
+  Y[0] = (float)sh_norm(0, 0);
+  if (deg < 1) return;
+  const float n11 = (float)sh_norm(1, 1), n10 = (float)sh_norm(1, 0);
+  Y[1] = -n11 * y;
+  Y[2] = n10 * z;
+  Y[3] = -n11 * x;
+  if (deg < 2) return;
+  const float n22 = (float)sh_norm(2, 2), n21 = (float)sh_norm(2, 1), n20 = (float)sh_norm(2, 0);
+  const float xx = x * x, yy = y * y, zz = z * z;
+  Y[4] = 6.0f * n22 * x * y;
+  Y[5] = -3.0f * n21 * y * z;
+  Y[6] = 0.5f * n20 * (3.0f * zz - 1.0f);
+  Y[7] = -3.0f * n21 * x * z;
+  Y[8] = 3.0f * n22 * (xx - yy);
+  if (deg < 3) return;
+  const float n33 = (float)sh_norm(3, 3), n32 = (float)sh_norm(3, 2), n31 = (float)sh_norm(3, 1),
+              n30 = (float)sh_norm(3, 0);
+  Y[9] = -15.0f * n33 * y * (3.0f * xx - yy);
+  Y[10] = 30.0f * n32 * x * y * z;
+  Y[11] = -1.5f * n31 * y * (5.0f * zz - 1.0f);
+  Y[12] = 0.5f * n30 * z * (5.0f * zz - 3.0f);
+  Y[13] = -1.5f * n31 * x * (5.0f * zz - 1.0f);
+  Y[14] = 15.0f * n32 * z * (xx - yy);
+  Y[15] = -15.0f * n33 * x * (xx - 3.0f * yy);
+}
+
+// Gradient of each basis polynomial with respect to (x,y,z) (the radial part is removed later).
+__device__ __forceinline__ void sh_grad(int deg, float x, float y, float z, float3* dY) {
+  dY[0] = make_float3(0.f, 0.f, 0.f);
+  if (deg < 1) return;
+  const float n11 = (float)sh_norm(1, 1), n10 = (float)sh_norm(1, 0);
+  dY[1] = make_float3(0.f, -n11, 0.f);
+  dY[2] = make_float3(0.f, 0.f, n10);
+  dY[3] = make_float3(-n11, 0.f, 0.f);
+  if (deg < 2) return;
+  const float n22 = (float)sh_norm(2, 2), n21 = (float)sh_norm(2, 1), n20 = (float)sh_norm(2, 0);
+  dY[4] = make_float3(6.0f * n22 * y, 6.0f * n22 * x, 0.f);
+  dY[5] = make_float3(0.f, -3.0f * n21 * z, -3.0f * n21 * y);
+  dY[6] = make_float3(0.f, 0.f, 3.0f * n20 * z);
+  dY[7] = make_float3(-3.0f * n21 * z, 0.f, -3.0f * n21 * x);
+  dY[8] = make_float3(6.0f * n22 * x, -6.0f * n22 * y, 0.f);
+  if (deg < 3) return;
+  const float n33 = (float)sh_norm(3, 3), n32 = (float)sh_norm(3, 2), n31 = (float)sh_norm(3, 1),
+              n30 = (float)sh_norm(3, 0);
+  const float xx = x * x, yy = y * y, zz = z * z;
+  dY[9] = make_float3(-90.0f * n33 * x * y, -45.0f * n33 * (xx - yy), 0.f);
+  dY[10] = make_float3(30.0f * n32 * y * z, 30.0f * n32 * x * z, 30.0f * n32 * x * y);
+  dY[11] = make_float3(0.f, -1.5f * n31 * (5.0f * zz - 1.0f), -15.0f * n31 * y * z);
+  dY[12] = make_float3(0.f, 0.f, 0.5f * n30 * (15.0f * zz - 3.0f));
+  dY[13] = make_float3(-1.5f * n31 * (5.0f * zz - 1.0f), 0.f, -15.0f * n31 * x * z);
+  dY[14] = make_float3(30.0f * n32 * x * z, -30.0f * n32 * y * z, 15.0f * n32 * (xx - yy));
+  dY[15] = make_float3(-45.0f * n33 * (xx - yy), 90.0f * n33 * x * y, 0.f);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// K1: preprocess.  One thread per global primitive id (grid-stride).
+// ---------------------------------------------------------------------------------------------
+template <int MAXV>
+__global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ ViewTable<MAXV> vt, int64_t total,
+                                                    const Params P, uint32_t* __restrict__ depth_key,
+                                                    uint32_t* __restrict__ sort_vals, ushort4* __restrict__ rect,
+                                                    Rec* __restrict__ rec) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+    const ViewDesc& vd = vt.v[view_of_prim(vt, g)];
+    const int64_t i = g - vd.prim_base;
+    const float mx = vd.means[3 * i + 0], my = vd.means[3 * i + 1], mz = vd.means[3 * i + 2];
+    const float s0 = vd.scales[3 * i + 0], s1 = vd.scales[3 * i + 1], s2 = vd.scales[3 * i + 2];
+    const float4 q4 = *reinterpret_cast<const float4*>(vd.quats + 4 * i);
+    const float beta = vd.betas[i], kappa = vd.opac[i];
+    const float* V = vd.V;
+
+    // camera-space mean (key path)
+    float tx = kadd(kadd(kadd(kmul(V[0], mx), kmul(V[1], my)), kmul(V[2], mz)), V[3]);
+    float ty = kadd(kadd(kadd(kmul(V[4], mx), kmul(V[5], my)), kmul(V[6], mz)), V[7]);
+    float tz = kadd(kadd(kadd(kmul(V[8], mx), kmul(V[9], my)), kmul(V[10], mz)), V[11]);
+    bool valid = tz > vd.znear;
+    float iz = kdiv(1.0f, tz);
+    float u = kadd(kmul(vd.fx, kmul(tx, iz)), vd.cx);
+    float v = kadd(kmul(vd.fy, kmul(ty, iz)), vd.cy);
+
+    // rotation
+    float n2 = kadd(kadd(kadd(kmul(q4.x, q4.x), kmul(q4.y, q4.y)), kmul(q4.z, q4.z)), kmul(q4.w, q4.w));
+    valid = valid && (n2 > 0.0f);
+    float rn = kdiv(1.0f, ksqrt(n2));
+    float w = kmul(q4.x, rn), x = kmul(q4.y, rn), y = kmul(q4.z, rn), z = kmul(q4.w, rn);
+    float xx = kmul(x, x), yy = kmul(y, y), zz = kmul(z, z), xy = kmul(x, y), xz = kmul(x, z), yz = kmul(y, z);
+    float wx = kmul(w, x), wy = kmul(w, y), wz = kmul(w, z);
+    float R[9];
+    R[0] = ksub(1.0f, kmul(2.0f, kadd(yy, zz)));
+    R[1] = kmul(2.0f, ksub(xy, wz));
+    R[2] = kmul(2.0f, kadd(xz, wy));
+    R[3] = kmul(2.0f, kadd(xy, wz));
+    R[4] = ksub(1.0f, kmul(2.0f, kadd(xx, zz)));
+    R[5] = kmul(2.0f, ksub(yz, wx));
+    R[6] = kmul(2.0f, ksub(xz, wy));
+    R[7] = kmul(2.0f, kadd(yz, wx));
+    R[8] = ksub(1.0f, kmul(2.0f, kadd(xx, yy)));
+
+    // shape modification phi_bar on the scale vector
+    valid = valid && (beta > 0.0f);
+    const float log2e = (float)1.4426950408889634;
+    float rdb = kmul(P.rho, ksub(beta, 2.0f));
+    float ex = key_exp2(kmul(-rdb, log2e));
+    float phi = kdiv(2.0f, kadd(1.0f, ex));
+    float sp[3] = {kmul(phi, s0), kmul(phi, s1), kmul(phi, s2)};
+    float M[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) M[3 * a + b] = kmul(R[3 * a + b], sp[b]);
+    float Sg[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = a; b < 3; ++b) {
+        float t = kadd(kadd(kmul(M[3 * a], M[3 * b]), kmul(M[3 * a + 1], M[3 * b + 1])), kmul(M[3 * a + 2], M[3 * b + 2]));
+        Sg[3 * a + b] = t;
+        Sg[3 * b + a] = t;
+      }
+
+    // EWA Jacobian with the tangent clamp
+    float limx = kdiv(kmul(P.clamp_fov, kmul(0.5f, (float)vd.W)), vd.fx);
+    float limy = kdiv(kmul(P.clamp_fov, kmul(0.5f, (float)vd.H)), vd.fy);
+    float rx = fminf(fmaxf(kmul(tx, iz), -limx), limx);
+    float ry = fminf(fmaxf(kmul(ty, iz), -limy), limy);
+    float txc = kmul(rx, tz), tyc = kmul(ry, tz);
+    float iz2 = kmul(iz, iz);
+    float J00 = kmul(vd.fx, iz), J02 = -kmul(kmul(vd.fx, txc), iz2);
+    float J11 = kmul(vd.fy, iz), J12 = -kmul(kmul(vd.fy, tyc), iz2);
+    float T[6];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      T[b] = kadd(kmul(J00, V[b]), kmul(J02, V[8 + b]));
+      T[3 + b] = kadd(kmul(J11, V[4 + b]), kmul(J12, V[8 + b]));
+    }
+    float U[6];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        U[3 * a + b] = kadd(kadd(kmul(T[3 * a], Sg[b]), kmul(T[3 * a + 1], Sg[3 + b])), kmul(T[3 * a + 2], Sg[6 + b]));
+    float S00 = kadd(kadd(kmul(U[0], T[0]), kmul(U[1], T[1])), kmul(U[2], T[2]));
+    float S01 = kadd(kadd(kmul(U[0], T[3]), kmul(U[1], T[4])), kmul(U[2], T[5]));
+    float S11 = kadd(kadd(kmul(U[3], T[3]), kmul(U[4], T[4])), kmul(U[5], T[5]));
+    float ca = kadd(S00, P.dilation), cb = S01, cc = kadd(S11, P.dilation);
+    float det = ksub(kmul(ca, cc), kmul(cb, cb));
+    valid = valid && (det > 0.0f);
+
+    // opacity-aware, beta-dependent extent
+    float ratio = kdiv(kappa, P.alpha_min);
+    valid = valid && (ratio > 1.0f);
+    const float ln2 = (float)0.6931471805599453;
+    float L = kmul(key_log2(ratio), ln2);
+    float a2 = kmul(2.0f, L);
+    float qs;
+    if (P.mode == 0) {
+      float e2 = kmul(kdiv(2.0f, beta), key_log2(a2));
+      qs = key_exp2(e2);
+    } else {
+      qs = a2;
+    }
+    float onep = kadd(1.0f, P.margin_rel);
+    float hx = kadd(kmul(ksqrt(kmul(qs, ca)), onep), P.margin_abs);
+    float hy = kadd(kmul(ksqrt(kmul(qs, cc)), onep), P.margin_abs);
+    hx = fminf(hx, 1.0e7f);
+    hy = fminf(hy, 1.0e7f);
+    float fx0 = floorf(kdiv(ksub(u, hx), 16.0f));
+    float fx1 = kadd(floorf(kdiv(kadd(u, hx), 16.0f)), 1.0f);
+    float fy0 = floorf(kdiv(ksub(v, hy), 16.0f));
+    float fy1 = kadd(floorf(kdiv(kadd(v, hy), 16.0f)), 1.0f);
+    fx0 = fminf(fmaxf(fx0, 0.0f), (float)vd.tiles_x);
+    fx1 = fminf(fmaxf(fx1, 0.0f), (float)vd.tiles_x);
+    fy0 = fminf(fmaxf(fy0, 0.0f), (float)vd.tiles_y);
+    fy1 = fminf(fmaxf(fy1, 0.0f), (float)vd.tiles_y);
+    int x0 = (int)fx0, x1 = (int)fx1, y0 = (int)fy0, y1 = (int)fy1;
+    bool touched = valid && x1 > x0 && y1 > y0;
+
+    depth_key[g] = touched ? __float_as_uint(tz) : kCulledKey;
+    sort_vals[g] = (uint32_t)g;
+    rect[g] = touched ? make_ushort4((unsigned short)x0, (unsigned short)y0, (unsigned short)x1, (unsigned short)y1)
+                      : make_ushort4(0, 0, 0, 0);
+    if (!touched) continue;
+
+    // SH colour (ordinary FP32)
+    float dvx = mx - vd.campos[0], dvy = my - vd.campos[1], dvz = mz - vd.campos[2];
+    float dn = rsqrtf(dvx * dvx + dvy * dvy + dvz * dvz);
+    float Y[16];
+    sh_eval(vd.sh_degree, dvx * dn, dvy * dn, dvz * dn, Y);
+    const int nb = (vd.sh_degree + 1) * (vd.sh_degree + 1);
+    const float* sh = vd.shs + (int64_t)3 * nb * i;
+    float col[3] = {0.5f, 0.5f, 0.5f};
+    for (int k = 0; k < nb; ++k) {
+      col[0] += Y[k] * sh[3 * k + 0];
+      col[1] += Y[k] * sh[3 * k + 1];
+      col[2] += Y[k] * sh[3 * k + 2];
+    }
+    float idet = 1.0f / det;
+    Rec r;
+    r.a = make_float4(u, v, kmul(kmul(qs, onep), onep), P.mode == 0 ? 0.5f * beta : 1.0f);
+    r.b = make_float4(cc * idet, -cb * idet, ca * idet, kappa);
+    r.c = make_float4(fmaxf(col[0], 0.f), fmaxf(col[1], 0.f), fmaxf(col[2], 0.f), 0.f);
+    rec[g] = r;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// K8: preprocess backward.  g2d[3g..3g+2] holds the compositing stage's gradients of
+// (mx, my, conic a, conic b) (conic c, kappa, hb, r) (g, b, -, -).  Writes every output.
+// ---------------------------------------------------------------------------------------------
+template <int MAXV>
+__global__ void __launch_bounds__(256) k_preprocess_bwd(const __grid_constant__ ViewTable<MAXV> vt, int64_t total,
+                                                        const Params P, const uint32_t* __restrict__ depth_key,
+                                                        const float4* __restrict__ g2d) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+    const ViewDesc& vd = vt.v[view_of_prim(vt, g)];
+    const int64_t i = g - vd.prim_base;
+    const int nb = (vd.sh_degree + 1) * (vd.sh_degree + 1);
+    float* gsh = vd.g_shs + (int64_t)3 * nb * i;
+    if (depth_key[g] == kCulledKey) {
+      for (int k = 0; k < 3; ++k) { vd.g_means[3 * i + k] = 0.f; vd.g_scales[3 * i + k] = 0.f; }
+      *reinterpret_cast<float4*>(vd.g_quats + 4 * i) = make_float4(0.f, 0.f, 0.f, 0.f);
+      vd.g_betas[i] = 0.f;
+      vd.g_opac[i] = 0.f;
+      for (int k = 0; k < 3 * nb; ++k) gsh[k] = 0.f;
+      continue;
+    }
+    const float4 ga = g2d[3 * g + 0], gb = g2d[3 * g + 1], gc = g2d[3 * g + 2];
+    const float g_mx = ga.x, g_my = ga.y, g_A = ga.z, g_B = ga.w, g_C = gb.x, g_kappa = gb.y, g_hb = gb.z;
+    const float g_rgb[3] = {gb.w, gc.x, gc.y};
+
+    const float mu[3] = {vd.means[3 * i], vd.means[3 * i + 1], vd.means[3 * i + 2]};
+    const float s[3] = {vd.scales[3 * i], vd.scales[3 * i + 1], vd.scales[3 * i + 2]};
+    const float4 q4 = *reinterpret_cast<const float4*>(vd.quats + 4 * i);
+    const float beta = vd.betas[i];
+    const float* V = vd.V;
+
+    // ---- recompute the forward quantities (ordinary FP32)
+    float t[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) t[a] = V[4 * a] * mu[0] + V[4 * a + 1] * mu[1] + V[4 * a + 2] * mu[2] + V[4 * a + 3];
+    const float iz = 1.0f / t[2], iz2 = iz * iz;
+    const float qn2 = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
+    const float rn = rsqrtf(qn2);
+    const float w = q4.x * rn, x = q4.y * rn, y = q4.z * rn, z = q4.w * rn;
+    float R[9];
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z); R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z); R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y); R[7] = 2.f * (y * z + w * x); R[8] = 1.f - 2.f * (x * x + y * y);
+    const float phi = 2.0f / (1.0f + expf(-P.rho * (beta - 2.0f)));
+    const float sp[3] = {phi * s[0], phi * s[1], phi * s[2]};
+    float M[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) M[3 * a + b] = R[3 * a + b] * sp[b];
+    float Sg[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) Sg[3 * a + b] = M[3 * a] * M[3 * b] + M[3 * a + 1] * M[3 * b + 1] + M[3 * a + 2] * M[3 * b + 2];
+    const float limx = P.clamp_fov * 0.5f * (float)vd.W / vd.fx;
+    const float limy = P.clamp_fov * 0.5f * (float)vd.H / vd.fy;
+    const float rxr = t[0] * iz, ryr = t[1] * iz;
+    const bool clx = rxr < -limx || rxr > limx, cly = ryr < -limy || ryr > limy;
+    const float rxc = fminf(fmaxf(rxr, -limx), limx), ryc = fminf(fmaxf(ryr, -limy), limy);
+    const float txc = rxc * t[2], tyc = ryc * t[2];
+    const float J00 = vd.fx * iz, J02 = -vd.fx * txc * iz2, J11 = vd.fy * iz, J12 = -vd.fy * tyc * iz2;
+    float T[6];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      T[b] = J00 * V[b] + J02 * V[8 + b];
+      T[3 + b] = J11 * V[4 + b] + J12 * V[8 + b];
+    }
+    float TS[6];  // T Sigma
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) TS[3 * a + b] = T[3 * a] * Sg[b] + T[3 * a + 1] * Sg[3 + b] + T[3 * a + 2] * Sg[6 + b];
+    const float ca = TS[0] * T[0] + TS[1] * T[1] + TS[2] * T[2] + P.dilation;
+    const float cb = TS[0] * T[3] + TS[1] * T[4] + TS[2] * T[5];
+    const float cc = TS[3] * T[3] + TS[4] * T[4] + TS[5] * T[5] + P.dilation;
+    const float idet = 1.0f / (ca * cc - cb * cb);
+    const float QA = cc * idet, QB = -cb * idet, QC = ca * idet;
+
+    // ---- conic = inverse(Sigma'):  dL/dSigma' = -Q G_Q Q,  G_Q = [[gA, gB/2], [gB/2, gC]]
+    const float h = 0.5f * g_B;
+    const float t00 = QA * g_A + QB * h, t01 = QA * h + QB * g_C;
+    const float t10 = QB * g_A + QC * h, t11 = QB * h + QC * g_C;
+    const float GS00 = -(t00 * QA + t01 * QB), GS01 = -(t00 * QB + t01 * QC), GS11 = -(t10 * QB + t11 * QC);
+    // ---- Sigma' = T Sigma T^T: G_Sigma = T^T GS T,  G_T = 2 GS T Sigma
+    float GT[6];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      GT[b] = 2.f * (GS00 * TS[b] + GS01 * TS[3 + b]);
+      GT[3 + b] = 2.f * (GS01 * TS[b] + GS11 * TS[3 + b]);
+    }
+    float GSig[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        GSig[3 * a + b] = T[a] * (GS00 * T[b] + GS01 * T[3 + b]) + T[3 + a] * (GS01 * T[b] + GS11 * T[3 + b]);
+    // ---- T = J W: only J00, J02, J11, J12 are non-zero
+    float gJ00 = 0.f, gJ02 = 0.f, gJ11 = 0.f, gJ12 = 0.f;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      gJ00 += GT[b] * V[b];
+      gJ02 += GT[b] * V[8 + b];
+      gJ11 += GT[3 + b] * V[4 + b];
+      gJ12 += GT[3 + b] * V[8 + b];
+    }
+    float gt[3] = {0.f, 0.f, 0.f};
+    gt[2] += gJ00 * (-vd.fx * iz2) + gJ11 * (-vd.fy * iz2);
+    gt[2] += gJ02 * (2.f * vd.fx * txc * iz2 * iz) + gJ12 * (2.f * vd.fy * tyc * iz2 * iz);
+    const float gtxc = gJ02 * (-vd.fx * iz2), gtyc = gJ12 * (-vd.fy * iz2);
+    if (clx) gt[2] += gtxc * rxc; else gt[0] += gtxc;
+    if (cly) gt[2] += gtyc * ryc; else gt[1] += gtyc;
+    // ---- 2D mean
+    gt[0] += g_mx * vd.fx * iz;
+    gt[1] += g_my * vd.fy * iz;
+    gt[2] += -(g_mx * vd.fx * t[0] + g_my * vd.fy * t[1]) * iz2;
+    float gmu[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) gmu[a] = V[a] * gt[0] + V[4 + a] * gt[1] + V[8 + a] * gt[2];
+    // ---- Sigma = M M^T: G_M = 2 G_Sigma M;  M = R diag(sp)
+    float gR[9], gsp[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        float gM = 2.f * (GSig[3 * a] * M[b] + GSig[3 * a + 1] * M[3 + b] + GSig[3 * a + 2] * M[6 + b]);
+        gR[3 * a + b] = gM * sp[b];
+        gsp[b] += gM * R[3 * a + b];
+      }
+    const float gphi = s[0] * gsp[0] + s[1] * gsp[1] + s[2] * gsp[2];
+    float gbeta = gphi * P.rho * phi * (1.0f - 0.5f * phi);
+    if (P.mode == 0) gbeta += 0.5f * g_hb;
+    // ---- rotation from the normalised quaternion
+    float gw = 2.f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
+    float gx = 2.f * (y * gR[1] + z * gR[2] + y * gR[3] - 2.f * x * gR[4] - w * gR[5] + z * gR[6] + w * gR[7] - 2.f * x * gR[8]);
+    float gy = 2.f * (-2.f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] + z * gR[7] - 2.f * y * gR[8]);
+    float gz = 2.f * (-2.f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * z * gR[4] + y * gR[5] + x * gR[6] + y * gR[7]);
+    const float dotq = w * gw + x * gx + y * gy + z * gz;
+    const float4 gq = make_float4((gw - w * dotq) * rn, (gx - x * dotq) * rn, (gy - y * dotq) * rn, (gz - z * dotq) * rn);
+
+    // ---- SH colour
+    const float dvx = mu[0] - vd.campos[0], dvy = mu[1] - vd.campos[1], dvz = mu[2] - vd.campos[2];
+    const float idn = rsqrtf(dvx * dvx + dvy * dvy + dvz * dvz);
+    const float dx = dvx * idn, dy = dvy * idn, dz = dvz * idn;
+    float Y[16];
+    float3 dY[16];
+    sh_eval(vd.sh_degree, dx, dy, dz, Y);
+    const float* sh = vd.shs + (int64_t)3 * nb * i;
+    float raw[3] = {0.5f, 0.5f, 0.5f};
+    for (int k = 0; k < nb; ++k) {
+      raw[0] += Y[k] * sh[3 * k];
+      raw[1] += Y[k] * sh[3 * k + 1];
+      raw[2] += Y[k] * sh[3 * k + 2];
+    }
+    const float graw[3] = {raw[0] > 0.f ? g_rgb[0] : 0.f, raw[1] > 0.f ? g_rgb[1] : 0.f, raw[2] > 0.f ? g_rgb[2] : 0.f};
+    float gd[3] = {0.f, 0.f, 0.f};
+    if (vd.sh_degree > 0) sh_grad(vd.sh_degree, dx, dy, dz, dY);
+    for (int k = 0; k < nb; ++k) {
+      gsh[3 * k] = Y[k] * graw[0];
+      gsh[3 * k + 1] = Y[k] * graw[1];
+      gsh[3 * k + 2] = Y[k] * graw[2];
+      if (k > 0) {
+        const float gy_k = sh[3 * k] * graw[0] + sh[3 * k + 1] * graw[1] + sh[3 * k + 2] * graw[2];
+        gd[0] += gy_k * dY[k].x;
+        gd[1] += gy_k * dY[k].y;
+        gd[2] += gy_k * dY[k].z;
+      }
+    }
+    const float dd = dx * gd[0] + dy * gd[1] + dz * gd[2];
+    gmu[0] += (gd[0] - dx * dd) * idn;
+    gmu[1] += (gd[1] - dy * dd) * idn;
+    gmu[2] += (gd[2] - dz * dd) * idn;
+
+    for (int k = 0; k < 3; ++k) {
+      vd.g_means[3 * i + k] = gmu[k];
+      vd.g_scales[3 * i + k] = phi * gsp[k];
+    }
+    *reinterpret_cast<float4*>(vd.g_quats + 4 * i) = gq;
+    vd.g_betas[i] = gbeta;
+    vd.g_opac[i] = g_kappa;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// launch helpers
+// ---------------------------------------------------------------------------------------------
+static int grid_for(int64_t total, int num_sms) {
+  // grid-stride kernels: enough CTAs for 8 resident 256-thread CTAs per SM, no more than needed
+  int64_t need = (total + 255) / 256;
+  int64_t cap = (int64_t)num_sms * 8;
+  return (int)(need < cap ? (need > 0 ? need : 1) : cap);
+}
+
+template <int MAXV>
+void launch_preprocess(const ViewTable<MAXV>& vt, int64_t total, const Params& P, uint32_t* depth_key,
+                       uint32_t* sort_vals, ushort4* rect, Rec* rec, int num_sms, cudaStream_t s) {
+  if (total <= 0) return;
+  k_preprocess<MAXV><<<grid_for(total, num_sms), 256, 0, s>>>(vt, total, P, depth_key, sort_vals, rect, rec);
+  count_launches(1);
+}
+
+template <int MAXV>
+void launch_preprocess_bwd(const ViewTable<MAXV>& vt, int64_t total, const Params& P, const uint32_t* depth_key,
+                           const float4* g2d, int num_sms, cudaStream_t s) {
+  if (total <= 0) return;
+  k_preprocess_bwd<MAXV><<<grid_for(total, num_sms), 256, 0, s>>>(vt, total, P, depth_key, g2d);
+  count_launches(1);
+}
+
+// ln2^k / k! rounded to float, computed here in long double and uploaded once per stream use
+void set_key_constants(cudaStream_t s) {
+  float c[8];
+  long double ln2 = 0.693147180559945309417232121458176568L;
+  long double t = 1.0L;
+  for (int k = 0; k < 8; ++k) {
+    if (k > 0) t = t * ln2 / (long double)k;
+    c[k] = (float)t;
+  }
+  cudaMemcpyToSymbolAsync(c_exp2_coef, c, sizeof(c), 0, cudaMemcpyHostToDevice, s);
+}
+
+template void launch_preprocess<1>(const ViewTable<1>&, int64_t, const Params&, uint32_t*, uint32_t*, ushort4*, Rec*,
+                                   int, cudaStream_t);
+template void launch_preprocess<kServeMaxViews>(const ViewTable<kServeMaxViews>&, int64_t, const Params&, uint32_t*,
+                                                uint32_t*, ushort4*, Rec*, int, cudaStream_t);
+template void launch_preprocess_bwd<1>(const ViewTable<1>&, int64_t, const Params&, const uint32_t*, const float4*, int,
+                                       cudaStream_t);
+template void launch_preprocess_bwd<kServeMaxViews>(const ViewTable<kServeMaxViews>&, int64_t, const Params&,
+                                                    const uint32_t*, const float4*, int, cudaStream_t);
+
+}  // namespace ges

@@ -1,0 +1,388 @@
+// Binning: duplicate (tile, primitive) keys and sort them by tile, then depth.
+//
+// The result is a stable sort of the 64-bit keys (tile << 32 | depth bits) with values =
+// primitive index, computed as an LSD radix sort whose low 32-bit passes run on the N
+// primitives instead of the K duplicates: every duplicate of a primitive shares its depth
+// bits, so sorting primitives by depth first and duplicating them in that order gives the
+// same list as sorting the duplicates on the depth digits.  The remaining passes are a
+// stable radix sort of the duplicates on the tile id alone (ceil(log2 tiles) bits).
+//   K2  exclusive scan of tiles touched, in depth order        (u64 offsets, K on the device)
+//   K3  keygen: load-balanced expansion, one thread per output entry
+//   K4  stable LSD radix passes (<= 8-bit digits): per-chunk histogram, scan, stable scatter
+//   K5  per-tile [start, end) from the sorted tile ids
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace ges {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = 16;
+constexpr int kChunk = kThreads * kItems;  // elements per CTA in scans and radix passes
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_scan(T v) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, v, o);
+    if ((int)lane_id() >= o) v += y;
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------- scan kernels
+template <typename TIn, typename TOut>
+__global__ void __launch_bounds__(kThreads) k_scan_reduce(const TIn* __restrict__ in, int64_t n, TOut* __restrict__ sums) {
+  const int64_t base = (int64_t)blockIdx.x * kChunk + (int64_t)threadIdx.x * kItems;
+  TOut acc = 0;
+#pragma unroll
+  for (int k = 0; k < kItems; ++k)
+    if (base + k < n) acc += (TOut)in[base + k];
+  __shared__ TOut red[kThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane_id() == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    TOut t = 0;
+    for (int w = 0; w < kThreads / 32; ++w) t += red[w];
+    sums[blockIdx.x] = t;
+  }
+}
+
+// exclusive scan of one chunk per CTA plus a per-CTA offset (block_off may be null)
+template <typename TIn, typename TOut>
+__global__ void __launch_bounds__(kThreads) k_scan_down(const TIn* __restrict__ in, TOut* __restrict__ out, int64_t n,
+                                                        const TOut* __restrict__ block_off, TOut* __restrict__ total) {
+  const int64_t base = (int64_t)blockIdx.x * kChunk + (int64_t)threadIdx.x * kItems;
+  TOut v[kItems];
+  TOut acc = 0;
+#pragma unroll
+  for (int k = 0; k < kItems; ++k) {
+    v[k] = (base + k < n) ? (TOut)in[base + k] : TOut(0);
+    acc += v[k];
+  }
+  __shared__ TOut ws[kThreads / 32 + 1];
+  TOut inc = warp_inclusive_scan(acc);
+  const int w = threadIdx.x >> 5;
+  if (lane_id() == 31) ws[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    TOut x = (lane_id() < kThreads / 32) ? ws[lane_id()] : TOut(0);
+    TOut xi = warp_inclusive_scan(x);
+    if (lane_id() < kThreads / 32) ws[lane_id()] = xi - x;
+    if (lane_id() == 31) ws[kThreads / 32] = xi;
+  }
+  __syncthreads();
+  TOut run = inc - acc + ws[w] + (block_off ? block_off[blockIdx.x] : TOut(0));
+  // in may alias out: all loads of this thread happened above
+#pragma unroll
+  for (int k = 0; k < kItems; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+  if (total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0)
+    *total = (block_off ? block_off[blockIdx.x] : TOut(0)) + ws[kThreads / 32];
+}
+
+// ---------------------------------------------------------------- radix kernels
+// hist layout: [bin][chunk] so that one exclusive scan gives every (bin, chunk) output offset
+// element count of a radix pass: the device count (0 if it exceeds the buffer capacity) or the host one
+__device__ __forceinline__ int64_t element_count(int64_t n_host, const unsigned long long* n_dev, int64_t cap) {
+  if (!n_dev) return n_host;
+  const unsigned long long n = *n_dev;
+  return n > (unsigned long long)cap ? 0 : (int64_t)n;
+}
+
+__global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restrict__ keys, int64_t n_host,
+                                                         const unsigned long long* __restrict__ n_dev, int64_t cap,
+                                                         int shift, int bits,
+                                                         uint32_t* __restrict__ hist, int64_t nchunks) {
+  __shared__ uint32_t cnt[256];
+  const int nbins = 1 << bits;
+  for (int b = threadIdx.x; b < nbins; b += kThreads) cnt[b] = 0;
+  __syncthreads();
+  const int64_t n = element_count(n_host, n_dev, cap);
+  const int64_t base = (int64_t)blockIdx.x * kChunk;
+  const uint32_t mask = (uint32_t)nbins - 1u;
+  if (base < n) {
+#pragma unroll 4
+    for (int k = 0; k < kItems; ++k) {
+      int64_t idx = base + (int64_t)k * kThreads + threadIdx.x;
+      if (idx < n) atomicAdd(&cnt[(keys[idx] >> shift) & mask], 1u);
+    }
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nbins; b += kThreads) hist[(int64_t)b * nchunks + blockIdx.x] = cnt[b];
+}
+
+// Stable scatter.  Warp w of the CTA owns chunk elements [w*512, (w+1)*512) and walks them in
+// order, 32 at a time; lanes with equal digits are ranked by lane order (match.any), so the
+// final position preserves input order within each digit.
+__global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __restrict__ keys_in,
+                                                            const uint32_t* __restrict__ vals_in,
+                                                            uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+                                                            int64_t n_host, const unsigned long long* __restrict__ n_dev,
+                                                            int64_t cap, int shift, int bits,
+                                                            const uint32_t* __restrict__ hist_scanned,
+                                                            int64_t nchunks) {
+  constexpr int kWarps = kThreads / 32;
+  __shared__ uint32_t wcnt[kWarps][257];
+  __shared__ uint32_t goff[256];
+  const int nbins = 1 << bits;
+  const uint32_t mask = (uint32_t)nbins - 1u;
+  const int64_t n = element_count(n_host, n_dev, cap);
+  const int64_t base = (int64_t)blockIdx.x * kChunk;
+  if (base >= n) return;  // uniform across the CTA
+  const int w = threadIdx.x >> 5;
+  const unsigned lane = lane_id();
+  for (int i = threadIdx.x; i < kWarps * 257; i += kThreads) (&wcnt[0][0])[i] = 0;
+  for (int b = threadIdx.x; b < nbins; b += kThreads) goff[b] = hist_scanned[(int64_t)b * nchunks + blockIdx.x];
+  __syncthreads();
+  const unsigned lt_mask = (1u << lane) - 1u;
+  uint32_t key[kItems], val[kItems], rank[kItems];
+  int dig[kItems];
+#pragma unroll
+  for (int r = 0; r < kItems; ++r) {
+    const int64_t idx = base + (int64_t)w * (kItems * 32) + r * 32 + lane;
+    const bool ok = idx < n;
+    key[r] = ok ? keys_in[idx] : 0u;
+    val[r] = ok ? vals_in[idx] : 0u;
+    const int d = ok ? (int)((key[r] >> shift) & mask) : 256;
+    dig[r] = d;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t prev = wcnt[w][d];
+    __syncwarp();
+    if ((peers & lt_mask) == 0) wcnt[w][d] = prev + (uint32_t)__popc(peers);
+    __syncwarp();
+    rank[r] = prev + (uint32_t)__popc(peers & lt_mask);
+  }
+  __syncthreads();
+  // exclusive prefix over warps, per digit
+  for (int b = threadIdx.x; b < nbins; b += kThreads) {
+    uint32_t run = 0;
+#pragma unroll
+    for (int ww = 0; ww < kWarps; ++ww) {
+      uint32_t c = wcnt[ww][b];
+      wcnt[ww][b] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kItems; ++r) {
+    const int d = dig[r];
+    if (d < 256) {
+      const uint32_t pos = goff[d] + wcnt[w][d] + rank[r];
+      keys_out[pos] = key[r];
+      vals_out[pos] = val[r];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- K2 input
+__global__ void k_gather_touched(const uint32_t* __restrict__ sorted_vals, const ushort4* __restrict__ rect, int64_t n,
+                                 uint32_t* __restrict__ touched) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const ushort4 r = rect[sorted_vals[j]];
+    touched[j] = (uint32_t)(r.z - r.x) * (uint32_t)(r.w - r.y);
+  }
+}
+
+// ---------------------------------------------------------------- K3 keygen
+constexpr int kKeygenEntries = 2048;
+
+template <int MAXV>
+__global__ void __launch_bounds__(kThreads) k_keygen(const __grid_constant__ ViewTable<MAXV> vt,
+                                                     const unsigned long long* __restrict__ offsets,
+                                                     const unsigned long long* __restrict__ K_dev, int64_t n,
+                                                     const uint32_t* __restrict__ sorted_vals,
+                                                     const ushort4* __restrict__ rect, int64_t cap,
+                                                     uint32_t* __restrict__ tile_keys, uint32_t* __restrict__ tile_vals,
+                                                     uint32_t* __restrict__ flags) {
+  __shared__ uint32_t win[kKeygenEntries + 2];
+  __shared__ int64_t s_jlo, s_jhi;
+  const unsigned long long K = *K_dev;
+  if ((int64_t)K > cap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(flags, kFlagOverflow);
+    return;
+  }
+  const int64_t e0 = (int64_t)blockIdx.x * kKeygenEntries;
+  if (e0 >= (int64_t)K) return;
+  const int64_t e1 = min(e0 + (int64_t)kKeygenEntries, (int64_t)K);
+  if (threadIdx.x < 2) {
+    // last j with offsets[j] <= e (for e = e0 and e = e1 - 1)
+    const unsigned long long e = threadIdx.x == 0 ? (unsigned long long)e0 : (unsigned long long)(e1 - 1);
+    int64_t lo = 0, hi = n;  // first j with offsets[j] > e lies in (lo, hi]
+    while (lo < hi) {
+      int64_t mid = (lo + hi) >> 1;
+      if (offsets[mid] <= e) lo = mid + 1; else hi = mid;
+    }
+    if (threadIdx.x == 0) s_jlo = lo - 1; else s_jhi = lo - 1;
+  }
+  __syncthreads();
+  const int64_t jlo = s_jlo, jhi = s_jhi;
+  const int wn = (int)(jhi - jlo + 1);  // <= kKeygenEntries (each primitive in the window owns >= 1 entry)
+  for (int k = threadIdx.x; k < wn; k += kThreads) {
+    unsigned long long o = offsets[jlo + k];
+    win[k] = (uint32_t)((o > (unsigned long long)e0 ? o : (unsigned long long)e0) - (unsigned long long)e0);
+  }
+  __syncthreads();
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += kThreads) {
+    const uint32_t rel = (uint32_t)(e - e0);
+    int lo = 0, hi = wn - 1;  // last k with win[k] <= rel
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (win[mid] <= rel) lo = mid; else hi = mid - 1;
+    }
+    const int64_t j = jlo + lo;
+    const uint32_t g = sorted_vals[j];
+    const uint32_t local = (uint32_t)(e - (int64_t)offsets[j]);
+    const ushort4 r = rect[g];
+    const uint32_t rw = (uint32_t)(r.z - r.x);
+    const uint32_t tyy = local / rw, txx = local - tyy * rw;
+    const ViewDesc& vd = vt.v[view_of_prim(vt, (int64_t)g)];
+    tile_keys[e] = (uint32_t)vd.tile_base + ((uint32_t)r.y + tyy) * (uint32_t)vd.tiles_x + (uint32_t)r.x + txx;
+    tile_vals[e] = g;
+  }
+}
+
+// ---------------------------------------------------------------- K5 ranges
+__global__ void k_ranges(const uint32_t* __restrict__ tile_keys, const unsigned long long* __restrict__ K_dev, int64_t cap,
+                         uint2* __restrict__ ranges) {
+  const int64_t K = (int64_t)*K_dev;
+  if (K > cap) return;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < K; e += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t t = tile_keys[e];
+    if (e == 0 || tile_keys[e - 1] != t) ranges[t].x = (uint32_t)e;
+    if (e == K - 1 || tile_keys[e + 1] != t) ranges[t].y = (uint32_t)(e + 1);
+  }
+}
+
+__global__ void k_make_keys(const uint32_t* __restrict__ tile_keys, const uint32_t* __restrict__ tile_vals,
+                            const uint32_t* __restrict__ depth_key, const unsigned long long* __restrict__ K_dev,
+                            int64_t cap, unsigned long long* __restrict__ keys64) {
+  const int64_t K = (int64_t)*K_dev;
+  if (K > cap) return;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < K; e += (int64_t)gridDim.x * blockDim.x)
+    keys64[e] = ((unsigned long long)tile_keys[e] << 32) | depth_key[tile_vals[e]];
+}
+
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace
+
+// ---------------------------------------------------------------- host drivers
+size_t ScanScratch::required(int64_t max_n) {
+  size_t total = 0;
+  int64_t n = max_n;
+  while (n > kChunk) {
+    n = cdiv(n, kChunk);
+    total += (size_t)(n + 1) * sizeof(unsigned long long);
+  }
+  return total + 256;
+}
+
+template <typename TIn, typename TOut>
+static void scan_level(const TIn* in, TOut* out, int64_t n, TOut* total, char* scratch, cudaStream_t s) {
+  const int64_t nb = cdiv(n, kChunk);
+  if (nb <= 1) {
+    k_scan_down<TIn, TOut><<<1, kThreads, 0, s>>>(in, out, n, nullptr, total);
+    count_launches(1);
+    return;
+  }
+  TOut* sums = reinterpret_cast<TOut*>(scratch);
+  char* next = scratch + (size_t)(nb + 1) * sizeof(unsigned long long);
+  k_scan_reduce<TIn, TOut><<<(unsigned)nb, kThreads, 0, s>>>(in, n, sums);
+  scan_level<TOut, TOut>(sums, sums, nb, (TOut*)nullptr, next, s);
+  k_scan_down<TIn, TOut><<<(unsigned)nb, kThreads, 0, s>>>(in, out, n, sums, total);
+  count_launches(2);
+}
+
+template <typename TIn, typename TOut>
+void scan_exclusive(const TIn* in, TOut* out, int64_t n, TOut* total, ScanScratch& sc, cudaStream_t s) {
+  if (n <= 0) {
+    if (total) cudaMemsetAsync(total, 0, sizeof(TOut), s);
+    return;
+  }
+  scan_level<TIn, TOut>(in, out, n, total, reinterpret_cast<char*>(sc.buf), s);
+}
+
+template void scan_exclusive<uint32_t, uint32_t>(const uint32_t*, uint32_t*, int64_t, uint32_t*, ScanScratch&, cudaStream_t);
+template void scan_exclusive<uint32_t, unsigned long long>(const uint32_t*, unsigned long long*, int64_t,
+                                                           unsigned long long*, ScanScratch&, cudaStream_t);
+
+void launch_gather_touched(const uint32_t* sorted_vals, const ushort4* rect, int64_t n, uint32_t* touched, cudaStream_t s) {
+  if (n <= 0) return;
+  int64_t blocks = cdiv(n, 256);
+  if (blocks > 65535 * 8) blocks = 65535 * 8;
+  k_gather_touched<<<(unsigned)blocks, 256, 0, s>>>(sorted_vals, rect, n, touched);
+  count_launches(1);
+}
+
+int64_t radix_hist_entries(int64_t n_cap, int total_bits) {
+  int passes = (total_bits + 7) / 8;
+  if (passes < 1) passes = 1;
+  int bits = (total_bits + passes - 1) / passes;
+  return ((int64_t)1 << bits) * cdiv(n_cap > 0 ? n_cap : 1, kChunk);
+}
+
+void radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_host, const unsigned long long* n_dev,
+                      int64_t n_cap, int total_bits, uint32_t* hist, int64_t hist_cap, ScanScratch& sc, cudaStream_t s) {
+  if (n_cap <= 0 || total_bits <= 0) return;
+  const int passes = (total_bits + 7) / 8;
+  const int bits_per = (total_bits + passes - 1) / passes;
+  const int64_t nchunks = cdiv(n_cap, kChunk);
+  for (int p = 0; p < passes; ++p) {
+    const int shift = p * bits_per;
+    const int bits = (total_bits - shift) < bits_per ? (total_bits - shift) : bits_per;
+    const int64_t entries = ((int64_t)1 << bits) * nchunks;
+    (void)hist_cap;
+    k_radix_hist<<<(unsigned)nchunks, kThreads, 0, s>>>(keys[cur], n_host, n_dev, n_cap, shift, bits, hist, nchunks);
+    scan_exclusive<uint32_t, uint32_t>(hist, hist, entries, (uint32_t*)nullptr, sc, s);
+    k_radix_scatter<<<(unsigned)nchunks, kThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_host,
+                                                           n_dev, n_cap, shift, bits, hist, nchunks);
+    count_launches(2);
+    cur ^= 1;
+  }
+}
+
+template <int MAXV>
+void launch_keygen(const ViewTable<MAXV>& vt, const unsigned long long* offsets, const unsigned long long* K_dev, int64_t n,
+                   const uint32_t* sorted_vals, const ushort4* rect, int64_t cap, uint32_t* tile_keys, uint32_t* tile_vals,
+                   uint32_t* flags, cudaStream_t s) {
+  if (n <= 0 || cap <= 0) return;
+  const int64_t blocks = cdiv(cap, kKeygenEntries);
+  k_keygen<MAXV><<<(unsigned)blocks, kThreads, 0, s>>>(vt, offsets, K_dev, n, sorted_vals, rect, cap, tile_keys, tile_vals,
+                                                       flags);
+  count_launches(1);
+}
+
+void launch_ranges(const uint32_t* tile_keys, const unsigned long long* K_dev, int64_t cap, uint2* ranges, int num_sms,
+                   cudaStream_t s) {
+  if (cap <= 0) return;
+  int64_t blocks = cdiv(cap, 256);
+  if (blocks > (int64_t)num_sms * 16) blocks = (int64_t)num_sms * 16;
+  k_ranges<<<(unsigned)blocks, 256, 0, s>>>(tile_keys, K_dev, cap, ranges);
+  count_launches(1);
+}
+
+void launch_make_keys(const uint32_t* tile_keys, const uint32_t* tile_vals, const uint32_t* depth_key,
+                      const unsigned long long* K_dev, int64_t cap, unsigned long long* keys64, cudaStream_t s) {
+  if (cap <= 0) return;
+  int64_t blocks = cdiv(cap, 256);
+  if (blocks > 4096) blocks = 4096;
+  k_make_keys<<<(unsigned)blocks, 256, 0, s>>>(tile_keys, tile_vals, depth_key, K_dev, cap, keys64);
+  count_launches(1);
+}
+
+template void launch_keygen<1>(const ViewTable<1>&, const unsigned long long*, const unsigned long long*, int64_t,
+                               const uint32_t*, const ushort4*, int64_t, uint32_t*, uint32_t*, uint32_t*, cudaStream_t);
+template void launch_keygen<kServeMaxViews>(const ViewTable<kServeMaxViews>&, const unsigned long long*,
+                                            const unsigned long long*, int64_t, const uint32_t*, const ushort4*, int64_t,
+                                            uint32_t*, uint32_t*, uint32_t*, cudaStream_t);
+
+}  // namespace ges

@@ -1,0 +1,300 @@
+"""Python binding of libges (include/ges.h).
+
+Argument marshalling only: every step of the rasterizer runs in the CUDA
+library.  The functions carry the C names (``ges_preprocess`` ...) and raise
+``GesError`` on a non-OK status.  Importing this module loads
+``_build/libges.so`` and raises if it has not been built -- there is no
+fallback path.
+
+Device arrays are passed as ``torch.Tensor`` (contiguous, on the library's
+device) or raw integer addresses; host arrays as numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libges.so")
+
+GES_OK = 0
+GES_ERR_INVALID_ARG = 1
+GES_ERR_OOM = 2
+GES_ERR_CUDA = 3
+GES_ERR_CAPACITY = 4
+GES_ERR_NOT_READY = 5
+GES_ERR_TIMEOUT = 6
+GES_ERR_BUSY = 7
+GES_ERR_DEVICE_WAIT = 8
+STATUS_NAMES = {0: "GES_OK", 1: "GES_ERR_INVALID_ARG", 2: "GES_ERR_OOM", 3: "GES_ERR_CUDA", 4: "GES_ERR_CAPACITY",
+                5: "GES_ERR_NOT_READY", 6: "GES_ERR_TIMEOUT", 7: "GES_ERR_BUSY", 8: "GES_ERR_DEVICE_WAIT"}
+
+GES_FALLOFF_GEF = 0
+GES_FALLOFF_PAPER_APPROX = 1
+
+# every symbol declared in include/ges.h
+EXPORTED = ["ges_last_error", "ges_params_default", "ges_ctx_create", "ges_ctx_destroy", "ges_frame_create",
+            "ges_frame_destroy", "ges_preprocess", "ges_bin_sort", "ges_render_fwd", "ges_render_bwd",
+            "ges_frame_status", "ges_frame_keys", "ges_frame_inspect", "ges_frame_count_work",
+            "ges_kernel_launches", "ges_serve_create", "ges_serve_add_scene",
+            "ges_serve_submit", "ges_serve_poll", "ges_serve_destroy"]
+
+
+class GesError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ges_camera(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("viewmat", ctypes.c_float * 16), ("campos", ctypes.c_float * 3), ("znear", ctypes.c_float),
+                ("bg", ctypes.c_float * 3)]
+
+
+class ges_params(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_float), ("falloff", ctypes.c_int32), ("dilation", ctypes.c_float),
+                ("alpha_max", ctypes.c_float), ("alpha_min", ctypes.c_float), ("t_min", ctypes.c_float),
+                ("extent_margin_rel", ctypes.c_float), ("extent_margin_abs", ctypes.c_float),
+                ("clamp_fov", ctypes.c_float)]
+
+
+class ges_scene(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("sh_degree", ctypes.c_int32), ("means", ctypes.c_void_p),
+                ("scales", ctypes.c_void_p), ("quats", ctypes.c_void_p), ("betas", ctypes.c_void_p),
+                ("opacities", ctypes.c_void_p), ("shs", ctypes.c_void_p)]
+
+
+class ges_grads(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("betas", ctypes.c_void_p), ("opacities", ctypes.c_void_p), ("shs", ctypes.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libges is not built ({_LIB_PATH} missing); run __graft_entry__.build()")
+    lib = ctypes.CDLL(_LIB_PATH)
+    P, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    sig = {
+        "ges_last_error": ([], ctypes.c_char_p),
+        "ges_params_default": ([P], i32),
+        "ges_ctx_create": ([ctypes.c_int, ctypes.c_size_t, P], i32),
+        "ges_ctx_destroy": ([P], None),
+        "ges_frame_create": ([P, i64, i32, i32, i64, P], i32),
+        "ges_frame_destroy": ([P], None),
+        "ges_preprocess": ([P, P, P, P, P], i32),
+        "ges_bin_sort": ([P, P], i32),
+        "ges_render_fwd": ([P, P, P, P, P], i32),
+        "ges_render_bwd": ([P, P, P, P, P, P, P], i32),
+        "ges_frame_status": ([P, P, P], i32),
+        "ges_frame_keys": ([P, P, P, P, i64, P], i32),
+        "ges_frame_inspect": ([P, P, P, P, P, P, P], i32),
+        "ges_frame_count_work": ([P, P, P, P, P], i32),
+        "ges_kernel_launches": ([], u64),
+        "ges_serve_create": ([P, P, i32, P], i32),
+        "ges_serve_add_scene": ([P, P, P], i32),
+        "ges_serve_submit": ([P, i32, P, P, P], i32),
+        "ges_serve_poll": ([P, u64, i64, P], i32),
+        "ges_serve_destroy": ([P], i32),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = _load()
+LIB_PATH = _LIB_PATH
+
+
+def last_error() -> str:
+    return _lib.ges_last_error().decode()
+
+
+def _check(status):
+    if status != GES_OK:
+        raise GesError(status, last_error())
+    return status
+
+
+def _addr(t):
+    """Device/host address of a tensor, numpy array, int or None."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"]
+        return t.ctypes.data
+    assert t.is_contiguous(), "arrays must be contiguous"
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ------------------------------------------------------------------ struct builders
+def params_default() -> ges_params:
+    p = ges_params()
+    _check(_lib.ges_params_default(ctypes.byref(p)))
+    return p
+
+
+def make_params(**kw) -> ges_params:
+    p = params_default()
+    alias = {"mode": "falloff", "margin_rel": "extent_margin_rel", "margin_abs": "extent_margin_abs"}
+    for k, v in kw.items():
+        setattr(p, alias.get(k, k), v)
+    return p
+
+
+def make_camera(cam) -> ges_camera:
+    """From any object with width, height, fx, fy, cx, cy, viewmat (4x4), campos, znear, bg."""
+    c = ges_camera()
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    vm = np.asarray(cam.viewmat, np.float32).reshape(16)
+    for i in range(16):
+        c.viewmat[i] = float(vm[i])
+    cp = np.asarray(cam.campos, np.float32).reshape(3)
+    bg = np.asarray(cam.bg, np.float32).reshape(3)
+    for i in range(3):
+        c.campos[i] = float(cp[i])
+        c.bg[i] = float(bg[i])
+    c.znear = float(cam.znear)
+    return c
+
+
+def make_scene(means, scales, quats, betas, opacities, shs, sh_degree) -> ges_scene:
+    s = ges_scene()
+    s.n = int(means.shape[0])
+    s.sh_degree = int(sh_degree)
+    s.means, s.scales, s.quats = _addr(means), _addr(scales), _addr(quats)
+    s.betas, s.opacities, s.shs = _addr(betas), _addr(opacities), _addr(shs)
+    return s
+
+
+def make_grads(means, scales, quats, betas, opacities, shs) -> ges_grads:
+    g = ges_grads()
+    g.means, g.scales, g.quats = _addr(means), _addr(scales), _addr(quats)
+    g.betas, g.opacities, g.shs = _addr(betas), _addr(opacities), _addr(shs)
+    return g
+
+
+# ------------------------------------------------------------------ C entry points
+def ges_ctx_create(device: int = 0, hbm_budget_bytes: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.ges_ctx_create(int(device), int(hbm_budget_bytes), ctypes.byref(h)))
+    return h.value
+
+
+def ges_ctx_destroy(ctx: int) -> None:
+    _lib.ges_ctx_destroy(ctx)
+
+
+def ges_frame_create(ctx: int, n_capacity: int, width: int, height: int, key_capacity: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.ges_frame_create(ctx, int(n_capacity), int(width), int(height), int(key_capacity), ctypes.byref(h)))
+    return h.value
+
+
+def ges_frame_destroy(frame: int) -> None:
+    _lib.ges_frame_destroy(frame)
+
+
+def ges_preprocess(frame: int, scene: ges_scene, cam: ges_camera, params: ges_params, stream=None) -> None:
+    _check(_lib.ges_preprocess(frame, ctypes.byref(scene), ctypes.byref(cam), ctypes.byref(params), _stream(stream)))
+
+
+def ges_bin_sort(frame: int, stream=None) -> None:
+    _check(_lib.ges_bin_sort(frame, _stream(stream)))
+
+
+def ges_render_fwd(frame: int, img, final_T, n_contrib, stream=None) -> None:
+    _check(_lib.ges_render_fwd(frame, _addr(img), _addr(final_T), _addr(n_contrib), _stream(stream)))
+
+
+def ges_render_bwd(frame: int, scene: ges_scene, final_T, n_contrib, dL_dimg, grads: ges_grads, stream=None) -> None:
+    _check(_lib.ges_render_bwd(frame, ctypes.byref(scene), _addr(final_T), _addr(n_contrib), _addr(dL_dimg),
+                               ctypes.byref(grads), _stream(stream)))
+
+
+def ges_frame_status(frame: int, stream=None):
+    """Returns (status, K) without raising on GES_ERR_CAPACITY."""
+    k = ctypes.c_int64(0)
+    st = _lib.ges_frame_status(frame, _stream(stream), ctypes.byref(k))
+    if st not in (GES_OK, GES_ERR_CAPACITY):
+        _check(st)
+    return st, int(k.value)
+
+
+def ges_frame_keys(frame: int, stream=None):
+    """Sorted 64-bit keys and values of the last ges_bin_sort (host numpy arrays)."""
+    st, K = ges_frame_status(frame, stream)
+    _check(st)
+    keys = np.empty(K, np.uint64)
+    vals = np.empty(K, np.uint32)
+    k = ctypes.c_int64(0)
+    _check(_lib.ges_frame_keys(frame, _stream(stream), _addr(keys) if K else None, _addr(vals) if K else None,
+                               K, ctypes.byref(k)))
+    return keys, vals
+
+
+def ges_frame_inspect(frame: int, n: int, n_tiles: int, stream=None):
+    out = dict(depth_key=np.empty(n, np.uint32), rect=np.empty((n, 4), np.int32),
+               record=np.empty((n, 12), np.float32), ranges=np.empty((n_tiles, 2), np.uint32),
+               grad2d=np.empty((n, 12), np.float32))
+    _check(_lib.ges_frame_inspect(frame, _stream(stream), _addr(out["depth_key"]), _addr(out["rect"]),
+                                  _addr(out["record"]), _addr(out["ranges"]), _addr(out["grad2d"])))
+    return out
+
+
+def ges_frame_count_work(frame: int, stream=None):
+    """(evaluated, in_extent, K) of the last binned frame (synchronises)."""
+    a, b, k = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(_lib.ges_frame_count_work(frame, _stream(stream), ctypes.byref(a), ctypes.byref(b), ctypes.byref(k)))
+    return int(a.value), int(b.value), int(k.value)
+
+
+def ges_kernel_launches() -> int:
+    return int(_lib.ges_kernel_launches())
+
+
+def ges_serve_create(ctx: int, params: ges_params, max_slots: int) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.ges_serve_create(ctx, ctypes.byref(params), int(max_slots), ctypes.byref(h)))
+    return h.value
+
+
+def ges_serve_add_scene(srv: int, host_scene: ges_scene) -> int:
+    sid = ctypes.c_int32(-1)
+    _check(_lib.ges_serve_add_scene(srv, ctypes.byref(host_scene), ctypes.byref(sid)))
+    return int(sid.value)
+
+
+def ges_serve_submit(srv: int, scene_id: int, cam: ges_camera, out_img: np.ndarray) -> int:
+    t = ctypes.c_uint64(0)
+    _check(_lib.ges_serve_submit(srv, int(scene_id), ctypes.byref(cam), _addr(out_img), ctypes.byref(t)))
+    return int(t.value)
+
+
+def ges_serve_poll(srv: int, ticket: int, timeout_us: int = 0):
+    """Returns (status, latency_ms); status is GES_OK, GES_ERR_NOT_READY or GES_ERR_TIMEOUT."""
+    lat = ctypes.c_float(0.0)
+    st = _lib.ges_serve_poll(srv, int(ticket), int(timeout_us), ctypes.byref(lat))
+    if st not in (GES_OK, GES_ERR_NOT_READY, GES_ERR_TIMEOUT):
+        _check(st)
+    return st, float(lat.value)
+
+
+def ges_serve_destroy(srv: int) -> None:
+    _check(_lib.ges_serve_destroy(srv))
