@@ -166,6 +166,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=N_PRIMS)
+    ap.add_argument("--profile", action="store_true",
+                    help="minimal run for ncu: no work counters, e2e or CPU baseline; warmup + steps fwd+bwd")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference" or os.environ.get("GES_BENCH_ALLOW_SHORT")
     ws, rank, local = _dist()
@@ -197,11 +199,15 @@ def main():
     # key capacity: the largest K over the camera set, plus headroom (no host sync per frame)
     probe = render.Frame(sc.n, WIDTH, HEIGHT, key_capacity=0, ctx=ctx)
     Ks, Fs = [], []
-    for cam in cams:
+    for cam in (cams[:1] if args.profile else cams):
         probe.forward(t, sc.sh_degree, cam)
-        ev, inr, K = ges.ges_frame_count_work(probe.handle)
-        Ks.append(K)
-        Fs.append((ev, inr))
+        if args.profile:
+            Ks.append(int(ges.ges_frame_status(probe.handle)[1] * 1.3))
+            Fs.append((0, 0))
+        else:
+            ev, inr, K = ges.ges_frame_count_work(probe.handle)
+            Ks.append(K)
+            Fs.append((ev, inr))
     probe.close()
     del probe
     cap = int(max(Ks) * 1.05) + 4096
@@ -261,6 +267,10 @@ def main():
             ms = float(x.item())
         return ms, launches
 
+    if args.profile:
+        timed(args.steps, bwd=True)
+        print(json.dumps({"profile_run": True, "K": Ks[0]}))
+        return
     with ClockSampler(local) as clk:
         ms_fb, launches = timed(args.steps, bwd=True)
         stage = np.array([[ev[i][k].elapsed_time(ev[i][k + 1]) for k in range(nst - 1)] for i in range(args.steps)])

@@ -114,6 +114,8 @@ ges_status check_scene(const ges_scene* s) {
   if (s->n > 0 && (!s->means || !s->scales || !s->quats || !s->betas || !s->opacities || !s->shs))
     return fail(GES_ERR_INVALID_ARG, "scene array pointer is NULL");
   if (((uintptr_t)s->quats) & 15u) return fail(GES_ERR_INVALID_ARG, "quats must be 16-byte aligned");
+  if ((s->sh_degree == 1 || s->sh_degree == 3) && (((uintptr_t)s->shs) & 15u))
+    return fail(GES_ERR_INVALID_ARG, "shs must be 16-byte aligned for SH degree 1 and 3");
   return GES_OK;
 }
 
@@ -314,11 +316,7 @@ ges_status ges_preprocess(ges_frame* f, const ges_scene* scene, const ges_camera
   f->P = to_params(*params);
   f->n = scene->n;
   f->sh_degree = scene->sh_degree;
-  launch_preprocess<1>(f->vt, f->n, f->P, f->depth_key, f->pv[0], f->rect, f->rec, f->ctx->num_sms, s);
-  if (f->n > 0) {
-    cudaError_t e = cudaMemcpyAsync(f->dk[0], f->depth_key, 4 * f->n, cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(e, "copy depth keys");
-  }
+  launch_preprocess<1>(f->vt, f->n, f->P, f->depth_key, f->dk[0], f->pv[0], f->rect, f->rec, f->ctx->num_sms, s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "preprocess launch");
   f->have_pre = true;
@@ -389,7 +387,8 @@ ges_status ges_render_bwd(ges_frame* f, const ges_scene* scene, const float* fin
     return fail(GES_ERR_INVALID_ARG, "scene differs from the one preprocessed");
   if (f->n > 0 && (!out->means || !out->scales || !out->quats || !out->betas || !out->opacities || !out->shs))
     return fail(GES_ERR_INVALID_ARG, "gradient pointer is NULL");
-  if (((uintptr_t)out->quats) & 15u) return fail(GES_ERR_INVALID_ARG, "grad quats must be 16-byte aligned");
+  if ((((uintptr_t)out->quats) & 15u) || (((uintptr_t)out->shs) & 15u))
+    return fail(GES_ERR_INVALID_ARG, "gradient quats and shs must be 16-byte aligned");
   if ((st = use_device(f->ctx->device)) != GES_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   ViewDesc& v = f->vt.v[0];

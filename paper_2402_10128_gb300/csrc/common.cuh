@@ -2,6 +2,7 @@
 // projected-primitive record, and the fixed-order FP32 arithmetic of the key path.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -83,7 +84,8 @@ struct Params {
 // Projected primitive as the compositing kernels read it (48 bytes, gathered by id).
 //   a = (mean x, mean y, q limit, beta exponent hb)    hb = beta/2 (GEF) or 1
 //   b = (conic a, conic b, conic c, opacity)            q = a dx^2 + 2 b dx dy + c dy^2
-//   c = (r, g, b, 0)
+//   c = (r, g, b, extent)   extent = two fp16 half-widths (x, y) of the primitive's screen box,
+//                           rounded up, packed in the 32 bits of c.w
 struct __align__(16) Rec {
   float4 a, b, c;
 };
@@ -107,9 +109,25 @@ __device__ __forceinline__ float mufu_lg2(float x) {
 constexpr float kNegHalfLog2e = -0.72134752044448170f;  // -1/2 log2(e): exp(-p/2) = 2^(kNegHalfLog2e p)
 
 struct FragEval {
-  float dx, dy, q, p, G, alpha;
+  float dx, dy, q, p, G, alpha, lq;  // lq = log2 q (GEF exponent path only)
   bool in_range, clamped;
 };
+
+__device__ __forceinline__ float pack_extent(float hx, float hy) {
+  __half2 h = __halves2half2(__float2half_ru(hx), __float2half_ru(hy));
+  return *reinterpret_cast<float*>(&h);
+}
+__device__ __forceinline__ float2 unpack_extent(float w) {
+  __half2 h = *reinterpret_cast<__half2*>(&w);
+  return __half22float2(h);
+}
+
+// Does the primitive's screen box meet the block of pixel centres [x0,x1] x [y0,y1]?  Pixels
+// outside the box have q above the q limit, so skipping the block changes nothing.
+__device__ __forceinline__ bool box_meets_block(const Rec& r, float x0, float x1, float y0, float y1) {
+  const float2 h = unpack_extent(r.c.w);
+  return r.a.x + h.x >= x0 && r.a.x - h.x <= x1 && r.a.y + h.y >= y0 && r.a.y - h.y <= y1;
+}
 
 // q = d^T conic d with d = pixel - mean; p = q^hb; G = exp(-p/2); alpha = min(alpha_max, kappa G)
 __device__ __forceinline__ void eval_fragment(const Rec& r, float px, float py, float alpha_max, FragEval& f) {
@@ -121,14 +139,16 @@ __device__ __forceinline__ void eval_fragment(const Rec& r, float px, float py, 
   f.q = fmaxf(f.q, 0.0f);
   f.in_range = f.q <= r.a.z;  // beyond the extent alpha < alpha_min; decided without the MUFU work
   if (!f.in_range) {
-    f.p = f.G = f.alpha = 0.0f;
+    f.p = f.G = f.alpha = f.lq = 0.0f;
     f.clamped = false;
     return;
   }
   if (r.a.w == 1.0f) {
     f.p = f.q;
+    f.lq = 0.f;
   } else {
-    f.p = mufu_ex2(__fmul_rn(r.a.w, mufu_lg2(f.q)));
+    f.lq = mufu_lg2(f.q);
+    f.p = mufu_ex2(__fmul_rn(r.a.w, f.lq));
   }
   f.G = mufu_ex2(__fmul_rn(kNegHalfLog2e, f.p));
   float a = __fmul_rn(r.b.w, f.G);

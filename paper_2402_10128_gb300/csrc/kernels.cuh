@@ -11,7 +11,7 @@ void count_launches(int n);
 // ---- per-primitive kernels (preprocess.cu)
 template <int MAXV>
 void launch_preprocess(const ViewTable<MAXV>& vt, int64_t total, const Params& P, uint32_t* depth_key,
-                       uint32_t* sort_vals, ushort4* rect, Rec* rec, int num_sms, cudaStream_t s);
+                       uint32_t* sort_keys, uint32_t* sort_vals, ushort4* rect, Rec* rec, int num_sms, cudaStream_t s);
 template <int MAXV>
 void launch_preprocess_bwd(const ViewTable<MAXV>& vt, int64_t total, const Params& P, const uint32_t* depth_key,
                            const float4* g2d, int num_sms, cudaStream_t s);

@@ -16,15 +16,16 @@ namespace ges {
 
 namespace {
 
-// Real SH basis up to degree 3 at unit direction (x,y,z); returns (deg+1)^2 values.
-__device__ __forceinline__ void sh_eval(int deg, float x, float y, float z, float* Y) {
+// Real SH basis of degree <= DEG at unit direction (x,y,z): Y[0..(DEG+1)^2).
+template <int DEG>
+__device__ __forceinline__ void sh_eval(float x, float y, float z, float* Y) {
   Y[0] = (float)sh_norm(0, 0);
-  if (deg < 1) return;
+  if (DEG < 1) return;
   const float n11 = (float)sh_norm(1, 1), n10 = (float)sh_norm(1, 0);
   Y[1] = -n11 * y;
   Y[2] = n10 * z;
   Y[3] = -n11 * x;
-  if (deg < 2) return;
+  if (DEG < 2) return;
   const float n22 = (float)sh_norm(2, 2), n21 = (float)sh_norm(2, 1), n20 = (float)sh_norm(2, 0);
   const float xx = x * x, yy = y * y, zz = z * z;
   Y[4] = 6.0f * n22 * x * y;
@@ -32,7 +33,7 @@ __device__ __forceinline__ void sh_eval(int deg, float x, float y, float z, floa
   Y[6] = 0.5f * n20 * (3.0f * zz - 1.0f);
   Y[7] = -3.0f * n21 * x * z;
   Y[8] = 3.0f * n22 * (xx - yy);
-  if (deg < 3) return;
+  if (DEG < 3) return;
   const float n33 = (float)sh_norm(3, 3), n32 = (float)sh_norm(3, 2), n31 = (float)sh_norm(3, 1),
               n30 = (float)sh_norm(3, 0);
   Y[9] = -15.0f * n33 * y * (3.0f * xx - yy);
@@ -44,22 +45,23 @@ __device__ __forceinline__ void sh_eval(int deg, float x, float y, float z, floa
   Y[15] = -15.0f * n33 * x * (xx - 3.0f * yy);
 }
 
-// Gradient of each basis polynomial with respect to (x,y,z) (the radial part is removed later).
-__device__ __forceinline__ void sh_grad(int deg, float x, float y, float z, float3* dY) {
+// Gradient of each basis polynomial with respect to (x,y,z) (the radial part is removed by the caller).
+template <int DEG>
+__device__ __forceinline__ void sh_grad(float x, float y, float z, float3* dY) {
   dY[0] = make_float3(0.f, 0.f, 0.f);
-  if (deg < 1) return;
+  if (DEG < 1) return;
   const float n11 = (float)sh_norm(1, 1), n10 = (float)sh_norm(1, 0);
   dY[1] = make_float3(0.f, -n11, 0.f);
   dY[2] = make_float3(0.f, 0.f, n10);
   dY[3] = make_float3(-n11, 0.f, 0.f);
-  if (deg < 2) return;
+  if (DEG < 2) return;
   const float n22 = (float)sh_norm(2, 2), n21 = (float)sh_norm(2, 1), n20 = (float)sh_norm(2, 0);
   dY[4] = make_float3(6.0f * n22 * y, 6.0f * n22 * x, 0.f);
   dY[5] = make_float3(0.f, -3.0f * n21 * z, -3.0f * n21 * y);
   dY[6] = make_float3(0.f, 0.f, 3.0f * n20 * z);
   dY[7] = make_float3(-3.0f * n21 * z, 0.f, -3.0f * n21 * x);
   dY[8] = make_float3(6.0f * n22 * x, -6.0f * n22 * y, 0.f);
-  if (deg < 3) return;
+  if (DEG < 3) return;
   const float n33 = (float)sh_norm(3, 3), n32 = (float)sh_norm(3, 2), n31 = (float)sh_norm(3, 1),
               n30 = (float)sh_norm(3, 0);
   const float xx = x * x, yy = y * y, zz = z * z;
@@ -72,6 +74,91 @@ __device__ __forceinline__ void sh_grad(int deg, float x, float y, float z, floa
   dY[15] = make_float3(-45.0f * n33 * (xx - yy), 90.0f * n33 * x * y, 0.f);
 }
 
+// coefficients of one primitive: 3 (DEG+1)^2 floats; rows of 48 and 12 floats are 16-byte aligned
+template <int DEG>
+__device__ __forceinline__ void load_sh(const float* __restrict__ src, float* c) {
+  constexpr int kN = 3 * (DEG + 1) * (DEG + 1);
+  if constexpr (kN % 4 == 0) {
+#pragma unroll
+    for (int k = 0; k < kN / 4; ++k) {
+      const float4 v = reinterpret_cast<const float4*>(src)[k];
+      c[4 * k] = v.x; c[4 * k + 1] = v.y; c[4 * k + 2] = v.z; c[4 * k + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kN; ++k) c[k] = src[k];
+  }
+}
+
+template <int DEG>
+__device__ __forceinline__ void store_sh(float* __restrict__ dst, const float* c) {
+  constexpr int kN = 3 * (DEG + 1) * (DEG + 1);
+  if constexpr (kN % 4 == 0) {
+#pragma unroll
+    for (int k = 0; k < kN / 4; ++k)
+      reinterpret_cast<float4*>(dst)[k] = make_float4(c[4 * k], c[4 * k + 1], c[4 * k + 2], c[4 * k + 3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < kN; ++k) dst[k] = c[k];
+  }
+}
+
+// colour = max(0, sum_k c_k Y_k(dir) + 1/2) per channel
+template <int DEG>
+__device__ __forceinline__ float3 sh_colour(float dx, float dy, float dz, const float* __restrict__ sh) {
+  constexpr int kB = (DEG + 1) * (DEG + 1);
+  float c[3 * kB];
+  load_sh<DEG>(sh, c);
+  float Y[kB];
+  sh_eval<DEG>(dx, dy, dz, Y);
+  float r = 0.5f, g = 0.5f, b = 0.5f;
+#pragma unroll
+  for (int k = 0; k < kB; ++k) {
+    r = fmaf(Y[k], c[3 * k], r);
+    g = fmaf(Y[k], c[3 * k + 1], g);
+    b = fmaf(Y[k], c[3 * k + 2], b);
+  }
+  return make_float3(fmaxf(r, 0.f), fmaxf(g, 0.f), fmaxf(b, 0.f));
+}
+
+// backward of sh_colour: writes dL/dc (all coefficients) and returns dL/d(dir) (before the
+// projection onto the sphere's tangent plane)
+template <int DEG>
+__device__ __forceinline__ float3 sh_colour_bwd(float dx, float dy, float dz, const float* __restrict__ sh,
+                                                const float g_rgb[3], float* __restrict__ gsh) {
+  constexpr int kB = (DEG + 1) * (DEG + 1);
+  float c[3 * kB];
+  load_sh<DEG>(sh, c);
+  float Y[kB];
+  sh_eval<DEG>(dx, dy, dz, Y);
+  float raw[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+  for (int k = 0; k < kB; ++k) {
+    raw[0] = fmaf(Y[k], c[3 * k], raw[0]);
+    raw[1] = fmaf(Y[k], c[3 * k + 1], raw[1]);
+    raw[2] = fmaf(Y[k], c[3 * k + 2], raw[2]);
+  }
+  const float gr[3] = {raw[0] > 0.f ? g_rgb[0] : 0.f, raw[1] > 0.f ? g_rgb[1] : 0.f, raw[2] > 0.f ? g_rgb[2] : 0.f};
+  float out[3 * kB];
+  float3 gd = make_float3(0.f, 0.f, 0.f);
+  float3 dY[kB];
+  sh_grad<DEG>(dx, dy, dz, dY);
+#pragma unroll
+  for (int k = 0; k < kB; ++k) {
+    out[3 * k] = Y[k] * gr[0];
+    out[3 * k + 1] = Y[k] * gr[1];
+    out[3 * k + 2] = Y[k] * gr[2];
+    if (k > 0) {
+      const float gy = c[3 * k] * gr[0] + c[3 * k + 1] * gr[1] + c[3 * k + 2] * gr[2];
+      gd.x = fmaf(gy, dY[k].x, gd.x);
+      gd.y = fmaf(gy, dY[k].y, gd.y);
+      gd.z = fmaf(gy, dY[k].z, gd.z);
+    }
+  }
+  store_sh<DEG>(gsh, out);
+  return gd;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
@@ -80,6 +167,7 @@ __device__ __forceinline__ void sh_grad(int deg, float x, float y, float z, floa
 template <int MAXV>
 __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ ViewTable<MAXV> vt, int64_t total,
                                                     const Params P, uint32_t* __restrict__ depth_key,
+                                                    uint32_t* __restrict__ sort_keys,
                                                     uint32_t* __restrict__ sort_vals, ushort4* __restrict__ rect,
                                                     Rec* __restrict__ rec) {
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
@@ -197,7 +285,9 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ View
     int x0 = (int)fx0, x1 = (int)fx1, y0 = (int)fy0, y1 = (int)fy1;
     bool touched = valid && x1 > x0 && y1 > y0;
 
-    depth_key[g] = touched ? __float_as_uint(tz) : kCulledKey;
+    const uint32_t dkey = touched ? __float_as_uint(tz) : kCulledKey;
+    depth_key[g] = dkey;
+    sort_keys[g] = dkey;
     sort_vals[g] = (uint32_t)g;
     rect[g] = touched ? make_ushort4((unsigned short)x0, (unsigned short)y0, (unsigned short)x1, (unsigned short)y1)
                       : make_ushort4(0, 0, 0, 0);
@@ -206,21 +296,20 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ View
     // SH colour (ordinary FP32)
     float dvx = mx - vd.campos[0], dvy = my - vd.campos[1], dvz = mz - vd.campos[2];
     float dn = rsqrtf(dvx * dvx + dvy * dvy + dvz * dvz);
-    float Y[16];
-    sh_eval(vd.sh_degree, dvx * dn, dvy * dn, dvz * dn, Y);
     const int nb = (vd.sh_degree + 1) * (vd.sh_degree + 1);
     const float* sh = vd.shs + (int64_t)3 * nb * i;
-    float col[3] = {0.5f, 0.5f, 0.5f};
-    for (int k = 0; k < nb; ++k) {
-      col[0] += Y[k] * sh[3 * k + 0];
-      col[1] += Y[k] * sh[3 * k + 1];
-      col[2] += Y[k] * sh[3 * k + 2];
+    float3 col;
+    switch (vd.sh_degree) {
+      case 0: col = sh_colour<0>(dvx * dn, dvy * dn, dvz * dn, sh); break;
+      case 1: col = sh_colour<1>(dvx * dn, dvy * dn, dvz * dn, sh); break;
+      case 2: col = sh_colour<2>(dvx * dn, dvy * dn, dvz * dn, sh); break;
+      default: col = sh_colour<3>(dvx * dn, dvy * dn, dvz * dn, sh); break;
     }
     float idet = 1.0f / det;
     Rec r;
     r.a = make_float4(u, v, kmul(kmul(qs, onep), onep), P.mode == 0 ? 0.5f * beta : 1.0f);
     r.b = make_float4(cc * idet, -cb * idet, ca * idet, kappa);
-    r.c = make_float4(fmaxf(col[0], 0.f), fmaxf(col[1], 0.f), fmaxf(col[2], 0.f), 0.f);
+    r.c = make_float4(col.x, col.y, col.z, pack_extent(hx, hy));
     rec[g] = r;
   }
 }
@@ -369,34 +458,18 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(const __grid_constant__ 
     const float dvx = mu[0] - vd.campos[0], dvy = mu[1] - vd.campos[1], dvz = mu[2] - vd.campos[2];
     const float idn = rsqrtf(dvx * dvx + dvy * dvy + dvz * dvz);
     const float dx = dvx * idn, dy = dvy * idn, dz = dvz * idn;
-    float Y[16];
-    float3 dY[16];
-    sh_eval(vd.sh_degree, dx, dy, dz, Y);
     const float* sh = vd.shs + (int64_t)3 * nb * i;
-    float raw[3] = {0.5f, 0.5f, 0.5f};
-    for (int k = 0; k < nb; ++k) {
-      raw[0] += Y[k] * sh[3 * k];
-      raw[1] += Y[k] * sh[3 * k + 1];
-      raw[2] += Y[k] * sh[3 * k + 2];
+    float3 gd;
+    switch (vd.sh_degree) {
+      case 0: gd = sh_colour_bwd<0>(dx, dy, dz, sh, g_rgb, gsh); break;
+      case 1: gd = sh_colour_bwd<1>(dx, dy, dz, sh, g_rgb, gsh); break;
+      case 2: gd = sh_colour_bwd<2>(dx, dy, dz, sh, g_rgb, gsh); break;
+      default: gd = sh_colour_bwd<3>(dx, dy, dz, sh, g_rgb, gsh); break;
     }
-    const float graw[3] = {raw[0] > 0.f ? g_rgb[0] : 0.f, raw[1] > 0.f ? g_rgb[1] : 0.f, raw[2] > 0.f ? g_rgb[2] : 0.f};
-    float gd[3] = {0.f, 0.f, 0.f};
-    if (vd.sh_degree > 0) sh_grad(vd.sh_degree, dx, dy, dz, dY);
-    for (int k = 0; k < nb; ++k) {
-      gsh[3 * k] = Y[k] * graw[0];
-      gsh[3 * k + 1] = Y[k] * graw[1];
-      gsh[3 * k + 2] = Y[k] * graw[2];
-      if (k > 0) {
-        const float gy_k = sh[3 * k] * graw[0] + sh[3 * k + 1] * graw[1] + sh[3 * k + 2] * graw[2];
-        gd[0] += gy_k * dY[k].x;
-        gd[1] += gy_k * dY[k].y;
-        gd[2] += gy_k * dY[k].z;
-      }
-    }
-    const float dd = dx * gd[0] + dy * gd[1] + dz * gd[2];
-    gmu[0] += (gd[0] - dx * dd) * idn;
-    gmu[1] += (gd[1] - dy * dd) * idn;
-    gmu[2] += (gd[2] - dz * dd) * idn;
+    const float dd = dx * gd.x + dy * gd.y + dz * gd.z;
+    gmu[0] += (gd.x - dx * dd) * idn;
+    gmu[1] += (gd.y - dy * dd) * idn;
+    gmu[2] += (gd.z - dz * dd) * idn;
 
     for (int k = 0; k < 3; ++k) {
       vd.g_means[3 * i + k] = gmu[k];
@@ -420,9 +493,9 @@ static int grid_for(int64_t total, int num_sms) {
 
 template <int MAXV>
 void launch_preprocess(const ViewTable<MAXV>& vt, int64_t total, const Params& P, uint32_t* depth_key,
-                       uint32_t* sort_vals, ushort4* rect, Rec* rec, int num_sms, cudaStream_t s) {
+                       uint32_t* sort_keys, uint32_t* sort_vals, ushort4* rect, Rec* rec, int num_sms, cudaStream_t s) {
   if (total <= 0) return;
-  k_preprocess<MAXV><<<grid_for(total, num_sms), 256, 0, s>>>(vt, total, P, depth_key, sort_vals, rect, rec);
+  k_preprocess<MAXV><<<grid_for(total, num_sms), 256, 0, s>>>(vt, total, P, depth_key, sort_keys, sort_vals, rect, rec);
   count_launches(1);
 }
 
@@ -446,10 +519,10 @@ void set_key_constants(cudaStream_t s) {
   cudaMemcpyToSymbolAsync(c_exp2_coef, c, sizeof(c), 0, cudaMemcpyHostToDevice, s);
 }
 
-template void launch_preprocess<1>(const ViewTable<1>&, int64_t, const Params&, uint32_t*, uint32_t*, ushort4*, Rec*,
-                                   int, cudaStream_t);
+template void launch_preprocess<1>(const ViewTable<1>&, int64_t, const Params&, uint32_t*, uint32_t*, uint32_t*,
+                                   ushort4*, Rec*, int, cudaStream_t);
 template void launch_preprocess<kServeMaxViews>(const ViewTable<kServeMaxViews>&, int64_t, const Params&, uint32_t*,
-                                                uint32_t*, ushort4*, Rec*, int, cudaStream_t);
+                                                uint32_t*, uint32_t*, ushort4*, Rec*, int, cudaStream_t);
 template void launch_preprocess_bwd<1>(const ViewTable<1>&, int64_t, const Params&, const uint32_t*, const float4*, int,
                                        cudaStream_t);
 template void launch_preprocess_bwd<kServeMaxViews>(const ViewTable<kServeMaxViews>&, int64_t, const Params&,

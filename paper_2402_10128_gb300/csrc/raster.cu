@@ -4,9 +4,13 @@
 //   C = sum_i c_i alpha_i T_i + T_final bg,   T_i = prod_{j<i} (1 - alpha_j),
 // with alpha_i = min(alpha_max, kappa_i G_i) and the GES falloff G = exp(-1/2 q^(beta/2))
 // (Sec. 3.1, Eq. ges) or the paper's Gaussian-form rasterizer G = exp(-1/2 q).
-// One CTA per 16x16 tile, 256 threads, one pixel per thread.  A warp covers an 8x4 pixel
-// block (spatially compact, so a primitive tends to be in or out for the whole warp).
-// The tile's list is staged in shared memory 256 records at a time.
+//
+// One CTA of 128 threads per 16x16 tile; each thread owns two pixels, (x, y) and (x, y + 4),
+// so a warp covers an 8x8 block.  The tile's list is staged in shared memory 128 records at a
+// time.  Before any per-pixel work a warp tests the record's screen box against its 8x8 block
+// and skips the fragment for all 64 pixels when they do not meet (pixels outside the box are
+// beyond the primitive's extent).  Forward and backward share this mapping and the arithmetic
+// of eval_fragment, so they take the same skip / clamp / stop decisions bit for bit.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -14,71 +18,98 @@ namespace ges {
 
 namespace {
 
-constexpr int kBatch = 256;
+constexpr int kThreads = 128;  // per tile
+constexpr int kBatch = kThreads;
 
-__device__ __forceinline__ void pixel_of(int lt, int tiles_x, int& x, int& y) {
+struct WarpBlock {
+  int x, y;                    // first pixel of this thread
+  float bx0, bx1, by0, by1;    // pixel-centre bounds of the warp's 8x8 block
+};
+
+__device__ __forceinline__ WarpBlock warp_block(int lt, int tiles_x) {
   const int tx = lt % tiles_x, ty = lt / tiles_x;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  x = tx * kTile + (w & 1) * 8 + (lane & 7);
-  y = ty * kTile + (w >> 1) * 4 + (lane >> 3);
+  WarpBlock b;
+  const int ox = tx * kTile + (w & 1) * 8, oy = ty * kTile + (w >> 1) * 8;
+  b.x = ox + (lane & 7);
+  b.y = oy + (lane >> 3);
+  b.bx0 = (float)ox + 0.5f;
+  b.bx1 = (float)ox + 7.5f;
+  b.by0 = (float)oy + 0.5f;
+  b.by1 = (float)oy + 7.5f;
+  return b;
 }
 
 template <int MAXV, bool STATS>
-__global__ void __launch_bounds__(kBatch) k_render_fwd(const __grid_constant__ ViewTable<MAXV> vt,
-                                                       const uint2* __restrict__ ranges,
-                                                       const uint32_t* __restrict__ vals, const Rec* __restrict__ rec,
-                                                       const Params P, unsigned long long* __restrict__ stats) {
+__global__ void __launch_bounds__(kThreads) k_render_fwd(const __grid_constant__ ViewTable<MAXV> vt,
+                                                         const uint2* __restrict__ ranges,
+                                                         const uint32_t* __restrict__ vals, const Rec* __restrict__ rec,
+                                                         const Params P, unsigned long long* __restrict__ stats) {
   __shared__ Rec batch[kBatch];
   const int64_t tile = blockIdx.x;
   const ViewDesc& vd = vt.v[view_of_tile(vt, tile)];
-  int x, y;
-  pixel_of((int)(tile - vd.tile_base), vd.tiles_x, x, y);
-  const bool inside = x < vd.W && y < vd.H;
-  const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+  const WarpBlock wb = warp_block((int)(tile - vd.tile_base), vd.tiles_x);
   const uint2 rg = ranges[tile];
 
-  float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-  uint32_t last = 0;
+  float px[2], py[2], T[2], C0[2], C1[2], C2[2];
+  uint32_t last[2];
+  bool inside[2], done[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int y = wb.y + 4 * k;
+    inside[k] = wb.x < vd.W && y < vd.H;
+    done[k] = !inside[k];
+    px[k] = (float)wb.x + 0.5f;
+    py[k] = (float)y + 0.5f;
+    T[k] = 1.0f;
+    C0[k] = C1[k] = C2[k] = 0.f;
+    last[k] = 0;
+  }
   uint32_t n_eval = 0, n_range = 0;
-  bool done = !inside;
   for (uint32_t base = rg.x; base < rg.y; base += kBatch) {
-    if (__syncthreads_count(done) == kBatch) break;
+    if (__syncthreads_count(done[0] && done[1]) == kThreads) break;
     const uint32_t idx = base + threadIdx.x;
     if (idx < rg.y) batch[threadIdx.x] = rec[vals[idx]];
     __syncthreads();
     const int cnt = (int)min((uint32_t)kBatch, rg.y - base);
-    if (!__all_sync(0xffffffffu, done)) {
-      for (int j = 0; j < cnt; ++j) {
-        if (done) break;
-        const Rec r = batch[j];
+    for (int j = 0; j < cnt; ++j) {
+      if (__all_sync(0xffffffffu, done[0] && done[1])) break;
+      const Rec r = batch[j];
+      if (!box_meets_block(r, wb.bx0, wb.bx1, wb.by0, wb.by1)) continue;  // warp-uniform
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        if (done[k]) continue;
         FragEval f;
-        eval_fragment(r, px, py, P.alpha_max, f);
+        eval_fragment(r, px[k], py[k], P.alpha_max, f);
         if (STATS) {
           ++n_eval;
           n_range += f.in_range ? 1u : 0u;
         }
         if (f.alpha < P.alpha_min) continue;
-        const float Tn = T * (1.0f - f.alpha);
+        const float Tn = T[k] * (1.0f - f.alpha);
         if (Tn < P.t_min) {
-          done = true;
-          break;
+          done[k] = true;
+          continue;
         }
-        const float w = f.alpha * T;
-        C0 = fmaf(r.c.x, w, C0);
-        C1 = fmaf(r.c.y, w, C1);
-        C2 = fmaf(r.c.z, w, C2);
-        T = Tn;
-        last = base - rg.x + (uint32_t)j + 1u;
+        const float w = f.alpha * T[k];
+        C0[k] = fmaf(r.c.x, w, C0[k]);
+        C1[k] = fmaf(r.c.y, w, C1[k]);
+        C2[k] = fmaf(r.c.z, w, C2[k]);
+        T[k] = Tn;
+        last[k] = base - rg.x + (uint32_t)j + 1u;
       }
     }
   }
-  if (inside) {
-    const int64_t pix = (int64_t)y * vd.W + x, plane = (int64_t)vd.W * vd.H;
-    vd.img[pix] = C0 + T * vd.bg[0];
-    vd.img[plane + pix] = C1 + T * vd.bg[1];
-    vd.img[2 * plane + pix] = C2 + T * vd.bg[2];
-    vd.final_T[pix] = T;
-    vd.n_contrib[pix] = last;
+  const int64_t plane = (int64_t)vd.W * vd.H;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    if (!inside[k]) continue;
+    const int64_t pix = (int64_t)(wb.y + 4 * k) * vd.W + wb.x;
+    vd.img[pix] = C0[k] + T[k] * vd.bg[0];
+    vd.img[plane + pix] = C1[k] + T[k] * vd.bg[1];
+    vd.img[2 * plane + pix] = C2[k] + T[k] * vd.bg[2];
+    vd.final_T[pix] = T[k];
+    vd.n_contrib[pix] = last[k];
   }
   if (STATS) {
     unsigned long long a = n_eval, b = n_range;
@@ -94,10 +125,24 @@ __global__ void __launch_bounds__(kBatch) k_render_fwd(const __grid_constant__ V
   }
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Sums 16 per-lane values over the warp with a reduce-scatter butterfly (16 shuffles instead of
+// 16 x 5): at each step a lane keeps half of its values and receives the partner's copy of that
+// half.  On return lane L holds the full sum of value ((L >> 1) & 15) (L and L^1 hold the same).
+__device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16]) {
+  const unsigned lane = threadIdx.x & 31u;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+  for (int step = 0; step < 4; ++step) {
+    const int half = 8 >> step;          // values kept after this step
+    const int o = 16 >> step;            // partner distance
+    const bool upper = (lane & (unsigned)o) != 0;
+#pragma unroll
+    for (int k = 0; k < half; ++k) {
+      const float send = upper ? v[k] : v[k + half];
+      const float keep = upper ? v[k + half] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
 // Backward.  Per pixel, walks its contributors back to front, recovering T_i = T_{i+1}/(1-alpha_i)
@@ -106,41 +151,53 @@ __device__ __forceinline__ float warp_sum(float v) {
 //   dalpha/dkappa = G, dalpha/dG = kappa (0 where alpha is clamped)
 //   dG/dp = -G/2,  p = q^hb:  dp/dq = hb p / q,  dp/dhb = p ln q  (0 for q < 1e-12)
 //   q = a dx^2 + 2 b dx dy + c dy^2, dx = px - mx
-// Per-pixel terms are summed over the warp by shuffles, then one vector atomic per field group.
+// A thread sums its two pixels' terms, the warp sums by a reduce-scatter butterfly, and ten lanes
+// add the ten per-primitive sums with one atomic each.
 template <int MAXV>
-__global__ void __launch_bounds__(kBatch) k_render_bwd(const __grid_constant__ ViewTable<MAXV> vt,
-                                                       const uint2* __restrict__ ranges,
-                                                       const uint32_t* __restrict__ vals, const Rec* __restrict__ rec,
-                                                       const Params P, float4* __restrict__ g2d) {
+__global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__ ViewTable<MAXV> vt,
+                                                         const uint2* __restrict__ ranges,
+                                                         const uint32_t* __restrict__ vals, const Rec* __restrict__ rec,
+                                                         const Params P, float4* __restrict__ g2d) {
   __shared__ Rec batch[kBatch];
   __shared__ uint32_t ids[kBatch];
   __shared__ uint32_t s_max_last;
   const int64_t tile = blockIdx.x;
   const ViewDesc& vd = vt.v[view_of_tile(vt, tile)];
-  int x, y;
-  pixel_of((int)(tile - vd.tile_base), vd.tiles_x, x, y);
-  const bool inside = x < vd.W && y < vd.H;
-  const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+  const WarpBlock wb = warp_block((int)(tile - vd.tile_base), vd.tiles_x);
   const uint2 rg = ranges[tile];
-  const int64_t pix = (int64_t)y * vd.W + x, plane = (int64_t)vd.W * vd.H;
+  const int64_t plane = (int64_t)vd.W * vd.H;
 
-  float T = 0.f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f;
-  uint32_t last = 0;
-  if (inside) {
-    T = vd.final_T[pix];
-    last = vd.n_contrib[pix];
-    gC0 = vd.dL_dimg[pix];
-    gC1 = vd.dL_dimg[plane + pix];
-    gC2 = vd.dL_dimg[2 * plane + pix];
+  float px[2], py[2], T[2], gC0[2], gC1[2], gC2[2], S0[2], S1[2], S2[2];
+  uint32_t last[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int y = wb.y + 4 * k;
+    const bool inside = wb.x < vd.W && y < vd.H;
+    px[k] = (float)wb.x + 0.5f;
+    py[k] = (float)y + 0.5f;
+    T[k] = 0.f; gC0[k] = gC1[k] = gC2[k] = 0.f;
+    last[k] = 0;
+    if (inside) {
+      const int64_t pix = (int64_t)y * vd.W + wb.x;
+      T[k] = vd.final_T[pix];
+      last[k] = vd.n_contrib[pix];
+      gC0[k] = vd.dL_dimg[pix];
+      gC1[k] = vd.dL_dimg[plane + pix];
+      gC2[k] = vd.dL_dimg[2 * plane + pix];
+    }
+    S0[k] = T[k] * vd.bg[0];
+    S1[k] = T[k] * vd.bg[1];
+    S2[k] = T[k] * vd.bg[2];
   }
-  float S0 = T * vd.bg[0], S1 = T * vd.bg[1], S2 = T * vd.bg[2];
   if (threadIdx.x == 0) s_max_last = 0;
   __syncthreads();
-  atomicMax(&s_max_last, last);
+  atomicMax(&s_max_last, max(last[0], last[1]));
   __syncthreads();
   const uint32_t max_last = s_max_last;
+  const uint32_t wlast = __reduce_max_sync(0xffffffffu, max(last[0], last[1]));
   const bool gef = P.mode == 0;
   const float ln2 = 0.69314718055994531f;
+  const unsigned lane = threadIdx.x & 31u;
 
   for (uint32_t end = rg.x + max_last; end > rg.x;) {
     const uint32_t start = (end - rg.x > (uint32_t)kBatch) ? end - kBatch : rg.x;
@@ -153,57 +210,62 @@ __global__ void __launch_bounds__(kBatch) k_render_bwd(const __grid_constant__ V
     }
     __syncthreads();
     for (int j = (int)(end - start) - 1; j >= 0; --j) {
-      const uint32_t k = start - rg.x + (uint32_t)j + 1u;  // 1-based position in the tile's list
-      float g[10];
+      const uint32_t kpos = start - rg.x + (uint32_t)j + 1u;  // 1-based position in the tile's list
+      if (kpos > wlast) continue;                             // beyond every pixel of this warp
+      const Rec r = batch[j];
+      if (!box_meets_block(r, wb.bx0, wb.bx1, wb.by0, wb.by1)) continue;  // warp-uniform
+      float g[16];
 #pragma unroll
-      for (int t = 0; t < 10; ++t) g[t] = 0.f;
+      for (int t = 0; t < 16; ++t) g[t] = 0.f;
       bool contrib = false;
-      if (k <= last) {
-        const Rec r = batch[j];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        if (kpos > last[k]) continue;
         FragEval f;
-        eval_fragment(r, px, py, P.alpha_max, f);
-        if (f.alpha >= P.alpha_min) {
-          contrib = true;
-          const float oma = 1.0f - f.alpha;
-          T = T / oma;
-          const float w = f.alpha * T;
-          const float dLda = gC0 * (r.c.x * T - S0 / oma) + gC1 * (r.c.y * T - S1 / oma) + gC2 * (r.c.z * T - S2 / oma);
-          S0 = fmaf(r.c.x, w, S0);
-          S1 = fmaf(r.c.y, w, S1);
-          S2 = fmaf(r.c.z, w, S2);
-          g[7] = gC0 * w;
-          g[8] = gC1 * w;
-          g[9] = gC2 * w;
-          const float dG = f.clamped ? 0.f : dLda * r.b.w;
-          g[5] = f.clamped ? 0.f : dLda * f.G;
-          const float dp = dG * (-0.5f * f.G);
-          float dq;
-          if (gef) {
-            if (f.q > 1e-12f) {
-              dq = dp * r.a.w * f.p / f.q;
-              g[6] = dp * f.p * (mufu_lg2(f.q) * ln2);
+        eval_fragment(r, px[k], py[k], P.alpha_max, f);
+        if (f.alpha < P.alpha_min) continue;
+        contrib = true;
+        const float inv = __frcp_rn(1.0f - f.alpha);
+        T[k] *= inv;
+        const float w = f.alpha * T[k];
+        const float dLda = gC0[k] * (r.c.x * T[k] - S0[k] * inv) + gC1[k] * (r.c.y * T[k] - S1[k] * inv) +
+                           gC2[k] * (r.c.z * T[k] - S2[k] * inv);
+        S0[k] = fmaf(r.c.x, w, S0[k]);
+        S1[k] = fmaf(r.c.y, w, S1[k]);
+        S2[k] = fmaf(r.c.z, w, S2[k]);
+        g[7] += gC0[k] * w;
+        g[8] += gC1[k] * w;
+        g[9] += gC2[k] * w;
+        const float dG = f.clamped ? 0.f : dLda * r.b.w;
+        g[5] += f.clamped ? 0.f : dLda * f.G;
+        const float dp = dG * (-0.5f * f.G);
+        float dq;
+        if (gef) {
+          if (f.q > 1e-12f) {
+            if (r.a.w == 1.0f) {
+              dq = dp;
+              g[6] += dp * f.q * (mufu_lg2(f.q) * ln2);
             } else {
-              dq = 0.f;
+              dq = dp * r.a.w * f.p * __frcp_rn(f.q);
+              g[6] += dp * f.p * (f.lq * ln2);
             }
           } else {
-            dq = dp;
+            dq = 0.f;
           }
-          g[0] = dq * (-2.f) * (r.b.x * f.dx + r.b.y * f.dy);
-          g[1] = dq * (-2.f) * (r.b.y * f.dx + r.b.z * f.dy);
-          g[2] = dq * f.dx * f.dx;
-          g[3] = dq * 2.f * f.dx * f.dy;
-          g[4] = dq * f.dy * f.dy;
+        } else {
+          dq = dp;
         }
+        const float dqdx = dq * f.dx, dqdy = dq * f.dy;
+        g[0] -= 2.f * (r.b.x * dqdx + r.b.y * dqdy);
+        g[1] -= 2.f * (r.b.y * dqdx + r.b.z * dqdy);
+        g[2] += dqdx * f.dx;
+        g[3] += 2.f * dqdx * f.dy;
+        g[4] += dqdy * f.dy;
       }
       if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-        for (int t = 0; t < 10; ++t) g[t] = warp_sum(g[t]);
-        if ((threadIdx.x & 31) == 0) {
-          float4* dst = g2d + 3 * (int64_t)ids[j];
-          atomicAdd(dst + 0, make_float4(g[0], g[1], g[2], g[3]));
-          atomicAdd(dst + 1, make_float4(g[4], g[5], g[6], g[7]));
-          atomicAdd(reinterpret_cast<float2*>(dst + 2), make_float2(g[8], g[9]));
-        }
+        const float sum = warp_reduce_scatter16(g);
+        const unsigned slot = (lane >> 1) & 15u;
+        if ((lane & 1u) == 0 && slot < 10u) atomicAdd(reinterpret_cast<float*>(g2d + 3 * (int64_t)ids[j]) + slot, sum);
       }
     }
     end = start;
@@ -217,9 +279,9 @@ void launch_render_fwd(const ViewTable<MAXV>& vt, int64_t total_tiles, const uin
                        const Rec* rec, const Params& P, cudaStream_t s, unsigned long long* stats) {
   if (total_tiles <= 0) return;
   if (stats)
-    k_render_fwd<MAXV, true><<<(unsigned)total_tiles, kBatch, 0, s>>>(vt, ranges, vals, rec, P, stats);
+    k_render_fwd<MAXV, true><<<(unsigned)total_tiles, kThreads, 0, s>>>(vt, ranges, vals, rec, P, stats);
   else
-    k_render_fwd<MAXV, false><<<(unsigned)total_tiles, kBatch, 0, s>>>(vt, ranges, vals, rec, P, nullptr);
+    k_render_fwd<MAXV, false><<<(unsigned)total_tiles, kThreads, 0, s>>>(vt, ranges, vals, rec, P, nullptr);
   count_launches(1);
 }
 
@@ -227,7 +289,7 @@ template <int MAXV>
 void launch_render_bwd(const ViewTable<MAXV>& vt, int64_t total_tiles, const uint2* ranges, const uint32_t* vals,
                        const Rec* rec, const Params& P, float4* g2d, cudaStream_t s) {
   if (total_tiles <= 0) return;
-  k_render_bwd<MAXV><<<(unsigned)total_tiles, kBatch, 0, s>>>(vt, ranges, vals, rec, P, g2d);
+  k_render_bwd<MAXV><<<(unsigned)total_tiles, kThreads, 0, s>>>(vt, ranges, vals, rec, P, g2d);
   count_launches(1);
 }
 

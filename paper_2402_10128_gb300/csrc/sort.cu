@@ -101,27 +101,47 @@ __global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restr
                                                          const unsigned long long* __restrict__ n_dev, int64_t cap,
                                                          int shift, int bits,
                                                          uint32_t* __restrict__ hist, int64_t nchunks) {
-  __shared__ uint32_t cnt[256];
+  constexpr int kWarps = kThreads / 32;
+  __shared__ uint32_t cnt[kWarps][256];  // one private histogram per warp: less atomic contention
   const int nbins = 1 << bits;
-  for (int b = threadIdx.x; b < nbins; b += kThreads) cnt[b] = 0;
+  for (int i = threadIdx.x; i < kWarps * 256; i += kThreads) (&cnt[0][0])[i] = 0;
   __syncthreads();
   const int64_t n = element_count(n_host, n_dev, cap);
   const int64_t base = (int64_t)blockIdx.x * kChunk;
   const uint32_t mask = (uint32_t)nbins - 1u;
+  const int w = threadIdx.x >> 5;
   if (base < n) {
-#pragma unroll 4
-    for (int k = 0; k < kItems; ++k) {
-      int64_t idx = base + (int64_t)k * kThreads + threadIdx.x;
-      if (idx < n) atomicAdd(&cnt[(keys[idx] >> shift) & mask], 1u);
+    if (base + kChunk <= n) {
+      const uint4* k4 = reinterpret_cast<const uint4*>(keys + base);
+#pragma unroll
+      for (int k = 0; k < kItems / 4; ++k) {
+        const uint4 v = k4[k * kThreads + threadIdx.x];
+        atomicAdd(&cnt[w][(v.x >> shift) & mask], 1u);
+        atomicAdd(&cnt[w][(v.y >> shift) & mask], 1u);
+        atomicAdd(&cnt[w][(v.z >> shift) & mask], 1u);
+        atomicAdd(&cnt[w][(v.w >> shift) & mask], 1u);
+      }
+    } else {
+      for (int k = 0; k < kItems; ++k) {
+        int64_t idx = base + (int64_t)k * kThreads + threadIdx.x;
+        if (idx < n) atomicAdd(&cnt[w][(keys[idx] >> shift) & mask], 1u);
+      }
     }
   }
   __syncthreads();
-  for (int b = threadIdx.x; b < nbins; b += kThreads) hist[(int64_t)b * nchunks + blockIdx.x] = cnt[b];
+  for (int b = threadIdx.x; b < nbins; b += kThreads) {
+    uint32_t t = 0;
+#pragma unroll
+    for (int ww = 0; ww < kWarps; ++ww) t += cnt[ww][b];
+    hist[(int64_t)b * nchunks + blockIdx.x] = t;
+  }
 }
 
 // Stable scatter.  Warp w of the CTA owns chunk elements [w*512, (w+1)*512) and walks them in
-// order, 32 at a time; lanes with equal digits are ranked by lane order (match.any), so the
-// final position preserves input order within each digit.
+// order, 32 at a time; lanes with equal digits are ranked by lane order (match.any), so ranks
+// preserve input order within each digit.  The chunk is first reordered by digit in shared
+// memory, then written out so that consecutive threads store consecutive positions of one
+// digit's run (coalesced).
 __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __restrict__ keys_in,
                                                             const uint32_t* __restrict__ vals_in,
                                                             uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
@@ -132,11 +152,16 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
   constexpr int kWarps = kThreads / 32;
   __shared__ uint32_t wcnt[kWarps][257];
   __shared__ uint32_t goff[256];
+  __shared__ uint32_t bstart[257];
+  __shared__ uint32_t wsum[kWarps];
+  __shared__ uint32_t skeys[kChunk];
+  __shared__ uint32_t svals[kChunk];
   const int nbins = 1 << bits;
   const uint32_t mask = (uint32_t)nbins - 1u;
   const int64_t n = element_count(n_host, n_dev, cap);
   const int64_t base = (int64_t)blockIdx.x * kChunk;
   if (base >= n) return;  // uniform across the CTA
+  const int count = (int)min((int64_t)kChunk, n - base);
   const int w = threadIdx.x >> 5;
   const unsigned lane = lane_id();
   for (int i = threadIdx.x; i < kWarps * 257; i += kThreads) (&wcnt[0][0])[i] = 0;
@@ -144,15 +169,13 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
   __syncthreads();
   const unsigned lt_mask = (1u << lane) - 1u;
   uint32_t key[kItems], val[kItems], rank[kItems];
-  int dig[kItems];
 #pragma unroll
   for (int r = 0; r < kItems; ++r) {
-    const int64_t idx = base + (int64_t)w * (kItems * 32) + r * 32 + lane;
-    const bool ok = idx < n;
-    key[r] = ok ? keys_in[idx] : 0u;
-    val[r] = ok ? vals_in[idx] : 0u;
+    const int li = w * (kItems * 32) + r * 32 + (int)lane;
+    const bool ok = li < count;
+    key[r] = ok ? keys_in[base + li] : 0u;
+    val[r] = ok ? vals_in[base + li] : 0u;
     const int d = ok ? (int)((key[r] >> shift) & mask) : 256;
-    dig[r] = d;
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     const uint32_t prev = wcnt[w][d];
     __syncwarp();
@@ -161,25 +184,55 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
     rank[r] = prev + (uint32_t)__popc(peers & lt_mask);
   }
   __syncthreads();
-  // exclusive prefix over warps, per digit
-  for (int b = threadIdx.x; b < nbins; b += kThreads) {
-    uint32_t run = 0;
+  // per digit: exclusive prefix over warps, and the digit's total in the chunk
+  uint32_t total = 0;
+  if ((int)threadIdx.x < nbins) {
+    const int b = threadIdx.x;
 #pragma unroll
     for (int ww = 0; ww < kWarps; ++ww) {
       uint32_t c = wcnt[ww][b];
-      wcnt[ww][b] = run;
+      wcnt[ww][b] = total;
+      total += c;
+    }
+  }
+  // exclusive scan of the digit totals over the CTA (thread b holds digit b)
+  uint32_t inc = total;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if ((int)lane >= o) inc += y;
+  }
+  if (lane == 31) wsum[w] = inc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int ww = 0; ww < kWarps; ++ww) {
+      uint32_t c = wsum[ww];
+      wsum[ww] = run;
       run += c;
     }
   }
   __syncthreads();
+  if ((int)threadIdx.x < nbins) bstart[threadIdx.x] = wsum[w] + inc - total;
+  __syncthreads();
+  // reorder the chunk by digit in shared memory
 #pragma unroll
   for (int r = 0; r < kItems; ++r) {
-    const int d = dig[r];
-    if (d < 256) {
-      const uint32_t pos = goff[d] + wcnt[w][d] + rank[r];
-      keys_out[pos] = key[r];
-      vals_out[pos] = val[r];
+    const int li = w * (kItems * 32) + r * 32 + (int)lane;
+    if (li < count) {
+      const int d = (int)((key[r] >> shift) & mask);
+      const uint32_t pos = bstart[d] + wcnt[w][d] + rank[r];
+      skeys[pos] = key[r];
+      svals[pos] = val[r];
     }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < count; i += kThreads) {
+    const uint32_t k = skeys[i];
+    const int d = (int)((k >> shift) & mask);
+    const uint32_t gpos = goff[d] + ((uint32_t)i - bstart[d]);
+    keys_out[gpos] = k;
+    vals_out[gpos] = svals[i];
   }
 }
 
