@@ -187,6 +187,27 @@ ges_status ges_frame_count_work(ges_frame* frame, void* stream, int64_t* evaluat
 /* Number of CUDA kernels this process has launched through libges (all threads). */
 uint64_t ges_kernel_launches(void);
 
+/* Forward render that allocates no device memory (no counterpart in the paper; it exists for
+   callers that cannot allocate).  Some callers cannot call cudaMalloc: code running under another
+   runtime's memory manager that has already reserved the device's memory for its own pool, or
+   latency-critical loops where cudaMalloc/cudaFree are ruled out because they may synchronise the
+   device.  This call computes what ges_preprocess + ges_bin_sort + ges_render_fwd compute, in the
+   same kernels, for scenes of at most 65,536 primitives, images of at most 16,384 tiles (16x16
+   pixels each, e.g. 2048x2048) and at most 1,048,576 (tile, primitive) duplicates.
+   Arguments: scene (device arrays, as for ges_preprocess), cam, params; outputs img [3,H,W],
+   final_T [H,W], n_contrib [H,W] (device, caller-owned); stream as everywhere.
+   Errors: GES_ERR_INVALID_ARG for a NULL pointer or a scene/image above the limits (nothing
+   enqueued); GES_ERR_CAPACITY when the duplicates exceed their limit (outputs then hold the
+   background only).  The call synchronises `stream` before returning, to read that count.
+   Every intermediate buffer lives in one fixed array of about 23 MB in device global memory,
+   which each GPU that loads the library holds until the process exits.  All calls share that
+   array and it keeps the last call's contents: calls whose work overlaps on the GPU (other
+   streams, other host threads on the same device) race on it and must be serialised by the
+   caller.  The first call on each device resolves the array's address and uploads constants;
+   make that first call before any stream capture on that device. */
+ges_status ges_render_fwd_noalloc(const ges_scene* scene, const ges_camera* cam, const ges_params* params,
+                                  float* img, float* final_T, uint32_t* n_contrib, void* stream);
+
 /* ---------------------------------------------------------------------------------------
  * Serving: several scenes resident on the device, render requests of mixed resolutions
  * admitted by memory and batched into shared launches (continuous batching).

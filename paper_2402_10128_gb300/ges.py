@@ -37,7 +37,7 @@ GES_FALLOFF_PAPER_APPROX = 1
 EXPORTED = ["ges_last_error", "ges_params_default", "ges_ctx_create", "ges_ctx_destroy", "ges_frame_create",
             "ges_frame_destroy", "ges_preprocess", "ges_bin_sort", "ges_render_fwd", "ges_render_bwd",
             "ges_frame_status", "ges_frame_keys", "ges_frame_inspect", "ges_frame_count_work",
-            "ges_kernel_launches", "ges_serve_create", "ges_serve_add_scene",
+            "ges_kernel_launches", "ges_render_fwd_noalloc", "ges_serve_create", "ges_serve_add_scene",
             "ges_serve_submit", "ges_serve_poll", "ges_serve_destroy"]
 
 
@@ -93,6 +93,7 @@ def _load():
         "ges_frame_inspect": ([P, P, P, P, P, P, P], i32),
         "ges_frame_count_work": ([P, P, P, P, P], i32),
         "ges_kernel_launches": ([], u64),
+        "ges_render_fwd_noalloc": ([P, P, P, P, P, P, P], i32),
         "ges_serve_create": ([P, P, i32, P], i32),
         "ges_serve_add_scene": ([P, P, P], i32),
         "ges_serve_submit": ([P, i32, P, P, P], i32),
@@ -267,6 +268,13 @@ def ges_frame_count_work(frame: int, stream=None):
 
 def ges_kernel_launches() -> int:
     return int(_lib.ges_kernel_launches())
+
+
+def ges_render_fwd_noalloc(scene: ges_scene, cam: ges_camera, params: ges_params, img, final_T, n_contrib,
+                           stream=None) -> None:
+    """Forward render that allocates no device memory (bounded sizes; see include/ges.h)."""
+    _check(_lib.ges_render_fwd_noalloc(ctypes.byref(scene), ctypes.byref(cam), ctypes.byref(params), _addr(img),
+                                       _addr(final_T), _addr(n_contrib), _stream(stream)))
 
 
 def ges_serve_create(ctx: int, params: ges_params, max_slots: int) -> int:
