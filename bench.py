@@ -155,17 +155,125 @@ def cpu_baseline(sc, cams, pixels, cores):
                       f"fwd+bwd (FP64 brute force over all primitives); Mpix/s extrapolated from the sampled pixels"}
 
 
+def serving_bench(n_requests, rate_mults, slots, dev, seed=40):
+    """Serving workload: 4 resident scenes (cube generator, SH3: 0.3M/0.8M/1.5M/3M primitives),
+    requests at 800x800 / 1245x825 / 1920x1080 from random cameras, Poisson arrivals.  The same
+    arrival trace is served (a) by the batched server (continuous batching, captured-graph
+    batches) and (b) by plain per-request launches of the frame API in arrival order.  Latency is
+    arrival to image-in-host-memory."""
+    import torch
+    from paper_2402_10128_gb300 import ges, render, scenes
+    sizes = [300_000, 800_000, 1_500_000, 3_000_000]
+    scs = [scenes.cube_scene(n, seed=seed + i, sh_degree=3) for i, n in enumerate(sizes)]
+    cams = scenes.random_sphere_cameras(n_requests, seed + 10, radius=(3.0, 5.0),
+                                        sizes=((800, 800), (1245, 825), (1920, 1080)))
+    rng = np.random.default_rng(seed + 20)
+    which = rng.integers(0, len(scs), n_requests)
+    gcams = [ges.make_camera(c) for c in cams]
+    ctx = render.default_context(dev.index or 0)
+    # (b) per-request path: one frame per resolution (sized for the largest scene), images copied to host
+    dev_scenes = [render.scene_tensors(sc, dev) for sc in scs]
+    frames = {}
+    host_out = [np.empty((3, c.height, c.width), np.float32) for c in cams]
+    n_max = max(sc.n for sc in scs)
+
+    def per_request(i):
+        w = which[i]
+        c = cams[i]
+        key = (c.width, c.height)
+        fr = frames.get(key)
+        if fr is None:
+            fr = frames[key] = render.Frame(n_max, c.width, c.height, key_capacity=0, ctx=ctx)
+        img, _, _ = fr.forward(dev_scenes[w], 3, gcams[i])
+        host_out[i][...] = img.cpu().numpy()
+
+    for i in range(min(12, n_requests)):  # warm-up: frames, capacities
+        per_request(i)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(n_requests):
+        per_request(i)
+    service = (time.perf_counter() - t0) / n_requests
+    capacity = 1.0 / service  # requests/s of back-to-back per-request launches
+
+    srv = ges.ges_serve_create(ctx.handle, ges.params_default(), slots)
+    keep = []
+    for sc in scs:
+        arrs = [np.ascontiguousarray(a, np.float32) for a in sc.arrays()]
+        keep.append(arrs)
+        ges.ges_serve_add_scene(srv, ges.make_scene(*arrs, sc.sh_degree))
+    # warm-up of the server (workspaces, graphs)
+    for i in range(min(16, n_requests)):
+        t = ges.ges_serve_submit(srv, int(which[i]), gcams[i], host_out[i])
+        ges.ges_serve_poll(srv, t, 120_000_000)
+
+    results = []
+    for mult in rate_mults:
+        rate = mult * capacity
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, n_requests))
+        # (a) server
+        tickets = [None] * n_requests
+        t_start = time.perf_counter() + 0.01
+
+        def submitter():
+            for i in range(n_requests):
+                dt = t_start + arrivals[i] - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                tickets[i] = ges.ges_serve_submit(srv, int(which[i]), gcams[i], host_out[i])
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        lat_srv = []
+        for i in range(n_requests):
+            while tickets[i] is None:
+                time.sleep(0.0002)
+            st, lat = ges.ges_serve_poll(srv, tickets[i], 120_000_000)
+            assert st == ges.GES_OK
+            lat_srv.append(lat)
+        th.join()
+        t_end_srv = time.perf_counter()
+        span_srv = t_end_srv - t_start
+        # (b) per-request launches, FIFO, same arrivals
+        lat_pr = []
+        t_start = time.perf_counter() + 0.01
+        for i in range(n_requests):
+            dt = t_start + arrivals[i] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            per_request(i)
+            lat_pr.append(1e3 * (time.perf_counter() - (t_start + arrivals[i])))
+        span_pr = time.perf_counter() - t_start
+        pix = sum(c.width * c.height for c in cams)
+        results.append({
+            "rate_mult": mult, "rate_req_s": rate,
+            "batched": {"p50_ms": float(np.percentile(lat_srv, 50)), "p99_ms": float(np.percentile(lat_srv, 99)),
+                        "req_s": n_requests / span_srv, "mpix_s": pix / span_srv / 1e6},
+            "per_request": {"p50_ms": float(np.percentile(lat_pr, 50)), "p99_ms": float(np.percentile(lat_pr, 99)),
+                            "req_s": n_requests / span_pr, "mpix_s": pix / span_pr / 1e6}})
+    ges.ges_serve_destroy(srv)
+    for fr in frames.values():
+        fr.close()
+    return {"workload": "4 resident cube scenes (0.3M/0.8M/1.5M/3M prims, SH3); 800x800/1245x825/1920x1080 "
+                        "requests, random cameras at radius 3-5, Poisson arrivals",
+            "requests": n_requests, "slots": slots, "per_request_service_ms": 1e3 * service,
+            "per_request_capacity_req_s": capacity, "rates": results}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--ref-pixels", type=int, default=96)
-    ap.add_argument("--cpu-pixels", type=int, default=768)
+    ap.add_argument("--ref-pixels", type=int, default=4096)
+    ap.add_argument("--cpu-pixels", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=N_PRIMS)
+    ap.add_argument("--serve-requests", type=int, default=100)
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="minimal run for ncu: no work counters, e2e or CPU baseline; warmup + steps fwd+bwd")
     args = ap.parse_args()
@@ -327,6 +435,11 @@ def main():
         out["e2e"] = e2e(args, sc, gcam, frame, params, dev, stream, ws, dist)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sc, cams, args.cpu_pixels, os.cpu_count() or 1)
+    if not args.no_serve:
+        del t, grads
+        frame.close()
+        torch.cuda.empty_cache()
+        out["serving"] = serving_bench(args.serve_requests, (0.5, 1.0, 2.0), args.serve_slots, dev)
     if rank == 0:
         print(json.dumps(out))
     if dist:

@@ -311,12 +311,14 @@ ges_status ges_preprocess(ges_frame* f, const ges_scene* scene, const ges_camera
     return fail(GES_ERR_INVALID_ARG, "camera %dx%d != frame %dx%d", cam->width, cam->height, f->W, f->H);
   if ((st = use_device(f->ctx->device)) != GES_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  f->vt.n = 1;
-  fill_view(f->vt.v[0], *cam, *scene, 0, 0);
+  f->vt.t.n = 1;
+  fill_view(f->vt.t.v[0], *cam, *scene, 0, 0);
+  f->vt.t.total_prims = (unsigned long long)scene->n;
+  f->vt.t.total_tiles = f->n_tiles;
   f->P = to_params(*params);
   f->n = scene->n;
   f->sh_degree = scene->sh_degree;
-  launch_preprocess<1>(f->vt, f->n, f->P, f->depth_key, f->dk[0], f->pv[0], f->rect, f->rec, f->ctx->num_sms, s);
+  launch_preprocess<FrameViews>(f->vt, f->n, f->P, f->depth_key, f->dk[0], f->pv[0], f->rect, f->rec, f->ctx->num_sms, s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "preprocess launch");
   f->have_pre = true;
@@ -351,7 +353,7 @@ ges_status ges_bin_sort(ges_frame* f, void* stream) {
       if ((st = frame_alloc_keys(f, cap)) != GES_OK) return st;
     }
   }
-  launch_keygen<1>(f->vt, f->offsets, f->d_K, f->n, f->sorted_prims, f->rect, f->key_cap, f->tk[0], f->tv[0], f->d_flags, s);
+  launch_keygen<FrameViews>(f->vt, f->offsets, f->d_K, f->n, f->sorted_prims, f->rect, f->key_cap, f->tk[0], f->tv[0], f->d_flags, s);
   int tcur = 0;
   radix_sort_pairs(f->tk, f->tv, tcur, 0, f->d_K, f->key_cap, bits_for(f->n_tiles), f->hist, f->hist_cap, f->scan, s);
   f->tile_keys = f->tk[tcur];
@@ -368,10 +370,10 @@ ges_status ges_render_fwd(ges_frame* f, float* img, float* final_T, uint32_t* n_
   if (!f->have_sort) return fail(GES_ERR_INVALID_ARG, "ges_render_fwd before ges_bin_sort");
   ges_status st = use_device(f->ctx->device);
   if (st != GES_OK) return st;
-  f->vt.v[0].img = img;
-  f->vt.v[0].final_T = final_T;
-  f->vt.v[0].n_contrib = n_contrib;
-  launch_render_fwd<1>(f->vt, f->n_tiles, f->ranges, f->tile_vals, f->rec, f->P, (cudaStream_t)stream);
+  f->vt.t.v[0].img = img;
+  f->vt.t.v[0].final_T = final_T;
+  f->vt.t.v[0].n_contrib = n_contrib;
+  launch_render_fwd<FrameViews>(f->vt, f->n_tiles, f->ranges, f->tile_vals, f->rec, f->P, (cudaStream_t)stream);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "render_fwd launch");
   return GES_OK;
@@ -391,7 +393,7 @@ ges_status ges_render_bwd(ges_frame* f, const ges_scene* scene, const float* fin
     return fail(GES_ERR_INVALID_ARG, "gradient quats and shs must be 16-byte aligned");
   if ((st = use_device(f->ctx->device)) != GES_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  ViewDesc& v = f->vt.v[0];
+  ViewDesc& v = f->vt.t.v[0];
   v.means = scene->means; v.scales = scene->scales; v.quats = scene->quats; v.betas = scene->betas;
   v.opac = scene->opacities; v.shs = scene->shs;
   v.final_T = const_cast<float*>(final_T);
@@ -402,8 +404,8 @@ ges_status ges_render_bwd(ges_frame* f, const ges_scene* scene, const float* fin
   cudaError_t e;
   if (f->n > 0 && (e = cudaMemsetAsync(f->g2d, 0, sizeof(float4) * 3 * f->n, s)) != cudaSuccess)
     return cuda_fail(e, "memset g2d");
-  launch_render_bwd<1>(f->vt, f->n_tiles, f->ranges, f->tile_vals, f->rec, f->P, f->g2d, s);
-  launch_preprocess_bwd<1>(f->vt, f->n, f->P, f->depth_key, f->g2d, f->ctx->num_sms, s);
+  launch_render_bwd<FrameViews>(f->vt, f->n_tiles, f->ranges, f->tile_vals, f->rec, f->P, f->g2d, s);
+  launch_preprocess_bwd<FrameViews>(f->vt, f->n, f->P, f->depth_key, f->g2d, f->ctx->num_sms, s);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "render_bwd launch");
   return GES_OK;
 }
@@ -492,13 +494,13 @@ ges_status ges_frame_count_work(ges_frame* f, void* stream, int64_t* evaluated, 
     if ((st = ctx_alloc(f->ctx, (void**)&f->work_img, sizeof(float) * 5 * npx)) != GES_OK) return st;
     if ((st = ctx_alloc(f->ctx, (void**)&f->work_stats, 16)) != GES_OK) return st;
   }
-  ViewTable<1> vt = f->vt;
-  vt.v[0].img = f->work_img;
-  vt.v[0].final_T = f->work_img + 3 * npx;
-  vt.v[0].n_contrib = reinterpret_cast<uint32_t*>(f->work_img + 4 * npx);
+  FrameViews vt = f->vt;
+  vt.t.v[0].img = f->work_img;
+  vt.t.v[0].final_T = f->work_img + 3 * npx;
+  vt.t.v[0].n_contrib = reinterpret_cast<uint32_t*>(f->work_img + 4 * npx);
   cudaError_t e;
   if ((e = cudaMemsetAsync(f->work_stats, 0, 16, s)) != cudaSuccess) return cuda_fail(e, "memset stats");
-  launch_render_fwd<1>(vt, f->n_tiles, f->ranges, f->tile_vals, f->rec, f->P, s, f->work_stats);
+  launch_render_fwd<FrameViews>(vt, f->n_tiles, f->ranges, f->tile_vals, f->rec, f->P, s, f->work_stats);
   unsigned long long h[2] = {0, 0};
   if ((e = cudaMemcpyAsync(h, f->work_stats, 16, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(e, "copy stats");
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "sync");

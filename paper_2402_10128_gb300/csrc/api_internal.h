@@ -5,7 +5,7 @@
 
 #include <mutex>
 
-#include "../../include/ges.h"
+#include "ges.h"
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -48,7 +48,7 @@ struct ges_frame {
   uint32_t* d_flags = nullptr;
   unsigned long long* h_K = nullptr;  // pinned
   // state of the current frame
-  ges::ViewTable<1> vt;
+  ges::FrameViews vt;
   ges::Params P;
   int64_t n = 0;
   int32_t sh_degree = 0;

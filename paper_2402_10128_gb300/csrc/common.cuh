@@ -51,8 +51,28 @@ template <int MAXV>
 struct ViewTable {
   int32_t n;
   int32_t pad;
+  unsigned long long total_prims;  // sum of the views' n
+  long long total_tiles;           // sum of the views' tiles
   ViewDesc v[MAXV];
 };
+
+// Where a kernel finds its view table: passed by value as a __grid_constant__ parameter (a single
+// frame), or read from device memory (serving batches, whose captured graphs replay unchanged
+// while the table is rewritten between replays).
+template <int MAXV>
+struct ViewsByValue {
+  static constexpr int kMax = MAXV;
+  ViewTable<MAXV> t;
+  __device__ __forceinline__ const ViewTable<MAXV>& get() const { return t; }
+};
+template <int MAXV>
+struct ViewsInMemory {
+  static constexpr int kMax = MAXV;
+  const ViewTable<MAXV>* p;
+  __device__ __forceinline__ const ViewTable<MAXV>& get() const { return *p; }
+};
+using FrameViews = ViewsByValue<1>;
+using BatchViews = ViewsInMemory<kServeMaxViews>;
 
 template <int MAXV>
 __device__ __forceinline__ int view_of_prim(const ViewTable<MAXV>& vt, int64_t g) {

@@ -9,11 +9,13 @@ namespace ges {
 void count_launches(int n);
 
 // ---- per-primitive kernels (preprocess.cu)
-template <int MAXV>
-void launch_preprocess(const ViewTable<MAXV>& vt, int64_t total, const Params& P, uint32_t* depth_key,
-                       uint32_t* sort_keys, uint32_t* sort_vals, ushort4* rect, Rec* rec, int num_sms, cudaStream_t s);
-template <int MAXV>
-void launch_preprocess_bwd(const ViewTable<MAXV>& vt, int64_t total, const Params& P, const uint32_t* depth_key,
+// VS is FrameViews (table by value) or BatchViews (table in device memory).  grid_total sizes the
+// grid; the kernels loop over the table's total_prims.
+template <class VS>
+void launch_preprocess(const VS& vs, int64_t grid_total, const Params& P, uint32_t* depth_key, uint32_t* sort_keys,
+                       uint32_t* sort_vals, ushort4* rect, Rec* rec, int num_sms, cudaStream_t s);
+template <class VS>
+void launch_preprocess_bwd(const VS& vs, int64_t grid_total, const Params& P, const uint32_t* depth_key,
                            const float4* g2d, int num_sms, cudaStream_t s);
 void set_key_constants(cudaStream_t s);
 
@@ -27,9 +29,10 @@ struct ScanScratch {
 template <typename TIn, typename TOut>
 void scan_exclusive(const TIn* in, TOut* out, int64_t n, TOut* total, ScanScratch& sc, cudaStream_t s);
 
-// per-primitive tile counts in depth-sorted order: touched[j] = area(rect[sorted_vals[j]])
+// per-primitive tile counts in depth order: touched[j] = area(rect[sorted_vals[j]]) for j < count,
+// 0 for count <= j < n (count = *n_dev if given, else n)
 void launch_gather_touched(const uint32_t* sorted_vals, const ushort4* rect, int64_t n, uint32_t* touched,
-                           cudaStream_t s);
+                           cudaStream_t s, const unsigned long long* n_dev = nullptr);
 
 // stable LSD radix sort of (u32 key, u32 value) on the low `total_bits` bits.  The element count is
 // n_dev (device) if non-null, else n_host; buffers hold n_cap elements.  keys[cur]/vals[cur] hold the
@@ -38,8 +41,8 @@ void radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_
                       int64_t n_cap, int total_bits, uint32_t* hist, int64_t hist_cap, ScanScratch& sc, cudaStream_t s);
 int64_t radix_hist_entries(int64_t n_cap, int total_bits);
 
-template <int MAXV>
-void launch_keygen(const ViewTable<MAXV>& vt, const unsigned long long* offsets, const unsigned long long* K_dev,
+template <class VS>
+void launch_keygen(const VS& vs, const unsigned long long* offsets, const unsigned long long* K_dev,
                    int64_t n, const uint32_t* sorted_vals, const ushort4* rect, int64_t cap, uint32_t* tile_keys,
                    uint32_t* tile_vals, uint32_t* flags, cudaStream_t s);
 void launch_ranges(const uint32_t* tile_keys, const unsigned long long* K_dev, int64_t cap, uint2* ranges, int num_sms,
@@ -53,11 +56,14 @@ constexpr uint32_t kFlagOverflow = 1u;
 // ---- compositing (raster.cu)
 // stats (optional, device u64[2]): number of (fragment, pixel) pairs evaluated before the stop, and of
 // those within the primitive's extent (the ones that reach the falloff's transcendentals)
-template <int MAXV>
-void launch_render_fwd(const ViewTable<MAXV>& vt, int64_t total_tiles, const uint2* ranges, const uint32_t* vals,
-                       const Rec* rec, const Params& P, cudaStream_t s, unsigned long long* stats = nullptr);
-template <int MAXV>
-void launch_render_bwd(const ViewTable<MAXV>& vt, int64_t total_tiles, const uint2* ranges, const uint32_t* vals,
-                       const Rec* rec, const Params& P, float4* g2d, cudaStream_t s);
+// One CTA per tile (grid = total_tiles), or, with tile_counter, a persistent grid whose CTAs take
+// tiles from *tile_counter (zeroed by the caller) until the table's total_tiles are done.
+template <class VS>
+void launch_render_fwd(const VS& vs, int64_t total_tiles, const uint2* ranges, const uint32_t* vals, const Rec* rec,
+                       const Params& P, cudaStream_t s, unsigned long long* stats = nullptr,
+                       unsigned int* tile_counter = nullptr, int num_sms = 0);
+template <class VS>
+void launch_render_bwd(const VS& vs, int64_t total_tiles, const uint2* ranges, const uint32_t* vals, const Rec* rec,
+                       const Params& P, float4* g2d, cudaStream_t s);
 
 }  // namespace ges

@@ -136,9 +136,11 @@ extern "C" ges_status ges_render_fwd_noalloc(const ges_scene* scene, const ges_c
   cudaStream_t s = (cudaStream_t)stream;
   unsigned char* b = ds->base;
   const int64_t n = scene->n;
-  ViewTable<1> vt;
-  vt.n = 1;
-  fill_view(vt.v[0], *cam, *scene, 0, 0);
+  FrameViews vt;
+  vt.t.n = 1;
+  fill_view(vt.t.v[0], *cam, *scene, 0, 0);
+  vt.t.total_prims = (unsigned long long)scene->n;
+  vt.t.total_tiles = tiles;
   const Params P = to_params(*params);
   uint32_t* dk[2] = {at<uint32_t>(b, kL.dk0), at<uint32_t>(b, kL.dk1)};
   uint32_t* pv[2] = {at<uint32_t>(b, kL.pv0), at<uint32_t>(b, kL.pv1)};
@@ -161,19 +163,19 @@ extern "C" ges_status ges_render_fwd_noalloc(const ges_scene* scene, const ges_c
   // are never written by the ranges kernel)
   if ((e = cudaMemsetAsync(flags, 0, 4, s)) != cudaSuccess) return cuda_fail(e, "clear flags");
   if ((e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * tiles, s)) != cudaSuccess) return cuda_fail(e, "clear ranges");
-  launch_preprocess<1>(vt, n, P, depth_key, dk[0], pv[0], rect, rec, ds->num_sms, s);
+  launch_preprocess<FrameViews>(vt, n, P, depth_key, dk[0], pv[0], rect, rec, ds->num_sms, s);
   int cur = 0;
   radix_sort_pairs(dk, pv, cur, n, nullptr, n, 32, hist, kNaHistEntries, scan, s);
   launch_gather_touched(pv[cur], rect, n, touched, s);
   scan_exclusive<uint32_t, unsigned long long>(touched, offsets, n, dK, scan, s);
-  launch_keygen<1>(vt, offsets, dK, n, pv[cur], rect, kNaMaxKeys, tk[0], tv[0], flags, s);
+  launch_keygen<FrameViews>(vt, offsets, dK, n, pv[cur], rect, kNaMaxKeys, tk[0], tv[0], flags, s);
   int tcur = 0;
   radix_sort_pairs(tk, tv, tcur, 0, dK, kNaMaxKeys, bits_for(tiles), hist, kNaHistEntries, scan, s);
   launch_ranges(tk[tcur], dK, kNaMaxKeys, ranges, ds->num_sms, s);
-  vt.v[0].img = img;
-  vt.v[0].final_T = final_T;
-  vt.v[0].n_contrib = n_contrib;
-  launch_render_fwd<1>(vt, tiles, ranges, tv[tcur], rec, P, s);
+  vt.t.v[0].img = img;
+  vt.t.v[0].final_T = final_T;
+  vt.t.v[0].n_contrib = n_contrib;
+  launch_render_fwd<FrameViews>(vt, tiles, ranges, tv[tcur], rec, P, s);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "no-alloc render launch");
   // the duplicate count is known only on the device: wait for it to report an overflow
   uint32_t h_flags = 0;

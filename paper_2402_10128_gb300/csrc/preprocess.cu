@@ -164,12 +164,13 @@ __device__ __forceinline__ float3 sh_colour_bwd(float dx, float dy, float dz, co
 // ---------------------------------------------------------------------------------------------
 // K1: preprocess.  One thread per global primitive id (grid-stride).
 // ---------------------------------------------------------------------------------------------
-template <int MAXV>
-__global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ ViewTable<MAXV> vt, int64_t total,
-                                                    const Params P, uint32_t* __restrict__ depth_key,
+template <class VS>
+__global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ VS vs, const Params P, uint32_t* __restrict__ depth_key,
                                                     uint32_t* __restrict__ sort_keys,
                                                     uint32_t* __restrict__ sort_vals, ushort4* __restrict__ rect,
                                                     Rec* __restrict__ rec) {
+  const auto& vt = vs.get();
+  const int64_t total = (int64_t)vt.total_prims;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
     const ViewDesc& vd = vt.v[view_of_prim(vt, g)];
     const int64_t i = g - vd.prim_base;
@@ -318,10 +319,12 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ View
 // K8: preprocess backward.  g2d[3g..3g+2] holds the compositing stage's gradients of
 // (mx, my, conic a, conic b) (conic c, kappa, hb, r) (g, b, -, -).  Writes every output.
 // ---------------------------------------------------------------------------------------------
-template <int MAXV>
-__global__ void __launch_bounds__(256) k_preprocess_bwd(const __grid_constant__ ViewTable<MAXV> vt, int64_t total,
-                                                        const Params P, const uint32_t* __restrict__ depth_key,
+template <class VS>
+__global__ void __launch_bounds__(256) k_preprocess_bwd(const __grid_constant__ VS vs, const Params P,
+                                                        const uint32_t* __restrict__ depth_key,
                                                         const float4* __restrict__ g2d) {
+  const auto& vt = vs.get();
+  const int64_t total = (int64_t)vt.total_prims;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
     const ViewDesc& vd = vt.v[view_of_prim(vt, g)];
     const int64_t i = g - vd.prim_base;
@@ -491,19 +494,19 @@ static int grid_for(int64_t total, int num_sms) {
   return (int)(need < cap ? (need > 0 ? need : 1) : cap);
 }
 
-template <int MAXV>
-void launch_preprocess(const ViewTable<MAXV>& vt, int64_t total, const Params& P, uint32_t* depth_key,
-                       uint32_t* sort_keys, uint32_t* sort_vals, ushort4* rect, Rec* rec, int num_sms, cudaStream_t s) {
-  if (total <= 0) return;
-  k_preprocess<MAXV><<<grid_for(total, num_sms), 256, 0, s>>>(vt, total, P, depth_key, sort_keys, sort_vals, rect, rec);
+template <class VS>
+void launch_preprocess(const VS& vs, int64_t grid_total, const Params& P, uint32_t* depth_key, uint32_t* sort_keys,
+                       uint32_t* sort_vals, ushort4* rect, Rec* rec, int num_sms, cudaStream_t s) {
+  if (grid_total <= 0) return;
+  k_preprocess<VS><<<grid_for(grid_total, num_sms), 256, 0, s>>>(vs, P, depth_key, sort_keys, sort_vals, rect, rec);
   count_launches(1);
 }
 
-template <int MAXV>
-void launch_preprocess_bwd(const ViewTable<MAXV>& vt, int64_t total, const Params& P, const uint32_t* depth_key,
+template <class VS>
+void launch_preprocess_bwd(const VS& vs, int64_t grid_total, const Params& P, const uint32_t* depth_key,
                            const float4* g2d, int num_sms, cudaStream_t s) {
-  if (total <= 0) return;
-  k_preprocess_bwd<MAXV><<<grid_for(total, num_sms), 256, 0, s>>>(vt, total, P, depth_key, g2d);
+  if (grid_total <= 0) return;
+  k_preprocess_bwd<VS><<<grid_for(grid_total, num_sms), 256, 0, s>>>(vs, P, depth_key, g2d);
   count_launches(1);
 }
 
@@ -519,13 +522,11 @@ void set_key_constants(cudaStream_t s) {
   cudaMemcpyToSymbolAsync(c_exp2_coef, c, sizeof(c), 0, cudaMemcpyHostToDevice, s);
 }
 
-template void launch_preprocess<1>(const ViewTable<1>&, int64_t, const Params&, uint32_t*, uint32_t*, uint32_t*,
-                                   ushort4*, Rec*, int, cudaStream_t);
-template void launch_preprocess<kServeMaxViews>(const ViewTable<kServeMaxViews>&, int64_t, const Params&, uint32_t*,
-                                                uint32_t*, uint32_t*, ushort4*, Rec*, int, cudaStream_t);
-template void launch_preprocess_bwd<1>(const ViewTable<1>&, int64_t, const Params&, const uint32_t*, const float4*, int,
-                                       cudaStream_t);
-template void launch_preprocess_bwd<kServeMaxViews>(const ViewTable<kServeMaxViews>&, int64_t, const Params&,
-                                                    const uint32_t*, const float4*, int, cudaStream_t);
+template void launch_preprocess<FrameViews>(const FrameViews&, int64_t, const Params&, uint32_t*, uint32_t*, uint32_t*,
+                                            ushort4*, Rec*, int, cudaStream_t);
+template void launch_preprocess<BatchViews>(const BatchViews&, int64_t, const Params&, uint32_t*, uint32_t*, uint32_t*,
+                                            ushort4*, Rec*, int, cudaStream_t);
+template void launch_preprocess_bwd<FrameViews>(const FrameViews&, int64_t, const Params&, const uint32_t*,
+                                                const float4*, int, cudaStream_t);
 
 }  // namespace ges

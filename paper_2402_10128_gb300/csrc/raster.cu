@@ -41,12 +41,10 @@ __device__ __forceinline__ WarpBlock warp_block(int lt, int tiles_x) {
 }
 
 template <int MAXV, bool STATS>
-__global__ void __launch_bounds__(kThreads) k_render_fwd(const __grid_constant__ ViewTable<MAXV> vt,
-                                                         const uint2* __restrict__ ranges,
-                                                         const uint32_t* __restrict__ vals, const Rec* __restrict__ rec,
-                                                         const Params P, unsigned long long* __restrict__ stats) {
-  __shared__ Rec batch[kBatch];
-  const int64_t tile = blockIdx.x;
+__device__ __forceinline__ void render_tile_fwd(const ViewTable<MAXV>& vt, int64_t tile, Rec* batch,
+                                                const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
+                                                const Rec* __restrict__ rec, const Params& P,
+                                                unsigned long long* __restrict__ stats) {
   const ViewDesc& vd = vt.v[view_of_tile(vt, tile)];
   const WarpBlock wb = warp_block((int)(tile - vd.tile_base), vd.tiles_x);
   const uint2 rg = ranges[tile];
@@ -125,6 +123,36 @@ __global__ void __launch_bounds__(kThreads) k_render_fwd(const __grid_constant__
   }
 }
 
+template <class VS, bool STATS>
+__global__ void __launch_bounds__(kThreads) k_render_fwd(const __grid_constant__ VS vs, const uint2* __restrict__ ranges,
+                                                         const uint32_t* __restrict__ vals, const Rec* __restrict__ rec,
+                                                         const Params P, unsigned long long* __restrict__ stats) {
+  __shared__ Rec batch[kBatch];
+  render_tile_fwd<VS::kMax, STATS>(vs.get(), (int64_t)blockIdx.x, batch, ranges, vals, rec, P, stats);
+}
+
+// Persistent form: CTAs take tiles from a work counter until the table's total_tiles are done, so
+// a fixed grid serves batches of any size (the launch can be replayed from a captured graph).
+template <class VS>
+__global__ void __launch_bounds__(kThreads) k_render_fwd_persistent(const __grid_constant__ VS vs,
+                                                                    const uint2* __restrict__ ranges,
+                                                                    const uint32_t* __restrict__ vals,
+                                                                    const Rec* __restrict__ rec, const Params P,
+                                                                    unsigned int* __restrict__ tile_counter) {
+  __shared__ Rec batch[kBatch];
+  __shared__ unsigned int s_tile;
+  const auto& vt = vs.get();
+  const long long total = vt.total_tiles;
+  for (;;) {
+    __syncthreads();  // previous tile's readers of s_tile and batch are done
+    if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
+    __syncthreads();
+    const unsigned int tile = s_tile;
+    if ((long long)tile >= total) break;
+    render_tile_fwd<VS::kMax, false>(vt, (int64_t)tile, batch, ranges, vals, rec, P, nullptr);
+  }
+}
+
 // Sums 16 per-lane values over the warp with a reduce-scatter butterfly (16 shuffles instead of
 // 16 x 5): at each step a lane keeps half of its values and receives the partner's copy of that
 // half.  On return lane L holds the full sum of value ((L >> 1) & 15) (L and L^1 hold the same).
@@ -153,14 +181,14 @@ __device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16]) {
 //   q = a dx^2 + 2 b dx dy + c dy^2, dx = px - mx
 // A thread sums its two pixels' terms, the warp sums by a reduce-scatter butterfly, and ten lanes
 // add the ten per-primitive sums with one atomic each.
-template <int MAXV>
-__global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__ ViewTable<MAXV> vt,
-                                                         const uint2* __restrict__ ranges,
+template <class VS>
+__global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__ VS vs, const uint2* __restrict__ ranges,
                                                          const uint32_t* __restrict__ vals, const Rec* __restrict__ rec,
                                                          const Params P, float4* __restrict__ g2d) {
   __shared__ Rec batch[kBatch];
   __shared__ uint32_t ids[kBatch];
   __shared__ uint32_t s_max_last;
+  const auto& vt = vs.get();
   const int64_t tile = blockIdx.x;
   const ViewDesc& vd = vt.v[view_of_tile(vt, tile)];
   const WarpBlock wb = warp_block((int)(tile - vd.tile_base), vd.tiles_x);
@@ -274,31 +302,38 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
 
 }  // namespace
 
-template <int MAXV>
-void launch_render_fwd(const ViewTable<MAXV>& vt, int64_t total_tiles, const uint2* ranges, const uint32_t* vals,
-                       const Rec* rec, const Params& P, cudaStream_t s, unsigned long long* stats) {
+template <class VS>
+void launch_render_fwd(const VS& vs, int64_t total_tiles, const uint2* ranges, const uint32_t* vals, const Rec* rec,
+                       const Params& P, cudaStream_t s, unsigned long long* stats, unsigned int* tile_counter,
+                       int num_sms) {
   if (total_tiles <= 0) return;
-  if (stats)
-    k_render_fwd<MAXV, true><<<(unsigned)total_tiles, kThreads, 0, s>>>(vt, ranges, vals, rec, P, stats);
-  else
-    k_render_fwd<MAXV, false><<<(unsigned)total_tiles, kThreads, 0, s>>>(vt, ranges, vals, rec, P, nullptr);
+  if (tile_counter) {
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_fwd_persistent<VS>, kThreads, 0);
+    const int64_t grid = (int64_t)num_sms * (per_sm > 0 ? per_sm : 1);
+    k_render_fwd_persistent<VS><<<(unsigned)(grid < total_tiles ? grid : total_tiles), kThreads, 0, s>>>(
+        vs, ranges, vals, rec, P, tile_counter);
+  } else if (stats) {
+    k_render_fwd<VS, true><<<(unsigned)total_tiles, kThreads, 0, s>>>(vs, ranges, vals, rec, P, stats);
+  } else {
+    k_render_fwd<VS, false><<<(unsigned)total_tiles, kThreads, 0, s>>>(vs, ranges, vals, rec, P, nullptr);
+  }
   count_launches(1);
 }
 
-template <int MAXV>
-void launch_render_bwd(const ViewTable<MAXV>& vt, int64_t total_tiles, const uint2* ranges, const uint32_t* vals,
-                       const Rec* rec, const Params& P, float4* g2d, cudaStream_t s) {
+template <class VS>
+void launch_render_bwd(const VS& vs, int64_t total_tiles, const uint2* ranges, const uint32_t* vals, const Rec* rec,
+                       const Params& P, float4* g2d, cudaStream_t s) {
   if (total_tiles <= 0) return;
-  k_render_bwd<MAXV><<<(unsigned)total_tiles, kThreads, 0, s>>>(vt, ranges, vals, rec, P, g2d);
+  k_render_bwd<VS><<<(unsigned)total_tiles, kThreads, 0, s>>>(vs, ranges, vals, rec, P, g2d);
   count_launches(1);
 }
 
-template void launch_render_fwd<1>(const ViewTable<1>&, int64_t, const uint2*, const uint32_t*, const Rec*,
-                                   const Params&, cudaStream_t, unsigned long long*);
-template void launch_render_fwd<kServeMaxViews>(const ViewTable<kServeMaxViews>&, int64_t, const uint2*,
-                                                const uint32_t*, const Rec*, const Params&, cudaStream_t,
-                                                unsigned long long*);
-template void launch_render_bwd<1>(const ViewTable<1>&, int64_t, const uint2*, const uint32_t*, const Rec*,
-                                   const Params&, float4*, cudaStream_t);
+template void launch_render_fwd<FrameViews>(const FrameViews&, int64_t, const uint2*, const uint32_t*, const Rec*,
+                                            const Params&, cudaStream_t, unsigned long long*, unsigned int*, int);
+template void launch_render_fwd<BatchViews>(const BatchViews&, int64_t, const uint2*, const uint32_t*, const Rec*,
+                                            const Params&, cudaStream_t, unsigned long long*, unsigned int*, int);
+template void launch_render_bwd<FrameViews>(const FrameViews&, int64_t, const uint2*, const uint32_t*, const Rec*,
+                                            const Params&, float4*, cudaStream_t);
 
 }  // namespace ges

@@ -104,13 +104,20 @@ __global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restr
   constexpr int kWarps = kThreads / 32;
   __shared__ uint32_t cnt[kWarps][256];  // one private histogram per warp: less atomic contention
   const int nbins = 1 << bits;
-  for (int i = threadIdx.x; i < kWarps * 256; i += kThreads) (&cnt[0][0])[i] = 0;
-  __syncthreads();
   const int64_t n = element_count(n_host, n_dev, cap);
-  const int64_t base = (int64_t)blockIdx.x * kChunk;
   const uint32_t mask = (uint32_t)nbins - 1u;
   const int w = threadIdx.x >> 5;
-  if (base < n) {
+  // every column of the [bin][chunk] matrix is written (zeros past the element count), so the
+  // following scan over the whole matrix is correct for any count up to the capacity
+  for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const int64_t base = c * kChunk;
+    if (base >= n) {
+      for (int b = threadIdx.x; b < nbins; b += kThreads) hist[(int64_t)b * nchunks + c] = 0;
+      continue;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kWarps * 256; i += kThreads) (&cnt[0][0])[i] = 0;
+    __syncthreads();
     if (base + kChunk <= n) {
       const uint4* k4 = reinterpret_cast<const uint4*>(keys + base);
 #pragma unroll
@@ -127,13 +134,13 @@ __global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restr
         if (idx < n) atomicAdd(&cnt[w][(keys[idx] >> shift) & mask], 1u);
       }
     }
-  }
-  __syncthreads();
-  for (int b = threadIdx.x; b < nbins; b += kThreads) {
-    uint32_t t = 0;
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += kThreads) {
+      uint32_t t = 0;
 #pragma unroll
-    for (int ww = 0; ww < kWarps; ++ww) t += cnt[ww][b];
-    hist[(int64_t)b * nchunks + blockIdx.x] = t;
+      for (int ww = 0; ww < kWarps; ++ww) t += cnt[ww][b];
+      hist[(int64_t)b * nchunks + c] = t;
+    }
   }
 }
 
@@ -159,13 +166,14 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
   const int nbins = 1 << bits;
   const uint32_t mask = (uint32_t)nbins - 1u;
   const int64_t n = element_count(n_host, n_dev, cap);
-  const int64_t base = (int64_t)blockIdx.x * kChunk;
-  if (base >= n) return;  // uniform across the CTA
-  const int count = (int)min((int64_t)kChunk, n - base);
   const int w = threadIdx.x >> 5;
   const unsigned lane = lane_id();
+  for (int64_t c = blockIdx.x; c * kChunk < n; c += gridDim.x) {
+  const int64_t base = c * kChunk;
+  const int count = (int)min((int64_t)kChunk, n - base);
+  __syncthreads();  // the previous chunk's readers of the shared arrays are done
   for (int i = threadIdx.x; i < kWarps * 257; i += kThreads) (&wcnt[0][0])[i] = 0;
-  for (int b = threadIdx.x; b < nbins; b += kThreads) goff[b] = hist_scanned[(int64_t)b * nchunks + blockIdx.x];
+  for (int b = threadIdx.x; b < nbins; b += kThreads) goff[b] = hist_scanned[(int64_t)b * nchunks + c];
   __syncthreads();
   const unsigned lt_mask = (1u << lane) - 1u;
   uint32_t key[kItems], val[kItems], rank[kItems];
@@ -234,22 +242,30 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
     keys_out[gpos] = k;
     vals_out[gpos] = svals[i];
   }
+  }  // chunk loop
 }
 
 // ---------------------------------------------------------------- K2 input
-__global__ void k_gather_touched(const uint32_t* __restrict__ sorted_vals, const ushort4* __restrict__ rect, int64_t n,
-                                 uint32_t* __restrict__ touched) {
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-    const ushort4 r = rect[sorted_vals[j]];
-    touched[j] = (uint32_t)(r.z - r.x) * (uint32_t)(r.w - r.y);
+// touched[j] for j < len: the tile count of the j-th primitive in depth order, or 0 for j >= the
+// element count (host n, or the device count n_dev when given)
+__global__ void k_gather_touched(const uint32_t* __restrict__ sorted_vals, const ushort4* __restrict__ rect, int64_t len,
+                                 const unsigned long long* __restrict__ n_dev, uint32_t* __restrict__ touched) {
+  const int64_t n = n_dev ? (int64_t)*n_dev : len;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < len; j += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t t = 0;
+    if (j < n) {
+      const ushort4 r = rect[sorted_vals[j]];
+      t = (uint32_t)(r.z - r.x) * (uint32_t)(r.w - r.y);
+    }
+    touched[j] = t;
   }
 }
 
 // ---------------------------------------------------------------- K3 keygen
 constexpr int kKeygenEntries = 2048;
 
-template <int MAXV>
-__global__ void __launch_bounds__(kThreads) k_keygen(const __grid_constant__ ViewTable<MAXV> vt,
+template <class VS>
+__global__ void __launch_bounds__(kThreads) k_keygen(const __grid_constant__ VS vs,
                                                      const unsigned long long* __restrict__ offsets,
                                                      const unsigned long long* __restrict__ K_dev, int64_t n,
                                                      const uint32_t* __restrict__ sorted_vals,
@@ -258,14 +274,15 @@ __global__ void __launch_bounds__(kThreads) k_keygen(const __grid_constant__ Vie
                                                      uint32_t* __restrict__ flags) {
   __shared__ uint32_t win[kKeygenEntries + 2];
   __shared__ int64_t s_jlo, s_jhi;
+  const auto& vt = vs.get();
   const unsigned long long K = *K_dev;
   if ((int64_t)K > cap) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(flags, kFlagOverflow);
     return;
   }
-  const int64_t e0 = (int64_t)blockIdx.x * kKeygenEntries;
-  if (e0 >= (int64_t)K) return;
+  for (int64_t e0 = (int64_t)blockIdx.x * kKeygenEntries; e0 < (int64_t)K; e0 += (int64_t)gridDim.x * kKeygenEntries) {
   const int64_t e1 = min(e0 + (int64_t)kKeygenEntries, (int64_t)K);
+  __syncthreads();  // the previous block of entries is done with the window
   if (threadIdx.x < 2) {
     // last j with offsets[j] <= e (for e = e0 and e = e1 - 1)
     const unsigned long long e = threadIdx.x == 0 ? (unsigned long long)e0 : (unsigned long long)(e1 - 1);
@@ -301,6 +318,7 @@ __global__ void __launch_bounds__(kThreads) k_keygen(const __grid_constant__ Vie
     tile_keys[e] = (uint32_t)vd.tile_base + ((uint32_t)r.y + tyy) * (uint32_t)vd.tiles_x + (uint32_t)r.x + txx;
     tile_vals[e] = g;
   }
+  }  // entry-block loop
 }
 
 // ---------------------------------------------------------------- K5 ranges
@@ -325,6 +343,26 @@ __global__ void k_make_keys(const uint32_t* __restrict__ tile_keys, const uint32
 }
 
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// streaming multiprocessors of the current device (cached per device)
+int sm_count() {
+  static int cache[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 152;
+  if (!cache[dev]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = v > 0 ? v : 152;
+  }
+  return cache[dev];
+}
+
+// grid for a grid-stride loop over `items` units: at most `per_sm` CTAs per SM
+unsigned grid_cap(int64_t items, int per_sm) {
+  const int64_t cap = (int64_t)sm_count() * per_sm;
+  return (unsigned)(items < cap ? (items > 0 ? items : 1) : cap);
+}
 
 }  // namespace
 
@@ -368,11 +406,12 @@ template void scan_exclusive<uint32_t, uint32_t>(const uint32_t*, uint32_t*, int
 template void scan_exclusive<uint32_t, unsigned long long>(const uint32_t*, unsigned long long*, int64_t,
                                                            unsigned long long*, ScanScratch&, cudaStream_t);
 
-void launch_gather_touched(const uint32_t* sorted_vals, const ushort4* rect, int64_t n, uint32_t* touched, cudaStream_t s) {
+void launch_gather_touched(const uint32_t* sorted_vals, const ushort4* rect, int64_t n, uint32_t* touched, cudaStream_t s,
+                           const unsigned long long* n_dev) {
   if (n <= 0) return;
   int64_t blocks = cdiv(n, 256);
   if (blocks > 65535 * 8) blocks = 65535 * 8;
-  k_gather_touched<<<(unsigned)blocks, 256, 0, s>>>(sorted_vals, rect, n, touched);
+  k_gather_touched<<<(unsigned)blocks, 256, 0, s>>>(sorted_vals, rect, n, n_dev, touched);
   count_launches(1);
 }
 
@@ -394,23 +433,22 @@ void radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_
     const int bits = (total_bits - shift) < bits_per ? (total_bits - shift) : bits_per;
     const int64_t entries = ((int64_t)1 << bits) * nchunks;
     (void)hist_cap;
-    k_radix_hist<<<(unsigned)nchunks, kThreads, 0, s>>>(keys[cur], n_host, n_dev, n_cap, shift, bits, hist, nchunks);
+    k_radix_hist<<<grid_cap(nchunks, 8), kThreads, 0, s>>>(keys[cur], n_host, n_dev, n_cap, shift, bits, hist, nchunks);
     scan_exclusive<uint32_t, uint32_t>(hist, hist, entries, (uint32_t*)nullptr, sc, s);
-    k_radix_scatter<<<(unsigned)nchunks, kThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_host,
+    k_radix_scatter<<<grid_cap(nchunks, 4), kThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_host,
                                                            n_dev, n_cap, shift, bits, hist, nchunks);
     count_launches(2);
     cur ^= 1;
   }
 }
 
-template <int MAXV>
-void launch_keygen(const ViewTable<MAXV>& vt, const unsigned long long* offsets, const unsigned long long* K_dev, int64_t n,
+template <class VS>
+void launch_keygen(const VS& vs, const unsigned long long* offsets, const unsigned long long* K_dev, int64_t n,
                    const uint32_t* sorted_vals, const ushort4* rect, int64_t cap, uint32_t* tile_keys, uint32_t* tile_vals,
                    uint32_t* flags, cudaStream_t s) {
   if (n <= 0 || cap <= 0) return;
-  const int64_t blocks = cdiv(cap, kKeygenEntries);
-  k_keygen<MAXV><<<(unsigned)blocks, kThreads, 0, s>>>(vt, offsets, K_dev, n, sorted_vals, rect, cap, tile_keys, tile_vals,
-                                                       flags);
+  k_keygen<VS><<<grid_cap(cdiv(cap, kKeygenEntries), 8), kThreads, 0, s>>>(vs, offsets, K_dev, n, sorted_vals, rect, cap, tile_keys, tile_vals,
+                                                     flags);
   count_launches(1);
 }
 
@@ -432,10 +470,11 @@ void launch_make_keys(const uint32_t* tile_keys, const uint32_t* tile_vals, cons
   count_launches(1);
 }
 
-template void launch_keygen<1>(const ViewTable<1>&, const unsigned long long*, const unsigned long long*, int64_t,
-                               const uint32_t*, const ushort4*, int64_t, uint32_t*, uint32_t*, uint32_t*, cudaStream_t);
-template void launch_keygen<kServeMaxViews>(const ViewTable<kServeMaxViews>&, const unsigned long long*,
-                                            const unsigned long long*, int64_t, const uint32_t*, const ushort4*, int64_t,
-                                            uint32_t*, uint32_t*, uint32_t*, cudaStream_t);
+template void launch_keygen<FrameViews>(const FrameViews&, const unsigned long long*, const unsigned long long*, int64_t,
+                                        const uint32_t*, const ushort4*, int64_t, uint32_t*, uint32_t*, uint32_t*,
+                                        cudaStream_t);
+template void launch_keygen<BatchViews>(const BatchViews&, const unsigned long long*, const unsigned long long*, int64_t,
+                                        const uint32_t*, const ushort4*, int64_t, uint32_t*, uint32_t*, uint32_t*,
+                                        cudaStream_t);
 
 }  // namespace ges

@@ -1,0 +1,140 @@
+"""Serving loop (continuous batching through captured-graph batches) against the frame path.
+
+Each request's image must equal the same scene and camera rendered alone through
+ges_preprocess + ges_bin_sort + ges_render_fwd: the batch gives every view its own range of
+primitive and tile ids, so each tile's list (and hence each pixel) is the same alone and in a mix.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2402_10128_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ges():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+    from paper_2402_10128_gb300 import ges as g
+    return g
+
+
+def _host_scene(ges, sc):
+    arrs = [np.ascontiguousarray(a, np.float32) for a in sc.arrays()]
+    return ges.make_scene(*arrs, sc.sh_degree), arrs
+
+
+def _frame_render(scene, cam):
+    from paper_2402_10128_gb300 import render
+    t = render.scene_tensors(scene, "cuda")
+    fr = render.Frame(scene.n, cam.width, cam.height)
+    img, _, _ = fr.forward(t, scene.sh_degree, cam)
+    torch.cuda.synchronize()
+    return img.cpu().numpy()
+
+
+def _setup(ges, slots=4):
+    from paper_2402_10128_gb300 import render
+    ctx = render.default_context(0)
+    srv = ges.ges_serve_create(ctx.handle, ges.params_default(), slots)
+    scs = [scenes.cube_scene(3000, seed=31, sh_degree=3),
+           scenes.cube_scene(8000, seed=32, sh_degree=1, beta_range=(0.5, 6.0), beta_log=True),
+           scenes.cube_scene(1500, seed=33, sh_degree=0)]
+    keep = []
+    ids = []
+    for sc in scs:
+        hs, arrs = _host_scene(ges, sc)
+        keep.append(arrs)
+        ids.append(ges.ges_serve_add_scene(srv, hs))
+    return srv, scs, ids, keep
+
+
+def _cams(n, seed):
+    return scenes.random_sphere_cameras(n, seed, radius=(3.0, 5.0), sizes=((96, 96), (160, 90), (203, 117)))
+
+
+def test_each_result_same_alone_and_in_the_mix(ges):
+    srv, scs, ids, keep = _setup(ges, slots=4)
+    try:
+        cams = _cams(12, seed=5)
+        rng = np.random.default_rng(0)
+        which = rng.integers(0, len(scs), len(cams))
+        refs = [_frame_render(scs[w], c) for w, c in zip(which, cams)]
+        # alone: one request at a time
+        for k in (0, 1):
+            out = np.empty((3, cams[k].height, cams[k].width), np.float32)
+            t = ges.ges_serve_submit(srv, ids[which[k]], ges.make_camera(cams[k]), out)
+            st, lat = ges.ges_serve_poll(srv, t, 30_000_000)
+            assert st == ges.GES_OK and lat > 0
+            assert np.abs(out - refs[k]).max() <= IMG_TOL
+        # in the mix: all at once, several batches, resolutions and scenes interleaved
+        outs = [np.empty((3, c.height, c.width), np.float32) for c in cams]
+        tickets = [ges.ges_serve_submit(srv, ids[w], ges.make_camera(c), o) for w, c, o in zip(which, cams, outs)]
+        for t, o, r in zip(tickets, outs, refs):
+            st, _ = ges.ges_serve_poll(srv, t, 30_000_000)
+            assert st == ges.GES_OK
+            assert np.abs(o - r).max() <= IMG_TOL
+    finally:
+        ges.ges_serve_destroy(srv)
+
+
+def test_poll_semantics_and_errors(ges):
+    srv, scs, ids, keep = _setup(ges, slots=2)
+    try:
+        cam = _cams(1, seed=7)[0]
+        out = np.empty((3, cam.height, cam.width), np.float32)
+        with pytest.raises(ges.GesError) as e:
+            ges.ges_serve_submit(srv, 99, ges.make_camera(cam), out)
+        assert e.value.status == ges.GES_ERR_INVALID_ARG
+        with pytest.raises(ges.GesError):
+            ges.ges_serve_poll(srv, 123456, 0)
+        t = ges.ges_serve_submit(srv, ids[0], ges.make_camera(cam), out)
+        st, _ = ges.ges_serve_poll(srv, t, 0)
+        assert st in (ges.GES_OK, ges.GES_ERR_NOT_READY)
+        if st != ges.GES_OK:
+            st, _ = ges.ges_serve_poll(srv, t, 30_000_000)
+        assert st == ges.GES_OK
+    finally:
+        ges.ges_serve_destroy(srv)
+
+
+def test_scenes_cannot_be_added_once_serving(ges):
+    srv, scs, ids, keep = _setup(ges, slots=1)
+    try:
+        cam = _cams(1, seed=8)[0]
+        out = np.empty((3, cam.height, cam.width), np.float32)
+        t = ges.ges_serve_submit(srv, ids[2], ges.make_camera(cam), out)
+        assert ges.ges_serve_poll(srv, t, 30_000_000)[0] == ges.GES_OK
+        hs, arrs = _host_scene(ges, scs[0])
+        with pytest.raises(ges.GesError) as e:
+            ges.ges_serve_add_scene(srv, hs)
+        assert e.value.status == ges.GES_ERR_BUSY
+    finally:
+        ges.ges_serve_destroy(srv)
+
+
+def test_workspace_too_small_fails_cleanly(ges):
+    from paper_2402_10128_gb300 import render
+    ctx = render.Context(0, hbm_budget_bytes=64 << 20)
+    srv = ges.ges_serve_create(ctx.handle, ges.params_default(), 2)
+    try:
+        sc = scenes.cube_scene(2000, seed=3, sh_degree=0)
+        hs, arrs = _host_scene(ges, sc)
+        sid = ges.ges_serve_add_scene(srv, hs)
+        cam = _cams(1, seed=9)[0]
+        out = np.empty((3, cam.height, cam.width), np.float32)
+        t = ges.ges_serve_submit(srv, sid, ges.make_camera(cam), out)
+        t0 = time.time()
+        with pytest.raises(ges.GesError) as e:
+            ges.ges_serve_poll(srv, t, 30_000_000)
+        assert e.value.status == ges.GES_ERR_OOM and time.time() - t0 < 30
+    finally:
+        ges.ges_serve_destroy(srv)
+        ctx.close()
