@@ -140,6 +140,14 @@ def run_reference(args, ws, rank):
     print(json.dumps(out))
 
 
+def sfu_rates():
+    """Measured MUFU rates (results per SM per clock) from the SFU microbenchmark."""
+    from paper_2402_10128_gb300 import build
+    exe = build.build_microbench()
+    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    return json.loads(out.strip().splitlines()[-1])
+
+
 def cpu_baseline(sc, cams, pixels, cores):
     import oracle
     rng = np.random.default_rng(1)
@@ -311,11 +319,11 @@ def main():
         probe.forward(t, sc.sh_degree, cam)
         if args.profile:
             Ks.append(int(ges.ges_frame_status(probe.handle)[1] * 1.3))
-            Fs.append((0, 0))
+            Fs.append((0, 0, 0))
         else:
-            ev, inr, K = ges.ges_frame_count_work(probe.handle)
+            ev, inr, comp, K = ges.ges_frame_count_work(probe.handle)
             Ks.append(K)
-            Fs.append((ev, inr))
+            Fs.append((ev, inr, comp))
     probe.close()
     del probe
     cap = int(max(Ks) * 1.05) + 4096
@@ -392,23 +400,40 @@ def main():
     fwd_rate = ws * pix * args.steps / (ms_f / 1e3) / 1e6
     st_mean = stage.mean(0)
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel: the composites are bound by the special-function unit
+    # (MUFU); its per-instruction rates are measured live by the SFU microbenchmark
     peaks, src = _peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     stage_names = ["preprocess", "bin_sort", "render_fwd", "render_bwd+preprocess_bwd"]
     dom = int(np.argmax(st_mean))
     mean_eval = float(np.mean([f[0] for f in Fs]))
     mean_inr = float(np.mean([f[1] for f in Fs]))
+    mean_comp = float(np.mean([f[2] for f in Fs]))
     mean_K = float(np.mean(Ks))
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    # forward composite: 3 MUFU ops (lg2, ex2, ex2) per in-extent (fragment, pixel) pair; 16 MUFU lanes/SM/clk
-    mufu_peak = nsm * 16 * sm_mhz * 1e6 / 1e12  # Tops/s
+    sfu = sfu_rates()
+    r_ex2, r_lg2, r_rcp = (sfu["per_sm_per_clk"][k] for k in ("ex2", "lg2", "rcp"))
+    clk = nsm * sm_mhz * 1e6
+
+    def mufu_roofline(kernel, ms, n_lg2, n_ex2, n_rcp, work):
+        ops = n_lg2 + n_ex2 + n_rcp
+        t_peak = (n_lg2 / r_lg2 + n_ex2 / r_ex2 + n_rcp / r_rcp) / clk  # seconds at the measured rates
+        peak = ops / t_peak / 1e12
+        achieved = ops / (ms / 1e3) / 1e12
+        return {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (MUFU)",
+                "frac": achieved / peak, "traffic": None, "work": work,
+                "peak_source": (f"{nsm} SMs x {sm_mhz:.0f} MHz ({src} max clock) x measured MUFU rates per SM per clock "
+                                f"(ex2 {r_ex2:.1f}, lg2 {r_lg2:.1f}, rcp {r_rcp:.1f}; sfu_rates microbenchmark) "
+                                f"weighted by the kernel's instruction mix")}
+
+    bwd_ms = float(st_mean[3])
     fwd_ms = float(st_mean[2])
-    achieved_mufu = 3.0 * mean_inr / (fwd_ms / 1e3) / 1e12
-    roofline = {"kernel": "k_render_fwd (forward composite)", "bound": "alu", "achieved": achieved_mufu,
-                "peak": mufu_peak, "unit": "Tops/s (MUFU)", "frac": achieved_mufu / mufu_peak, "traffic": None,
-                "work": f"3 MUFU x {mean_inr:.3e} in-extent (fragment,pixel) pairs per frame",
-                "peak_source": f"{nsm} SMs x 16 MUFU/clk x {sm_mhz:.0f} MHz ({src} max clock)"}
+    roofline = mufu_roofline("k_render_bwd + k_preprocess_bwd (backward; k_render_bwd is 94% of it)", bwd_ms,
+                             mean_inr, 2 * mean_inr, 2 * mean_comp,
+                             f"per frame: lg2 + 2 ex2 per in-extent pair ({mean_inr:.3e}) + 2 rcp per composited "
+                             f"pair ({mean_comp:.3e})")
+    roofline_fwd = mufu_roofline("k_render_fwd (forward composite)", fwd_ms, mean_inr, 2 * mean_inr, 0,
+                                 f"per frame: lg2 + 2 ex2 per in-extent pair ({mean_inr:.3e})")
     # preprocess: HBM bytes per primitive (read 240 B at SH3, write 68 B)
     pre_bytes = sc.n * (240 + 68)
     pre_gbs = pre_bytes / (float(st_mean[0]) / 1e3) / 1e9
@@ -425,8 +450,9 @@ def main():
            "fwd_mpix_s": fwd_rate, "fwd_ms_per_frame": ms_f / args.steps,
            "stage_ms": dict(zip(stage_names, [float(x) for x in st_mean])),
            "dominant_stage": stage_names[dom],
-           "frame_stats": {"K_mean": mean_K, "evaluated_pairs_mean": mean_eval, "in_extent_pairs_mean": mean_inr},
-           "roofline": roofline,
+           "frame_stats": {"K_mean": mean_K, "evaluated_pairs_mean": mean_eval, "in_extent_pairs_mean": mean_inr,
+                           "composited_pairs_mean": mean_comp},
+           "roofline": roofline, "roofline_fwd": roofline_fwd, "sfu_rates": sfu,
            "preprocess_hbm": {"achieved_gbs": pre_gbs, "peak_gbs": hbm, "frac": pre_gbs / hbm,
                               "bytes_per_prim": 308, "note": "includes the depth-key copy launch"},
            "gpu_launches": int(launches), "clocks": clocks}

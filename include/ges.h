@@ -179,10 +179,11 @@ ges_status ges_frame_inspect(ges_frame* frame, void* stream, uint32_t* depth_key
 
 /* Inspection.  Re-runs the forward composite of the last ges_bin_sort into internal scratch
    buffers while counting work, then synchronises `stream`: *evaluated receives the number of
-   (fragment, pixel) pairs composited or tested before each pixel stopped, *in_extent those whose
-   q was within the primitive's extent (the pairs that evaluate the falloff), *num_keys K. */
+   (fragment, pixel) pairs tested before each pixel stopped, *in_extent those whose q was within
+   the primitive's extent (the pairs that evaluate the falloff), *composited those that were
+   composited (alpha >= alpha_min), *num_keys K.  Any output pointer may be NULL. */
 ges_status ges_frame_count_work(ges_frame* frame, void* stream, int64_t* evaluated, int64_t* in_extent,
-                                int64_t* num_keys);
+                                int64_t* composited, int64_t* num_keys);
 
 /* Number of CUDA kernels this process has launched through libges (all threads). */
 uint64_t ges_kernel_launches(void);

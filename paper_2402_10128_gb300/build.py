@@ -66,5 +66,21 @@ def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
     return LIB
 
 
+MICROBENCH = os.path.join(OUT, "sfu_rates")
+
+
+def build_microbench() -> str:
+    """The SFU-rate microbenchmark (paper_2402_10128_gb300/microbench/sfu_rates.cu)."""
+    os.makedirs(OUT, exist_ok=True)
+    src = os.path.join(PKG, "microbench", "sfu_rates.cu")
+    if not os.path.exists(MICROBENCH) or os.path.getmtime(MICROBENCH) < os.path.getmtime(src):
+        tmp = MICROBENCH + f".tmp{os.getpid()}"
+        r = subprocess.run([_nvcc(), *ARCH, "-O3", src, "-o", tmp], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("nvcc failed for the SFU microbenchmark:\n" + r.stdout + r.stderr)
+        os.replace(tmp, MICROBENCH)
+    return MICROBENCH
+
+
 if __name__ == "__main__":
     print(build(verbose=True))

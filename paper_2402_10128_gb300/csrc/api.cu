@@ -294,7 +294,7 @@ void ges_frame_destroy(ges_frame* f) {
   ctx_free(c, f->d_flags, 4);
   frame_free_keys(f);
   ctx_free(c, f->work_img, sizeof(float) * 5 * (size_t)f->W * f->H);
-  ctx_free(c, f->work_stats, 16);
+  ctx_free(c, f->work_stats, 32);
   if (f->h_K) cudaFreeHost(f->h_K);
   delete f;
 }
@@ -483,7 +483,8 @@ ges_status ges_frame_inspect(ges_frame* f, void* stream, uint32_t* depth_key, in
 
 uint64_t ges_kernel_launches(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
 
-ges_status ges_frame_count_work(ges_frame* f, void* stream, int64_t* evaluated, int64_t* in_extent, int64_t* num_keys) {
+ges_status ges_frame_count_work(ges_frame* f, void* stream, int64_t* evaluated, int64_t* in_extent, int64_t* composited,
+                                int64_t* num_keys) {
   if (!f) return fail(GES_ERR_INVALID_ARG, "frame is NULL");
   if (!f->have_sort) return fail(GES_ERR_INVALID_ARG, "no sorted keys yet");
   ges_status st = use_device(f->ctx->device);
@@ -492,20 +493,21 @@ ges_status ges_frame_count_work(ges_frame* f, void* stream, int64_t* evaluated, 
   const size_t npx = (size_t)f->W * f->H;
   if (!f->work_img) {
     if ((st = ctx_alloc(f->ctx, (void**)&f->work_img, sizeof(float) * 5 * npx)) != GES_OK) return st;
-    if ((st = ctx_alloc(f->ctx, (void**)&f->work_stats, 16)) != GES_OK) return st;
+    if ((st = ctx_alloc(f->ctx, (void**)&f->work_stats, 32)) != GES_OK) return st;
   }
   FrameViews vt = f->vt;
   vt.t.v[0].img = f->work_img;
   vt.t.v[0].final_T = f->work_img + 3 * npx;
   vt.t.v[0].n_contrib = reinterpret_cast<uint32_t*>(f->work_img + 4 * npx);
   cudaError_t e;
-  if ((e = cudaMemsetAsync(f->work_stats, 0, 16, s)) != cudaSuccess) return cuda_fail(e, "memset stats");
+  if ((e = cudaMemsetAsync(f->work_stats, 0, 32, s)) != cudaSuccess) return cuda_fail(e, "memset stats");
   launch_render_fwd<FrameViews>(vt, f->n_tiles, f->ranges, f->tile_vals, f->rec, f->P, s, f->work_stats);
-  unsigned long long h[2] = {0, 0};
-  if ((e = cudaMemcpyAsync(h, f->work_stats, 16, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(e, "copy stats");
+  unsigned long long h[3] = {0, 0, 0};
+  if ((e = cudaMemcpyAsync(h, f->work_stats, 24, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(e, "copy stats");
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "sync");
   if (evaluated) *evaluated = (int64_t)h[0];
   if (in_extent) *in_extent = (int64_t)h[1];
+  if (composited) *composited = (int64_t)h[2];
   return ges_frame_status(f, stream, num_keys);
 }
 

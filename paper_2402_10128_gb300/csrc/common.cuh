@@ -2,7 +2,6 @@
 // projected-primitive record, and the fixed-order FP32 arithmetic of the key path.
 #pragma once
 
-#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -104,8 +103,7 @@ struct Params {
 // Projected primitive as the compositing kernels read it (48 bytes, gathered by id).
 //   a = (mean x, mean y, q limit, beta exponent hb)    hb = beta/2 (GEF) or 1
 //   b = (conic a, conic b, conic c, opacity)            q = a dx^2 + 2 b dx dy + c dy^2
-//   c = (r, g, b, extent)   extent = two fp16 half-widths (x, y) of the primitive's screen box,
-//                           rounded up, packed in the 32 bits of c.w
+//   c = (r, g, b, 0)
 struct __align__(16) Rec {
   float4 a, b, c;
 };
@@ -132,22 +130,6 @@ struct FragEval {
   float dx, dy, q, p, G, alpha, lq;  // lq = log2 q (GEF exponent path only)
   bool in_range, clamped;
 };
-
-__device__ __forceinline__ float pack_extent(float hx, float hy) {
-  __half2 h = __halves2half2(__float2half_ru(hx), __float2half_ru(hy));
-  return *reinterpret_cast<float*>(&h);
-}
-__device__ __forceinline__ float2 unpack_extent(float w) {
-  __half2 h = *reinterpret_cast<__half2*>(&w);
-  return __half22float2(h);
-}
-
-// Does the primitive's screen box meet the block of pixel centres [x0,x1] x [y0,y1]?  Pixels
-// outside the box have q above the q limit, so skipping the block changes nothing.
-__device__ __forceinline__ bool box_meets_block(const Rec& r, float x0, float x1, float y0, float y1) {
-  const float2 h = unpack_extent(r.c.w);
-  return r.a.x + h.x >= x0 && r.a.x - h.x <= x1 && r.a.y + h.y >= y0 && r.a.y - h.y <= y1;
-}
 
 // q = d^T conic d with d = pixel - mean; p = q^hb; G = exp(-p/2); alpha = min(alpha_max, kappa G)
 __device__ __forceinline__ void eval_fragment(const Rec& r, float px, float py, float alpha_max, FragEval& f) {

@@ -21,13 +21,16 @@ void set_key_constants(cudaStream_t s);
 
 // ---- binning (sort.cu)
 struct ScanScratch {
-  void* buf = nullptr;   // device scratch for multi-level scans
+  void* buf = nullptr;   // device scratch for multi-level scans; the first kReserved bytes hold counters
   size_t bytes = 0;
+  static constexpr size_t kReserved = 256;
   static size_t required(int64_t max_n);
 };
-// exclusive prefix sum of n elements (in may equal out); *total (device, optional) gets the sum
+// exclusive prefix sum of n elements (in may equal out); *total (device, optional) gets the sum.
+// With n_dev, the element count is min(*n_dev, n) (n is then the capacity).
 template <typename TIn, typename TOut>
-void scan_exclusive(const TIn* in, TOut* out, int64_t n, TOut* total, ScanScratch& sc, cudaStream_t s);
+void scan_exclusive(const TIn* in, TOut* out, int64_t n, TOut* total, ScanScratch& sc, cudaStream_t s,
+                    const unsigned long long* n_dev = nullptr);
 
 // per-primitive tile counts in depth order: touched[j] = area(rect[sorted_vals[j]]) for j < count,
 // 0 for count <= j < n (count = *n_dev if given, else n)
@@ -41,10 +44,11 @@ void radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_
                       int64_t n_cap, int total_bits, uint32_t* hist, int64_t hist_cap, ScanScratch& sc, cudaStream_t s);
 int64_t radix_hist_entries(int64_t n_cap, int total_bits);
 
+// n: primitives (the capacity when n_dev gives the count on the device)
 template <class VS>
 void launch_keygen(const VS& vs, const unsigned long long* offsets, const unsigned long long* K_dev,
                    int64_t n, const uint32_t* sorted_vals, const ushort4* rect, int64_t cap, uint32_t* tile_keys,
-                   uint32_t* tile_vals, uint32_t* flags, cudaStream_t s);
+                   uint32_t* tile_vals, uint32_t* flags, cudaStream_t s, const unsigned long long* n_dev = nullptr);
 void launch_ranges(const uint32_t* tile_keys, const unsigned long long* K_dev, int64_t cap, uint2* ranges, int num_sms,
                    cudaStream_t s);
 // materialise the 64-bit keys (tile << 32 | depth key) of a sorted list (inspection only)

@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ VS v
     Rec r;
     r.a = make_float4(u, v, kmul(kmul(qs, onep), onep), P.mode == 0 ? 0.5f * beta : 1.0f);
     r.b = make_float4(cc * idet, -cb * idet, ca * idet, kappa);
-    r.c = make_float4(col.x, col.y, col.z, pack_extent(hx, hy));
+    r.c = make_float4(col.x, col.y, col.z, 0.f);
     rec[g] = r;
   }
 }

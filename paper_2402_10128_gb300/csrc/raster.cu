@@ -5,12 +5,12 @@
 // with alpha_i = min(alpha_max, kappa_i G_i) and the GES falloff G = exp(-1/2 q^(beta/2))
 // (Sec. 3.1, Eq. ges) or the paper's Gaussian-form rasterizer G = exp(-1/2 q).
 //
-// One CTA of 128 threads per 16x16 tile; each thread owns two pixels, (x, y) and (x, y + 4),
-// so a warp covers an 8x8 block.  The tile's list is staged in shared memory 128 records at a
-// time.  Before any per-pixel work a warp tests the record's screen box against its 8x8 block
-// and skips the fragment for all 64 pixels when they do not meet (pixels outside the box are
-// beyond the primitive's extent).  Forward and backward share this mapping and the arithmetic
-// of eval_fragment, so they take the same skip / clamp / stop decisions bit for bit.
+// Forward: one CTA of 256 threads per 16x16 tile, one pixel per thread, warps on 8x4 blocks.
+// Backward: one CTA of 128 threads per tile, two pixels per thread, (x, y) and (x, y + 4), so a
+// warp covers an 8x8 block and its per-fragment gradient sum is shared by 64 pixels.  The tile's
+// list is staged in shared memory one record per thread per round.  Both kernels evaluate every
+// (fragment, pixel) pair with eval_fragment, so they take the same skip / clamp / stop decisions
+// bit for bit whatever their thread layout.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -18,25 +18,28 @@ namespace ges {
 
 namespace {
 
-constexpr int kThreads = 128;  // per tile
+constexpr int kThreads = 128;  // backward, per tile
 constexpr int kBatch = kThreads;
+constexpr int kFwdThreads = 256;
+constexpr int kFwdBatch = kFwdThreads;
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 struct WarpBlock {
-  int x, y;                    // first pixel of this thread
-  float bx0, bx1, by0, by1;    // pixel-centre bounds of the warp's 8x8 block
+  int x, y;  // first pixel of this thread (the second is at y + 4)
 };
 
+// backward layout: warp w of the tile covers the 8x8 block at ((w & 1) * 8, (w >> 1) * 8)
 __device__ __forceinline__ WarpBlock warp_block(int lt, int tiles_x) {
   const int tx = lt % tiles_x, ty = lt / tiles_x;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   WarpBlock b;
-  const int ox = tx * kTile + (w & 1) * 8, oy = ty * kTile + (w >> 1) * 8;
-  b.x = ox + (lane & 7);
-  b.y = oy + (lane >> 3);
-  b.bx0 = (float)ox + 0.5f;
-  b.bx1 = (float)ox + 7.5f;
-  b.by0 = (float)oy + 0.5f;
-  b.by1 = (float)oy + 7.5f;
+  b.x = tx * kTile + (w & 1) * 8 + (lane & 7);
+  b.y = ty * kTile + (w >> 1) * 8 + (lane >> 3);
   return b;
 }
 
@@ -46,100 +49,84 @@ __device__ __forceinline__ void render_tile_fwd(const ViewTable<MAXV>& vt, int64
                                                 const Rec* __restrict__ rec, const Params& P,
                                                 unsigned long long* __restrict__ stats) {
   const ViewDesc& vd = vt.v[view_of_tile(vt, tile)];
-  const WarpBlock wb = warp_block((int)(tile - vd.tile_base), vd.tiles_x);
+  const int lt = (int)(tile - vd.tile_base);
+  const int tx = lt % vd.tiles_x, ty = lt / vd.tiles_x;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int x = tx * kTile + (w & 1) * 8 + (lane & 7);
+  const int y = ty * kTile + (w >> 1) * 4 + (lane >> 3);
+  const bool inside = x < vd.W && y < vd.H;
+  const float px = (float)x + 0.5f, py = (float)y + 0.5f;
   const uint2 rg = ranges[tile];
-
-  float px[2], py[2], T[2], C0[2], C1[2], C2[2];
-  uint32_t last[2];
-  bool inside[2], done[2];
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const int y = wb.y + 4 * k;
-    inside[k] = wb.x < vd.W && y < vd.H;
-    done[k] = !inside[k];
-    px[k] = (float)wb.x + 0.5f;
-    py[k] = (float)y + 0.5f;
-    T[k] = 1.0f;
-    C0[k] = C1[k] = C2[k] = 0.f;
-    last[k] = 0;
-  }
-  uint32_t n_eval = 0, n_range = 0;
-  for (uint32_t base = rg.x; base < rg.y; base += kBatch) {
-    if (__syncthreads_count(done[0] && done[1]) == kThreads) break;
+  float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+  uint32_t last = 0, n_eval = 0, n_range = 0, n_comp = 0;
+  bool done = !inside;
+  for (uint32_t base = rg.x; base < rg.y; base += kFwdBatch) {
+    if (__syncthreads_count(done) == kFwdThreads) break;
     const uint32_t idx = base + threadIdx.x;
     if (idx < rg.y) batch[threadIdx.x] = rec[vals[idx]];
     __syncthreads();
-    const int cnt = (int)min((uint32_t)kBatch, rg.y - base);
-    for (int j = 0; j < cnt; ++j) {
-      if (__all_sync(0xffffffffu, done[0] && done[1])) break;
-      const Rec r = batch[j];
-      if (!box_meets_block(r, wb.bx0, wb.bx1, wb.by0, wb.by1)) continue;  // warp-uniform
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        if (done[k]) continue;
+    const int cnt = (int)min((uint32_t)kFwdBatch, rg.y - base);
+    if (!__all_sync(0xffffffffu, done)) {
+      for (int j = 0; j < cnt; ++j) {
+        if (done) break;
+        const Rec r = batch[j];
         FragEval f;
-        eval_fragment(r, px[k], py[k], P.alpha_max, f);
-        if (STATS) {
-          ++n_eval;
-          n_range += f.in_range ? 1u : 0u;
-        }
+        eval_fragment(r, px, py, P.alpha_max, f);
+        if (STATS) { ++n_eval; n_range += f.in_range ? 1u : 0u; }
         if (f.alpha < P.alpha_min) continue;
-        const float Tn = T[k] * (1.0f - f.alpha);
-        if (Tn < P.t_min) {
-          done[k] = true;
-          continue;
-        }
-        const float w = f.alpha * T[k];
-        C0[k] = fmaf(r.c.x, w, C0[k]);
-        C1[k] = fmaf(r.c.y, w, C1[k]);
-        C2[k] = fmaf(r.c.z, w, C2[k]);
-        T[k] = Tn;
-        last[k] = base - rg.x + (uint32_t)j + 1u;
+        const float Tn = T * (1.0f - f.alpha);
+        if (Tn < P.t_min) { done = true; break; }
+        const float wgt = f.alpha * T;
+        C0 = fmaf(r.c.x, wgt, C0);
+        C1 = fmaf(r.c.y, wgt, C1);
+        C2 = fmaf(r.c.z, wgt, C2);
+        T = Tn;
+        last = base - rg.x + (uint32_t)j + 1u;
+        if (STATS) ++n_comp;
       }
     }
   }
-  const int64_t plane = (int64_t)vd.W * vd.H;
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    if (!inside[k]) continue;
-    const int64_t pix = (int64_t)(wb.y + 4 * k) * vd.W + wb.x;
-    vd.img[pix] = C0[k] + T[k] * vd.bg[0];
-    vd.img[plane + pix] = C1[k] + T[k] * vd.bg[1];
-    vd.img[2 * plane + pix] = C2[k] + T[k] * vd.bg[2];
-    vd.final_T[pix] = T[k];
-    vd.n_contrib[pix] = last[k];
+  if (inside) {
+    const int64_t pix = (int64_t)y * vd.W + x, plane = (int64_t)vd.W * vd.H;
+    vd.img[pix] = C0 + T * vd.bg[0];
+    vd.img[plane + pix] = C1 + T * vd.bg[1];
+    vd.img[2 * plane + pix] = C2 + T * vd.bg[2];
+    vd.final_T[pix] = T;
+    vd.n_contrib[pix] = last;
   }
   if (STATS) {
-    unsigned long long a = n_eval, b = n_range;
+    unsigned long long a = n_eval, b = n_range, c = n_comp;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       a += __shfl_xor_sync(0xffffffffu, a, o);
       b += __shfl_xor_sync(0xffffffffu, b, o);
+      c += __shfl_xor_sync(0xffffffffu, c, o);
     }
     if ((threadIdx.x & 31) == 0) {
       atomicAdd(stats, a);
       atomicAdd(stats + 1, b);
+      atomicAdd(stats + 2, c);
     }
   }
 }
 
 template <class VS, bool STATS>
-__global__ void __launch_bounds__(kThreads) k_render_fwd(const __grid_constant__ VS vs, const uint2* __restrict__ ranges,
+__global__ void __launch_bounds__(kFwdThreads) k_render_fwd(const __grid_constant__ VS vs, const uint2* __restrict__ ranges,
                                                          const uint32_t* __restrict__ vals, const Rec* __restrict__ rec,
                                                          const Params P, unsigned long long* __restrict__ stats) {
-  __shared__ Rec batch[kBatch];
+  __shared__ Rec batch[kFwdBatch];
   render_tile_fwd<VS::kMax, STATS>(vs.get(), (int64_t)blockIdx.x, batch, ranges, vals, rec, P, stats);
 }
 
 // Persistent form: CTAs take tiles from a work counter until the table's total_tiles are done, so
 // a fixed grid serves batches of any size (the launch can be replayed from a captured graph).
 template <class VS>
-__global__ void __launch_bounds__(kThreads) k_render_fwd_persistent(const __grid_constant__ VS vs,
+__global__ void __launch_bounds__(kFwdThreads) k_render_fwd_persistent(const __grid_constant__ VS vs,
                                                                     const uint2* __restrict__ ranges,
                                                                     const uint32_t* __restrict__ vals,
                                                                     const Rec* __restrict__ rec, const Params P,
                                                                     unsigned int* __restrict__ tile_counter) {
-  __shared__ Rec batch[kBatch];
+  __shared__ Rec batch[kFwdBatch];
   __shared__ unsigned int s_tile;
   const auto& vt = vs.get();
   const long long total = vt.total_tiles;
@@ -180,7 +167,8 @@ __device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16]) {
 //   dG/dp = -G/2,  p = q^hb:  dp/dq = hb p / q,  dp/dhb = p ln q  (0 for q < 1e-12)
 //   q = a dx^2 + 2 b dx dy + c dy^2, dx = px - mx
 // A thread sums its two pixels' terms, the warp sums by a reduce-scatter butterfly, and ten lanes
-// add the ten per-primitive sums with one atomic each.
+// add the ten per-primitive sums with one atomic each.  Reciprocals use the approximate MUFU
+// instruction (about 1 ulp); they only scale gradients, never decide a branch.
 template <class VS>
 __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__ VS vs, const uint2* __restrict__ ranges,
                                                          const uint32_t* __restrict__ vals, const Rec* __restrict__ rec,
@@ -241,7 +229,6 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
       const uint32_t kpos = start - rg.x + (uint32_t)j + 1u;  // 1-based position in the tile's list
       if (kpos > wlast) continue;                             // beyond every pixel of this warp
       const Rec r = batch[j];
-      if (!box_meets_block(r, wb.bx0, wb.bx1, wb.by0, wb.by1)) continue;  // warp-uniform
       float g[16];
 #pragma unroll
       for (int t = 0; t < 16; ++t) g[t] = 0.f;
@@ -253,7 +240,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
         eval_fragment(r, px[k], py[k], P.alpha_max, f);
         if (f.alpha < P.alpha_min) continue;
         contrib = true;
-        const float inv = __frcp_rn(1.0f - f.alpha);
+        const float inv = rcp_approx(1.0f - f.alpha);
         T[k] *= inv;
         const float w = f.alpha * T[k];
         const float dLda = gC0[k] * (r.c.x * T[k] - S0[k] * inv) + gC1[k] * (r.c.y * T[k] - S1[k] * inv) +
@@ -274,7 +261,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
               dq = dp;
               g[6] += dp * f.q * (mufu_lg2(f.q) * ln2);
             } else {
-              dq = dp * r.a.w * f.p * __frcp_rn(f.q);
+              dq = dp * r.a.w * f.p * rcp_approx(f.q);
               g[6] += dp * f.p * (f.lq * ln2);
             }
           } else {
@@ -309,14 +296,14 @@ void launch_render_fwd(const VS& vs, int64_t total_tiles, const uint2* ranges, c
   if (total_tiles <= 0) return;
   if (tile_counter) {
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_fwd_persistent<VS>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_fwd_persistent<VS>, kFwdThreads, 0);
     const int64_t grid = (int64_t)num_sms * (per_sm > 0 ? per_sm : 1);
-    k_render_fwd_persistent<VS><<<(unsigned)(grid < total_tiles ? grid : total_tiles), kThreads, 0, s>>>(
+    k_render_fwd_persistent<VS><<<(unsigned)(grid < total_tiles ? grid : total_tiles), kFwdThreads, 0, s>>>(
         vs, ranges, vals, rec, P, tile_counter);
   } else if (stats) {
-    k_render_fwd<VS, true><<<(unsigned)total_tiles, kThreads, 0, s>>>(vs, ranges, vals, rec, P, stats);
+    k_render_fwd<VS, true><<<(unsigned)total_tiles, kFwdThreads, 0, s>>>(vs, ranges, vals, rec, P, stats);
   } else {
-    k_render_fwd<VS, false><<<(unsigned)total_tiles, kThreads, 0, s>>>(vs, ranges, vals, rec, P, nullptr);
+    k_render_fwd<VS, false><<<(unsigned)total_tiles, kFwdThreads, 0, s>>>(vs, ranges, vals, rec, P, nullptr);
   }
   count_launches(1);
 }

@@ -34,8 +34,18 @@ __device__ __forceinline__ T warp_inclusive_scan(T v) {
 }
 
 // ---------------------------------------------------------------- scan kernels
+// element count of a scan: min(*n_dev, cap) when a device count is given, else cap
+__device__ __forceinline__ int64_t scan_count(int64_t cap, const unsigned long long* n_dev) {
+  if (!n_dev) return cap;
+  const unsigned long long n = *n_dev;
+  return n < (unsigned long long)cap ? (int64_t)n : cap;
+}
+
 template <typename TIn, typename TOut>
-__global__ void __launch_bounds__(kThreads) k_scan_reduce(const TIn* __restrict__ in, int64_t n, TOut* __restrict__ sums) {
+__global__ void __launch_bounds__(kThreads) k_scan_reduce(const TIn* __restrict__ in, int64_t cap,
+                                                          const unsigned long long* __restrict__ n_dev,
+                                                          TOut* __restrict__ sums) {
+  const int64_t n = scan_count(cap, n_dev);
   const int64_t base = (int64_t)blockIdx.x * kChunk + (int64_t)threadIdx.x * kItems;
   TOut acc = 0;
 #pragma unroll
@@ -55,8 +65,11 @@ __global__ void __launch_bounds__(kThreads) k_scan_reduce(const TIn* __restrict_
 
 // exclusive scan of one chunk per CTA plus a per-CTA offset (block_off may be null)
 template <typename TIn, typename TOut>
-__global__ void __launch_bounds__(kThreads) k_scan_down(const TIn* __restrict__ in, TOut* __restrict__ out, int64_t n,
+__global__ void __launch_bounds__(kThreads) k_scan_down(const TIn* __restrict__ in, TOut* __restrict__ out, int64_t cap,
+                                                        const unsigned long long* __restrict__ n_dev,
                                                         const TOut* __restrict__ block_off, TOut* __restrict__ total) {
+  const int64_t n = scan_count(cap, n_dev);
+  if ((int64_t)blockIdx.x * kChunk >= n && !(total && gridDim.x == 1)) return;  // idle CTA past the count
   const int64_t base = (int64_t)blockIdx.x * kChunk + (int64_t)threadIdx.x * kItems;
   TOut v[kItems];
   TOut acc = 0;
@@ -84,8 +97,8 @@ __global__ void __launch_bounds__(kThreads) k_scan_down(const TIn* __restrict__ 
     if (base + k < n) out[base + k] = run;
     run += v[k];
   }
-  if (total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0)
-    *total = (block_off ? block_off[blockIdx.x] : TOut(0)) + ws[kThreads / 32];
+  // single-block scans report the total here; multi-level scans get it from the level above
+  if (total && gridDim.x == 1 && threadIdx.x == 0) *total = ws[kThreads / 32];
 }
 
 // ---------------------------------------------------------------- radix kernels
@@ -97,24 +110,22 @@ __device__ __forceinline__ int64_t element_count(int64_t n_host, const unsigned 
   return n > (unsigned long long)cap ? 0 : (int64_t)n;
 }
 
+// hist layout: [bin][chunk] over the active chunks (ceil(count / kChunk)); the matrix size goes to
+// *entries (device) for the scan that follows
 __global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restrict__ keys, int64_t n_host,
                                                          const unsigned long long* __restrict__ n_dev, int64_t cap,
-                                                         int shift, int bits,
-                                                         uint32_t* __restrict__ hist, int64_t nchunks) {
+                                                         int shift, int bits, uint32_t* __restrict__ hist,
+                                                         unsigned long long* __restrict__ entries) {
   constexpr int kWarps = kThreads / 32;
   __shared__ uint32_t cnt[kWarps][256];  // one private histogram per warp: less atomic contention
   const int nbins = 1 << bits;
   const int64_t n = element_count(n_host, n_dev, cap);
   const uint32_t mask = (uint32_t)nbins - 1u;
   const int w = threadIdx.x >> 5;
-  // every column of the [bin][chunk] matrix is written (zeros past the element count), so the
-  // following scan over the whole matrix is correct for any count up to the capacity
+  const int64_t nchunks = (n + kChunk - 1) / kChunk;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *entries = (unsigned long long)nbins * (unsigned long long)nchunks;
   for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
     const int64_t base = c * kChunk;
-    if (base >= n) {
-      for (int b = threadIdx.x; b < nbins; b += kThreads) hist[(int64_t)b * nchunks + c] = 0;
-      continue;
-    }
     __syncthreads();
     for (int i = threadIdx.x; i < kWarps * 256; i += kThreads) (&cnt[0][0])[i] = 0;
     __syncthreads();
@@ -149,15 +160,17 @@ __global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restr
 // preserve input order within each digit.  The chunk is first reordered by digit in shared
 // memory, then written out so that consecutive threads store consecutive positions of one
 // digit's run (coalesced).
-__global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __restrict__ keys_in,
+constexpr int kScThreads = 512;                 // scatter CTA: twice the warps of the other kernels
+constexpr int kScItems = kChunk / kScThreads;   // 8 items per thread, same chunk
+
+__global__ void __launch_bounds__(kScThreads) k_radix_scatter(const uint32_t* __restrict__ keys_in,
                                                             const uint32_t* __restrict__ vals_in,
                                                             uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
                                                             int64_t n_host, const unsigned long long* __restrict__ n_dev,
                                                             int64_t cap, int shift, int bits,
-                                                            const uint32_t* __restrict__ hist_scanned,
-                                                            int64_t nchunks) {
-  constexpr int kWarps = kThreads / 32;
-  __shared__ uint32_t wcnt[kWarps][257];
+                                                            const uint32_t* __restrict__ hist_scanned) {
+  constexpr int kWarps = kScThreads / 32;
+  __shared__ uint16_t wcnt[kWarps][257];  // per warp and digit: at most 256 items, prefixes at most kChunk
   __shared__ uint32_t goff[256];
   __shared__ uint32_t bstart[257];
   __shared__ uint32_t wsum[kWarps];
@@ -166,20 +179,21 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
   const int nbins = 1 << bits;
   const uint32_t mask = (uint32_t)nbins - 1u;
   const int64_t n = element_count(n_host, n_dev, cap);
+  const int64_t nchunks = (n + kChunk - 1) / kChunk;
   const int w = threadIdx.x >> 5;
   const unsigned lane = lane_id();
   for (int64_t c = blockIdx.x; c * kChunk < n; c += gridDim.x) {
   const int64_t base = c * kChunk;
   const int count = (int)min((int64_t)kChunk, n - base);
   __syncthreads();  // the previous chunk's readers of the shared arrays are done
-  for (int i = threadIdx.x; i < kWarps * 257; i += kThreads) (&wcnt[0][0])[i] = 0;
-  for (int b = threadIdx.x; b < nbins; b += kThreads) goff[b] = hist_scanned[(int64_t)b * nchunks + c];
+  for (int i = threadIdx.x; i < kWarps * 257; i += kScThreads) (&wcnt[0][0])[i] = 0;
+  for (int b = threadIdx.x; b < nbins; b += kScThreads) goff[b] = hist_scanned[(int64_t)b * nchunks + c];
   __syncthreads();
   const unsigned lt_mask = (1u << lane) - 1u;
-  uint32_t key[kItems], val[kItems], rank[kItems];
+  uint32_t key[kScItems], val[kScItems], rank[kScItems];
 #pragma unroll
-  for (int r = 0; r < kItems; ++r) {
-    const int li = w * (kItems * 32) + r * 32 + (int)lane;
+  for (int r = 0; r < kScItems; ++r) {
+    const int li = w * (kScItems * 32) + r * 32 + (int)lane;
     const bool ok = li < count;
     key[r] = ok ? keys_in[base + li] : 0u;
     val[r] = ok ? vals_in[base + li] : 0u;
@@ -187,7 +201,7 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     const uint32_t prev = wcnt[w][d];
     __syncwarp();
-    if ((peers & lt_mask) == 0) wcnt[w][d] = prev + (uint32_t)__popc(peers);
+    if ((peers & lt_mask) == 0) wcnt[w][d] = (uint16_t)(prev + (uint32_t)__popc(peers));
     __syncwarp();
     rank[r] = prev + (uint32_t)__popc(peers & lt_mask);
   }
@@ -198,9 +212,9 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
     const int b = threadIdx.x;
 #pragma unroll
     for (int ww = 0; ww < kWarps; ++ww) {
-      uint32_t c = wcnt[ww][b];
-      wcnt[ww][b] = total;
-      total += c;
+      uint32_t cw = wcnt[ww][b];
+      wcnt[ww][b] = (uint16_t)total;
+      total += cw;
     }
   }
   // exclusive scan of the digit totals over the CTA (thread b holds digit b)
@@ -225,8 +239,8 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
   __syncthreads();
   // reorder the chunk by digit in shared memory
 #pragma unroll
-  for (int r = 0; r < kItems; ++r) {
-    const int li = w * (kItems * 32) + r * 32 + (int)lane;
+  for (int r = 0; r < kScItems; ++r) {
+    const int li = w * (kScItems * 32) + r * 32 + (int)lane;
     if (li < count) {
       const int d = (int)((key[r] >> shift) & mask);
       const uint32_t pos = bstart[d] + wcnt[w][d] + rank[r];
@@ -235,7 +249,7 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < count; i += kThreads) {
+  for (int i = threadIdx.x; i < count; i += kScThreads) {
     const uint32_t k = skeys[i];
     const int d = (int)((k >> shift) & mask);
     const uint32_t gpos = goff[d] + ((uint32_t)i - bstart[d]);
@@ -267,7 +281,8 @@ constexpr int kKeygenEntries = 2048;
 template <class VS>
 __global__ void __launch_bounds__(kThreads) k_keygen(const __grid_constant__ VS vs,
                                                      const unsigned long long* __restrict__ offsets,
-                                                     const unsigned long long* __restrict__ K_dev, int64_t n,
+                                                     const unsigned long long* __restrict__ K_dev, int64_t n_cap,
+                                                     const unsigned long long* __restrict__ n_dev,
                                                      const uint32_t* __restrict__ sorted_vals,
                                                      const ushort4* __restrict__ rect, int64_t cap,
                                                      uint32_t* __restrict__ tile_keys, uint32_t* __restrict__ tile_vals,
@@ -275,6 +290,7 @@ __global__ void __launch_bounds__(kThreads) k_keygen(const __grid_constant__ VS 
   __shared__ uint32_t win[kKeygenEntries + 2];
   __shared__ int64_t s_jlo, s_jhi;
   const auto& vt = vs.get();
+  const int64_t n = scan_count(n_cap, n_dev);
   const unsigned long long K = *K_dev;
   if ((int64_t)K > cap) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(flags, kFlagOverflow);
@@ -301,35 +317,88 @@ __global__ void __launch_bounds__(kThreads) k_keygen(const __grid_constant__ VS 
     win[k] = (uint32_t)((o > (unsigned long long)e0 ? o : (unsigned long long)e0) - (unsigned long long)e0);
   }
   __syncthreads();
-  for (int64_t e = e0 + threadIdx.x; e < e1; e += kThreads) {
-    const uint32_t rel = (uint32_t)(e - e0);
+  // each thread emits a run of kRun consecutive entries: one search for the run's first primitive,
+  // then a walk over the tiles (no division per entry) and 16-byte stores
+  constexpr int kRun = kKeygenEntries / kThreads;
+  const int64_t ea = e0 + (int64_t)threadIdx.x * kRun;
+  if (ea < e1) {
+    const int cnt = (int)min((int64_t)kRun, e1 - ea);
+    const uint32_t rel = (uint32_t)(ea - e0);
     int lo = 0, hi = wn - 1;  // last k with win[k] <= rel
     while (lo < hi) {
       int mid = (lo + hi + 1) >> 1;
       if (win[mid] <= rel) lo = mid; else hi = mid - 1;
     }
-    const int64_t j = jlo + lo;
-    const uint32_t g = sorted_vals[j];
-    const uint32_t local = (uint32_t)(e - (int64_t)offsets[j]);
-    const ushort4 r = rect[g];
-    const uint32_t rw = (uint32_t)(r.z - r.x);
-    const uint32_t tyy = local / rw, txx = local - tyy * rw;
-    const ViewDesc& vd = vt.v[view_of_prim(vt, (int64_t)g)];
-    tile_keys[e] = (uint32_t)vd.tile_base + ((uint32_t)r.y + tyy) * (uint32_t)vd.tiles_x + (uint32_t)r.x + txx;
-    tile_vals[e] = g;
+    int64_t j = jlo + lo;
+    uint32_t g = sorted_vals[j];
+    ushort4 r = rect[g];
+    uint32_t rw = (uint32_t)(r.z - r.x), area = rw * (uint32_t)(r.w - r.y);
+    uint32_t local = (uint32_t)(ea - (int64_t)offsets[j]);
+    uint32_t ly = local / rw, lx = local - ly * rw;
+    const ViewDesc* vd = &vt.v[view_of_prim(vt, (int64_t)g)];
+    uint32_t kk[kRun], vv[kRun];
+#pragma unroll
+    for (int q = 0; q < kRun; ++q) {
+      kk[q] = (uint32_t)vd->tile_base + ((uint32_t)r.y + ly) * (uint32_t)vd->tiles_x + (uint32_t)r.x + lx;
+      vv[q] = g;
+      if (q + 1 < cnt) {
+        ++local;
+        if (++lx == rw) {
+          lx = 0;
+          ++ly;
+        }
+        if (local == area) {  // the run continues with the next primitive in depth order
+          g = sorted_vals[++j];
+          r = rect[g];
+          rw = (uint32_t)(r.z - r.x);
+          area = rw * (uint32_t)(r.w - r.y);
+          local = lx = ly = 0;
+          vd = &vt.v[view_of_prim(vt, (int64_t)g)];
+        }
+      }
+    }
+    if (cnt == kRun) {
+      uint4* tk4 = reinterpret_cast<uint4*>(tile_keys + ea);
+      uint4* tv4 = reinterpret_cast<uint4*>(tile_vals + ea);
+#pragma unroll
+      for (int q = 0; q < kRun / 4; ++q) {
+        tk4[q] = make_uint4(kk[4 * q], kk[4 * q + 1], kk[4 * q + 2], kk[4 * q + 3]);
+        tv4[q] = make_uint4(vv[4 * q], vv[4 * q + 1], vv[4 * q + 2], vv[4 * q + 3]);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < kRun; ++q)
+        if (q < cnt) {
+          tile_keys[ea + q] = kk[q];
+          tile_vals[ea + q] = vv[q];
+        }
+    }
   }
   }  // entry-block loop
 }
 
 // ---------------------------------------------------------------- K5 ranges
+// one load per element: the neighbours come from the adjacent lanes (the warp's ends load theirs)
 __global__ void k_ranges(const uint32_t* __restrict__ tile_keys, const unsigned long long* __restrict__ K_dev, int64_t cap,
                          uint2* __restrict__ ranges) {
   const int64_t K = (int64_t)*K_dev;
   if (K > cap) return;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < K; e += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t t = tile_keys[e];
-    if (e == 0 || tile_keys[e - 1] != t) ranges[t].x = (uint32_t)e;
-    if (e == K - 1 || tile_keys[e + 1] != t) ranges[t].y = (uint32_t)(e + 1);
+  const unsigned lane = lane_id();
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  constexpr uint32_t kNone = 0xffffffffu;  // never a tile id
+  for (int64_t base = wid * 32; base < K; base += nwarps * 32) {
+    const int64_t e = base + lane;
+    const bool ok = e < K;
+    const uint32_t t = ok ? tile_keys[e] : kNone;
+    uint32_t prev = __shfl_up_sync(0xffffffffu, t, 1);
+    uint32_t next = __shfl_down_sync(0xffffffffu, t, 1);
+    if (lane == 0) prev = base > 0 ? tile_keys[base - 1] : kNone;
+    if (lane == 31) next = e + 1 < K ? tile_keys[e + 1] : kNone;
+    if (ok) {
+      if (prev != t) ranges[t].x = (uint32_t)e;
+      if (next != t) ranges[t].y = (uint32_t)(e + 1);
+    }
   }
 }
 
@@ -368,7 +437,7 @@ unsigned grid_cap(int64_t items, int per_sm) {
 
 // ---------------------------------------------------------------- host drivers
 size_t ScanScratch::required(int64_t max_n) {
-  size_t total = 0;
+  size_t total = kReserved;
   int64_t n = max_n;
   while (n > kChunk) {
     n = cdiv(n, kChunk);
@@ -377,34 +446,39 @@ size_t ScanScratch::required(int64_t max_n) {
   return total + 256;
 }
 
+// n is the capacity; with n_dev the element count is min(*n_dev, n) and CTAs past it do nothing
 template <typename TIn, typename TOut>
-static void scan_level(const TIn* in, TOut* out, int64_t n, TOut* total, char* scratch, cudaStream_t s) {
+static void scan_level(const TIn* in, TOut* out, int64_t n, const unsigned long long* n_dev, TOut* total, char* scratch,
+                       cudaStream_t s) {
   const int64_t nb = cdiv(n, kChunk);
   if (nb <= 1) {
-    k_scan_down<TIn, TOut><<<1, kThreads, 0, s>>>(in, out, n, nullptr, total);
+    k_scan_down<TIn, TOut><<<1, kThreads, 0, s>>>(in, out, n, n_dev, nullptr, total);
     count_launches(1);
     return;
   }
   TOut* sums = reinterpret_cast<TOut*>(scratch);
   char* next = scratch + (size_t)(nb + 1) * sizeof(unsigned long long);
-  k_scan_reduce<TIn, TOut><<<(unsigned)nb, kThreads, 0, s>>>(in, n, sums);
-  scan_level<TOut, TOut>(sums, sums, nb, (TOut*)nullptr, next, s);
-  k_scan_down<TIn, TOut><<<(unsigned)nb, kThreads, 0, s>>>(in, out, n, sums, total);
+  k_scan_reduce<TIn, TOut><<<(unsigned)nb, kThreads, 0, s>>>(in, n, n_dev, sums);
+  scan_level<TOut, TOut>(sums, sums, nb, nullptr, total, next, s);
+  k_scan_down<TIn, TOut><<<(unsigned)nb, kThreads, 0, s>>>(in, out, n, n_dev, sums, nullptr);
   count_launches(2);
 }
 
 template <typename TIn, typename TOut>
-void scan_exclusive(const TIn* in, TOut* out, int64_t n, TOut* total, ScanScratch& sc, cudaStream_t s) {
+void scan_exclusive(const TIn* in, TOut* out, int64_t n, TOut* total, ScanScratch& sc, cudaStream_t s,
+                    const unsigned long long* n_dev) {
   if (n <= 0) {
     if (total) cudaMemsetAsync(total, 0, sizeof(TOut), s);
     return;
   }
-  scan_level<TIn, TOut>(in, out, n, total, reinterpret_cast<char*>(sc.buf), s);
+  scan_level<TIn, TOut>(in, out, n, n_dev, total, reinterpret_cast<char*>(sc.buf) + ScanScratch::kReserved, s);
 }
 
-template void scan_exclusive<uint32_t, uint32_t>(const uint32_t*, uint32_t*, int64_t, uint32_t*, ScanScratch&, cudaStream_t);
+template void scan_exclusive<uint32_t, uint32_t>(const uint32_t*, uint32_t*, int64_t, uint32_t*, ScanScratch&, cudaStream_t,
+                                                 const unsigned long long*);
 template void scan_exclusive<uint32_t, unsigned long long>(const uint32_t*, unsigned long long*, int64_t,
-                                                           unsigned long long*, ScanScratch&, cudaStream_t);
+                                                           unsigned long long*, ScanScratch&, cudaStream_t,
+                                                           const unsigned long long*);
 
 void launch_gather_touched(const uint32_t* sorted_vals, const ushort4* rect, int64_t n, uint32_t* touched, cudaStream_t s,
                            const unsigned long long* n_dev) {
@@ -431,12 +505,13 @@ void radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_
   for (int p = 0; p < passes; ++p) {
     const int shift = p * bits_per;
     const int bits = (total_bits - shift) < bits_per ? (total_bits - shift) : bits_per;
-    const int64_t entries = ((int64_t)1 << bits) * nchunks;
+    const int64_t entries = ((int64_t)1 << bits) * nchunks;  // capacity of the matrix
     (void)hist_cap;
-    k_radix_hist<<<grid_cap(nchunks, 8), kThreads, 0, s>>>(keys[cur], n_host, n_dev, n_cap, shift, bits, hist, nchunks);
-    scan_exclusive<uint32_t, uint32_t>(hist, hist, entries, (uint32_t*)nullptr, sc, s);
-    k_radix_scatter<<<grid_cap(nchunks, 4), kThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_host,
-                                                           n_dev, n_cap, shift, bits, hist, nchunks);
+    unsigned long long* n_entries = reinterpret_cast<unsigned long long*>(sc.buf);
+    k_radix_hist<<<grid_cap(nchunks, 8), kThreads, 0, s>>>(keys[cur], n_host, n_dev, n_cap, shift, bits, hist, n_entries);
+    scan_exclusive<uint32_t, uint32_t>(hist, hist, entries, (uint32_t*)nullptr, sc, s, n_entries);
+    k_radix_scatter<<<grid_cap(nchunks, 4), kScThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_host,
+                                                           n_dev, n_cap, shift, bits, hist);
     count_launches(2);
     cur ^= 1;
   }
@@ -445,10 +520,10 @@ void radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_
 template <class VS>
 void launch_keygen(const VS& vs, const unsigned long long* offsets, const unsigned long long* K_dev, int64_t n,
                    const uint32_t* sorted_vals, const ushort4* rect, int64_t cap, uint32_t* tile_keys, uint32_t* tile_vals,
-                   uint32_t* flags, cudaStream_t s) {
+                   uint32_t* flags, cudaStream_t s, const unsigned long long* n_dev) {
   if (n <= 0 || cap <= 0) return;
-  k_keygen<VS><<<grid_cap(cdiv(cap, kKeygenEntries), 8), kThreads, 0, s>>>(vs, offsets, K_dev, n, sorted_vals, rect, cap, tile_keys, tile_vals,
-                                                     flags);
+  k_keygen<VS><<<grid_cap(cdiv(cap, kKeygenEntries), 8), kThreads, 0, s>>>(vs, offsets, K_dev, n, n_dev, sorted_vals, rect,
+                                                                        cap, tile_keys, tile_vals, flags);
   count_launches(1);
 }
 
@@ -472,9 +547,9 @@ void launch_make_keys(const uint32_t* tile_keys, const uint32_t* tile_vals, cons
 
 template void launch_keygen<FrameViews>(const FrameViews&, const unsigned long long*, const unsigned long long*, int64_t,
                                         const uint32_t*, const ushort4*, int64_t, uint32_t*, uint32_t*, uint32_t*,
-                                        cudaStream_t);
+                                        cudaStream_t, const unsigned long long*);
 template void launch_keygen<BatchViews>(const BatchViews&, const unsigned long long*, const unsigned long long*, int64_t,
                                         const uint32_t*, const ushort4*, int64_t, uint32_t*, uint32_t*, uint32_t*,
-                                        cudaStream_t);
+                                        cudaStream_t, const unsigned long long*);
 
 }  // namespace ges

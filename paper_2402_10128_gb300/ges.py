@@ -91,7 +91,7 @@ def _load():
         "ges_frame_status": ([P, P, P], i32),
         "ges_frame_keys": ([P, P, P, P, i64, P], i32),
         "ges_frame_inspect": ([P, P, P, P, P, P, P], i32),
-        "ges_frame_count_work": ([P, P, P, P, P], i32),
+        "ges_frame_count_work": ([P, P, P, P, P, P], i32),
         "ges_kernel_launches": ([], u64),
         "ges_render_fwd_noalloc": ([P, P, P, P, P, P, P], i32),
         "ges_serve_create": ([P, P, i32, P], i32),
@@ -260,10 +260,11 @@ def ges_frame_inspect(frame: int, n: int, n_tiles: int, stream=None):
 
 
 def ges_frame_count_work(frame: int, stream=None):
-    """(evaluated, in_extent, K) of the last binned frame (synchronises)."""
-    a, b, k = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
-    _check(_lib.ges_frame_count_work(frame, _stream(stream), ctypes.byref(a), ctypes.byref(b), ctypes.byref(k)))
-    return int(a.value), int(b.value), int(k.value)
+    """(evaluated, in_extent, composited, K) of the last binned frame (synchronises)."""
+    a, b, c, k = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(_lib.ges_frame_count_work(frame, _stream(stream), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                     ctypes.byref(k)))
+    return int(a.value), int(b.value), int(c.value), int(k.value)
 
 
 def ges_kernel_launches() -> int:
