@@ -138,9 +138,10 @@ ges_status ges_preprocess(ges_frame* frame, const ges_scene* scene, const ges_ca
                           const ges_params* params, void* stream);
 
 /* Binning: depth sort of the primitives (radix, 32-bit float keys), exclusive scan of
-   the tiles each touches, duplicate generation in depth order, stable radix sort by
-   tile id, and per-tile [start,end) ranges.  The result equals a stable sort of the
-   64-bit keys (tile << 32 | depth bits) with values = primitive index. */
+   the tiles each meets (per tile row, the columns its elliptical extent spans), duplicate
+   generation in depth order, stable radix sort by tile id, and per-tile [start,end) ranges.
+   The result equals a stable sort of the 64-bit keys (tile << 32 | depth bits) with
+   values = primitive index. */
 ges_status ges_bin_sort(ges_frame* frame, void* stream);
 
 /* Forward composite (Sec. 3.2): per pixel, front to back over its tile's list,
@@ -200,7 +201,7 @@ uint64_t ges_kernel_launches(void);
    Errors: GES_ERR_INVALID_ARG for a NULL pointer or a scene/image above the limits (nothing
    enqueued); GES_ERR_CAPACITY when the duplicates exceed their limit (outputs then hold the
    background only).  The call synchronises `stream` before returning, to read that count.
-   Every intermediate buffer lives in one fixed array of about 23 MB in device global memory,
+   Every intermediate buffer lives in one fixed array of about 24 MB in device global memory,
    which each GPU that loads the library holds until the process exits.  All calls share that
    array and it keeps the last call's contents: calls whose work overlaps on the GPU (other
    streams, other host threads on the same device) race on it and must be serialised by the

@@ -73,7 +73,7 @@ def _load():
     lib.ora_phi_exact.argtypes = [i64, P, P]
     lib.ora_sh_basis.argtypes = [i32, i64, P, P]
     lib.ora_keys.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, P, P, P]
-    lib.ora_sorted_keys.argtypes = [i64, P, P, P, i32, P, P]
+    lib.ora_sorted_keys.argtypes = [i64, P, P, P, P, P, P, P, P, P]
     lib.ora_project.argtypes = [i64, P, P, P, P, P, P, i32, P, P, P]
     lib.ora_render.argtypes = [i64, P, P, P, P, P, P, i32, P, P, i64, P, P, P, P, P, i32, i32]
     lib.ora_render.restype = i32
@@ -159,8 +159,9 @@ def sh_basis(degree: int, dirs):
 
 
 def keys(scene, cam, params=None):
-    """FP32 key module.  Returns dict with depth_key u32[n], rect i32[n,4] (x0,y0,x1,y1 tiles,
-    end-exclusive), touched u32[n], mean2d f32[n,2], cov2d f32[n,3], qstar f32[n]."""
+    """FP32 key module.  Returns dict with depth_key u32[n], rect i32[n,4] (bounding box of the
+    extent in tiles: x0,y0,x1,y1, end-exclusive), touched u32[n] (tiles the extent meets: the sum
+    of its row spans), mean2d f32[n,2], cov2d f32[n,3], qstar f32[n]."""
     n, m, s, q, b, o, _ = _scene64(scene)
     dk = np.empty(n, np.uint32)
     rect = np.empty((n, 4), np.int32)
@@ -174,14 +175,14 @@ def keys(scene, cam, params=None):
 
 
 def sorted_keys(scene, cam, params=None, key_info=None):
-    """Stable-sorted (key, value) list: key = tile << 32 | depth_key, value = primitive index."""
+    """Stable-sorted (key, value) list: key = tile << 32 | depth_key, value = primitive index,
+    one entry per tile of each primitive's row spans."""
     k = key_info if key_info is not None else keys(scene, cam, params)
-    n = k["touched"].shape[0]
     K = int(k["touched"].astype(np.uint64).sum())
-    tiles_x = (cam.width + 15) // 16
+    n, m, s, q, b, o, _ = _scene64(scene)
     kk = np.empty(K, np.uint64)
     vv = np.empty(K, np.uint32)
-    _load().ora_sorted_keys(n, _p(k["depth_key"]), _p(k["rect"]), _p(k["touched"]), int(tiles_x),
+    _load().ora_sorted_keys(n, _p(m), _p(s), _p(q), _p(b), _p(o), _p(cam_array(cam)), _p(par_array(params)),
                             _p(kk), _p(vv))
     return kk, vv
 

@@ -149,10 +149,52 @@ float key_log2(float x) {
 
 struct KeyOut {
   uint32_t depth_key;
-  int32_t rect[4];  // x0, y0, x1, y1 (tiles, end exclusive)
-  uint32_t touched;
-  float mean2d[2], cov2d[3], qstar;
+  int32_t rect[4];  // x0, y0, x1, y1 (tiles, end exclusive): bounding box of the extent
+  uint32_t touched; // tiles the extent actually meets (sum of the row spans)
+  float mean2d[2], cov2d[3], qstar, qlim, margin_abs;
 };
+
+// Tiles of row ty met by the ellipse {d : d^T cov^-1 d <= qlim} around the 2D mean (FP32, fixed
+// order, no contraction).  The row band is y in [16 ty, 16 ty + 16); within it the ellipse's
+// x-extent runs from its leftmost to its rightmost point, x(dy) = (b/c) dy +- sqrt((qlim - dy^2/c)
+// det/c), whose extremes over the whole ellipse lie at dy = +-b sqrt(qlim/a); over the band they lie
+// at that dy clamped into the band.  The span, widened by margin_abs, is clipped to the bounding
+// box's columns [rect0, rect2).  Per-primitive constants first, then one evaluation per row.
+struct RowConsts {
+  float Y, sl, g, ic, dys;
+};
+RowConsts row_consts(const KeyOut& k) {
+  const float a = k.cov2d[0], b = k.cov2d[1], c = k.cov2d[2], ql = k.qlim;
+  RowConsts r;
+  r.Y = std::sqrt(ql * c);
+  const float det = a * c - b * b;
+  r.sl = b / c;
+  r.g = det / c;
+  r.ic = 1.0f / c;
+  r.dys = b * std::sqrt(ql / a);
+  return r;
+}
+bool row_span(const KeyOut& k, const RowConsts& rc, int ty, int& tx0, int& tx1) {
+  const float u = k.mean2d[0], v = k.mean2d[1], ql = k.qlim;
+  const float lo = (float)(16 * ty) - v;
+  const float hi = (float)(16 * ty + 16) - v;
+  const float lo2 = std::fmax(lo, -rc.Y), hi2 = std::fmin(hi, rc.Y);
+  if (!(lo2 <= hi2)) return false;
+  const float dmax = std::fmin(std::fmax(rc.dys, lo2), hi2);
+  const float dmin = std::fmin(std::fmax(-rc.dys, lo2), hi2);
+  const float tr = std::fmax(ql - (dmax * dmax) * rc.ic, 0.0f);
+  const float tl = std::fmax(ql - (dmin * dmin) * rc.ic, 0.0f);
+  const float wr = std::sqrt(tr * rc.g), wl = std::sqrt(tl * rc.g);
+  const float xr = ((u + rc.sl * dmax) + wr) + k.margin_abs;
+  const float xl = ((u + rc.sl * dmin) - wl) - k.margin_abs;
+  float f0 = std::floor(xl * 0.0625f), f1 = std::floor(xr * 0.0625f);
+  const float r0 = (float)k.rect[0], r1 = (float)(k.rect[2] - 1);
+  f0 = std::fmin(std::fmax(f0, r0), r1);
+  f1 = std::fmin(std::fmax(f1, r0), r1);
+  tx0 = (int)f0;
+  tx1 = (int)f1;
+  return tx1 >= tx0;
+}
 
 void key_prim(const double* mu_d, const double* s_d, const double* q_d, double beta_d, double kappa_d,
               const Cam& cam, const Par& par, KeyOut& o) {
@@ -270,19 +312,25 @@ void key_prim(const double* mu_d, const double* s_d, const double* q_d, double b
   fy0 = std::fmin(std::fmax(fy0, 0.0f), (float)tiles_y);
   fy1 = std::fmin(std::fmax(fy1, 0.0f), (float)tiles_y);
   int x0 = (int)fx0, x1 = (int)fx1, y0 = (int)fy0, y1 = (int)fy1;
-  uint32_t touched = 0;
-  if (valid && x1 > x0 && y1 > y0) touched = (uint32_t)((x1 - x0) * (y1 - y0));
-  uint32_t zb;
-  std::memcpy(&zb, &tz, 4);
-  o.depth_key = touched ? zb : 0xffffffffu;
-  o.rect[0] = touched ? x0 : 0;
-  o.rect[1] = touched ? y0 : 0;
-  o.rect[2] = touched ? x1 : 0;
-  o.rect[3] = touched ? y1 : 0;
-  o.touched = touched;
   o.mean2d[0] = u; o.mean2d[1] = v;
   o.cov2d[0] = a; o.cov2d[1] = b; o.cov2d[2] = c;
   o.qstar = qs;
+  o.qlim = (qs * onep) * onep;
+  o.margin_abs = mabs;
+  o.rect[0] = x0; o.rect[1] = y0; o.rect[2] = x1; o.rect[3] = y1;
+  uint32_t touched = 0;
+  if (valid && x1 > x0 && y1 > y0) {
+    const RowConsts rc = row_consts(o);
+    for (int ty = y0; ty < y1; ++ty) {
+      int t0, t1;
+      if (row_span(o, rc, ty, t0, t1)) touched += (uint32_t)(t1 - t0 + 1);
+    }
+  }
+  uint32_t zb;
+  std::memcpy(&zb, &tz, 4);
+  o.depth_key = touched ? zb : 0xffffffffu;
+  if (!touched) o.rect[0] = o.rect[1] = o.rect[2] = o.rect[3] = 0;
+  o.touched = touched;
 }
 
 // ---------------------------------------------------------------------------
@@ -568,8 +616,12 @@ void tile_lists(const Prepared& P, const Cam& cam, std::vector<std::vector<int64
   lists.assign((size_t)tx * ty, {});
   for (int64_t i : P.order) {
     const KeyOut& k = P.keys[i];
-    for (int y = k.rect[1]; y < k.rect[3]; ++y)
-      for (int x = k.rect[0]; x < k.rect[2]; ++x) lists[(size_t)y * tx + x].push_back(i);
+    const RowConsts rc = row_consts(k);
+    for (int y = k.rect[1]; y < k.rect[3]; ++y) {
+      int t0, t1;
+      if (!row_span(k, rc, y, t0, t1)) continue;
+      for (int x = t0; x <= t1; ++x) lists[(size_t)y * tx + x].push_back(i);
+    }
   }
 }
 
@@ -619,23 +671,29 @@ void ora_keys(int64_t n, const double* means, const double* scales, const double
   }
 }
 
-// Sorted (key, value) list: key = tile << 32 | depth_key, value = primitive index,
-// stable in primitive index.  keys/vals hold sum(touched) entries.
-void ora_sorted_keys(int64_t n, const uint32_t* depth_key, const int32_t* rect, const uint32_t* touched, int tiles_x,
-                     uint64_t* keys, uint32_t* vals) {
+// Sorted (key, value) list: key = tile << 32 | depth_key, value = primitive index, stable in
+// primitive index; one entry per tile of each primitive's row spans.  keys/vals hold sum(touched).
+void ora_sorted_keys(int64_t n, const double* means, const double* scales, const double* quats, const double* betas,
+                     const double* opac, const double* cam_d, const double* par_d, uint64_t* keys, uint32_t* vals) {
+  Cam cam = read_cam(cam_d);
+  Par par = read_par(par_d);
+  const int tiles_x = (cam.W + TILE - 1) / TILE;
   std::vector<std::pair<uint64_t, uint32_t>> kv;
   for (int64_t i = 0; i < n; ++i) {
-    if (!touched[i]) continue;
-    for (int y = rect[4 * i + 1]; y < rect[4 * i + 3]; ++y)
-      for (int x = rect[4 * i + 0]; x < rect[4 * i + 2]; ++x) {
-        uint64_t tile = (uint64_t)y * tiles_x + x;
-        kv.emplace_back((tile << 32) | depth_key[i], (uint32_t)i);
-      }
+    KeyOut k;
+    key_prim(means + 3 * i, scales + 3 * i, quats + 4 * i, betas[i], opac[i], cam, par, k);
+    if (!k.touched) continue;
+    const RowConsts rc = row_consts(k);
+    for (int y = k.rect[1]; y < k.rect[3]; ++y) {
+      int t0, t1;
+      if (!row_span(k, rc, y, t0, t1)) continue;
+      for (int x = t0; x <= t1; ++x) kv.emplace_back((((uint64_t)y * tiles_x + x) << 32) | k.depth_key, (uint32_t)i);
+    }
   }
   std::stable_sort(kv.begin(), kv.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
-  for (size_t k = 0; k < kv.size(); ++k) {
-    keys[k] = kv[k].first;
-    vals[k] = kv[k].second;
+  for (size_t e = 0; e < kv.size(); ++e) {
+    keys[e] = kv[e].first;
+    vals[e] = kv[e].second;
   }
 }
 

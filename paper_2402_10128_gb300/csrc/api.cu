@@ -249,6 +249,8 @@ ges_status ges_frame_create(ges_ctx* ctx, int64_t n_capacity, int32_t width, int
   }
   A((void**)&f->rect, sizeof(ushort4) * N);
   A((void**)&f->rec, sizeof(Rec) * N);
+  A((void**)&f->ext, sizeof(float4) * N);
+  A((void**)&f->tprim, 4 * N);
   A((void**)&f->touched, 4 * N);
   A((void**)&f->offsets, 8 * N);
   A((void**)&f->g2d, sizeof(float4) * 3 * N);
@@ -286,6 +288,8 @@ void ges_frame_destroy(ges_frame* f) {
   }
   ctx_free(c, f->rect, sizeof(ushort4) * N);
   ctx_free(c, f->rec, sizeof(Rec) * N);
+  ctx_free(c, f->ext, sizeof(float4) * N);
+  ctx_free(c, f->tprim, 4 * N);
   ctx_free(c, f->touched, 4 * N);
   ctx_free(c, f->offsets, 8 * N);
   ctx_free(c, f->g2d, sizeof(float4) * 3 * N);
@@ -318,7 +322,8 @@ ges_status ges_preprocess(ges_frame* f, const ges_scene* scene, const ges_camera
   f->P = to_params(*params);
   f->n = scene->n;
   f->sh_degree = scene->sh_degree;
-  launch_preprocess<FrameViews>(f->vt, f->n, f->P, f->depth_key, f->dk[0], f->pv[0], f->rect, f->rec, f->ctx->num_sms, s);
+  launch_preprocess<FrameViews>(f->vt, f->n, f->P, f->depth_key, f->dk[0], f->pv[0], f->rect, f->rec, f->ext, f->tprim,
+                                f->ctx->num_sms, s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "preprocess launch");
   f->have_pre = true;
@@ -339,7 +344,7 @@ ges_status ges_bin_sort(ges_frame* f, void* stream) {
   radix_sort_pairs(f->dk, f->pv, cur, f->n, nullptr, f->n, 32, f->hist, f->hist_cap, f->scan, s);
   f->sorted_prims = f->pv[cur];
   // tiles touched in depth order, exclusive scan -> offsets, K
-  launch_gather_touched(f->sorted_prims, f->rect, f->n, f->touched, s);
+  launch_gather_touched(f->sorted_prims, f->tprim, f->n, f->touched, s);
   scan_exclusive<uint32_t, unsigned long long>(f->touched, f->offsets, f->n, f->d_K, f->scan, s);
   if (f->auto_cap) {
     if ((e = cudaMemcpyAsync(f->h_K, f->d_K, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(e, "read K");
@@ -353,7 +358,8 @@ ges_status ges_bin_sort(ges_frame* f, void* stream) {
       if ((st = frame_alloc_keys(f, cap)) != GES_OK) return st;
     }
   }
-  launch_keygen<FrameViews>(f->vt, f->offsets, f->d_K, f->n, f->sorted_prims, f->rect, f->key_cap, f->tk[0], f->tv[0], f->d_flags, s);
+  launch_keygen<FrameViews>(f->vt, f->offsets, f->touched, f->d_K, f->n, f->sorted_prims, f->rect, f->ext, f->rec,
+                            f->P.margin_abs, f->key_cap, f->tk[0], f->tv[0], f->d_flags, s);
   int tcur = 0;
   radix_sort_pairs(f->tk, f->tv, tcur, 0, f->d_K, f->key_cap, bits_for(f->n_tiles), f->hist, f->hist_cap, f->scan, s);
   f->tile_keys = f->tk[tcur];

@@ -30,7 +30,9 @@ struct ges_frame {
   uint32_t* pv[2] = {nullptr, nullptr};
   ushort4* rect = nullptr;
   ges::Rec* rec = nullptr;
-  uint32_t* touched = nullptr;
+  float4* ext = nullptr;           // extent shape: 2D covariance and q limit
+  uint32_t* tprim = nullptr;       // tiles met per primitive
+  uint32_t* touched = nullptr;     // the same, in depth order
   unsigned long long* offsets = nullptr;
   float4* g2d = nullptr;
   // per duplicate

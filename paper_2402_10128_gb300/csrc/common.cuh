@@ -109,6 +109,113 @@ struct __align__(16) Rec {
 };
 
 // ------------------------------------------------------------------------------------------
+// Key path: FP32 with every operation rounded separately (no contraction), in a fixed order.
+// These values decide integers (visibility, depth order, tile rectangles), so the oracle
+// evaluates the same sequence.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ float kadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float ksub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float kmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float kdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float ksqrt(float a) { return __fsqrt_rn(a); }
+
+
+// Tiles of row ty that the ellipse {d : d^T cov^-1 d <= qlim} around the 2D mean (u, v) meets, on
+// the key path.  ext = (a, b, c, qlim) with (a, b, c) the 2D covariance (with dilation).  The row
+// band is y in [16 ty, 16 ty + 16); inside it the ellipse's x-extent runs from its leftmost to its
+// rightmost point, x(dy) = (b/c) dy +- sqrt((qlim - dy^2/c) det/c), whose extremes over the whole
+// ellipse lie at dy = +-b sqrt(qlim/a); over the band they lie at that dy clamped into the band.
+// The span, widened by margin_abs, is clipped to the bounding box's columns [r.x, r.z).
+struct RowSpan {
+  float u, v, ql, mabs;  // 2D mean, q limit, absolute margin
+  float Y, sl, g, ic, dys;
+  float r0, r1;          // first and last column of the bounding box
+};
+
+__device__ __forceinline__ RowSpan make_row_span(const float4 ext, float u, float v, float mabs, const ushort4 r) {
+  const float a = ext.x, b = ext.y, c = ext.z, ql = ext.w;
+  RowSpan s;
+  s.u = u;
+  s.v = v;
+  s.ql = ql;
+  s.mabs = mabs;
+  s.Y = ksqrt(kmul(ql, c));
+  const float det = ksub(kmul(a, c), kmul(b, b));
+  s.sl = kdiv(b, c);
+  s.g = kdiv(det, c);
+  s.ic = kdiv(1.0f, c);
+  s.dys = kmul(b, ksqrt(kdiv(ql, a)));
+  s.r0 = (float)r.x;
+  s.r1 = (float)(r.z - 1);
+  return s;
+}
+
+__device__ __forceinline__ bool tile_row_span(const RowSpan& s, int ty, int& tx0, int& tx1) {
+  const float lo = ksub((float)(16 * ty), s.v);
+  const float hi = ksub((float)(16 * ty + 16), s.v);
+  const float lo2 = fmaxf(lo, -s.Y), hi2 = fminf(hi, s.Y);
+  if (!(lo2 <= hi2)) return false;
+  const float dmax = fminf(fmaxf(s.dys, lo2), hi2);
+  const float dmin = fminf(fmaxf(-s.dys, lo2), hi2);
+  const float tr = fmaxf(ksub(s.ql, kmul(kmul(dmax, dmax), s.ic)), 0.0f);
+  const float tl = fmaxf(ksub(s.ql, kmul(kmul(dmin, dmin), s.ic)), 0.0f);
+  const float wr = ksqrt(kmul(tr, s.g)), wl = ksqrt(kmul(tl, s.g));
+  const float xr = kadd(kadd(kadd(s.u, kmul(s.sl, dmax)), wr), s.mabs);
+  const float xl = ksub(ksub(kadd(s.u, kmul(s.sl, dmin)), wl), s.mabs);
+  float f0 = floorf(kmul(xl, 0.0625f)), f1 = floorf(kmul(xr, 0.0625f));
+  f0 = fminf(fmaxf(f0, s.r0), s.r1);
+  f1 = fminf(fmaxf(f1, s.r0), s.r1);
+  tx0 = (int)f0;
+  tx1 = (int)f1;
+  return tx1 >= tx0;
+}
+
+// ------------------------------------------------------------------------------------------
+// Warp-cooperative row walk.  The warp's primitives, h[i] tile rows each, are laid out as one list
+// of (primitive, row) slots in lane order; the slots are taken 32 at a time, one per lane, so that
+// every lane evaluates a row span whatever the mix of large and small primitives.
+// ------------------------------------------------------------------------------------------
+// exclusive prefix sum over the warp's lanes; total receives the sum of all lanes
+__device__ __forceinline__ unsigned warp_excl_scan(unsigned v, unsigned& total) {
+  const unsigned lane = threadIdx.x & 31u;
+  unsigned x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= (unsigned)d) x += y;
+  }
+  total = __shfl_sync(0xffffffffu, x, 31);
+  return x - v;
+}
+
+// the last lane i whose key[i] <= s, for keys nondecreasing over the lanes with key[0] = 0
+__device__ __forceinline__ int warp_last_le(unsigned key, unsigned s) {
+  int lo = 0;
+#pragma unroll
+  for (int step = 16; step; step >>= 1) {
+    const unsigned kv = __shfl_sync(0xffffffffu, key, lo + step);
+    if (kv <= s) lo += step;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ RowSpan shfl_row_span(const RowSpan& s, int src) {
+  RowSpan q;
+  q.u = __shfl_sync(0xffffffffu, s.u, src);
+  q.v = __shfl_sync(0xffffffffu, s.v, src);
+  q.ql = __shfl_sync(0xffffffffu, s.ql, src);
+  q.mabs = __shfl_sync(0xffffffffu, s.mabs, src);
+  q.Y = __shfl_sync(0xffffffffu, s.Y, src);
+  q.sl = __shfl_sync(0xffffffffu, s.sl, src);
+  q.g = __shfl_sync(0xffffffffu, s.g, src);
+  q.ic = __shfl_sync(0xffffffffu, s.ic, src);
+  q.dys = __shfl_sync(0xffffffffu, s.dys, src);
+  q.r0 = __shfl_sync(0xffffffffu, s.r0, src);
+  q.r1 = __shfl_sync(0xffffffffu, s.r1, src);
+  return q;
+}
+
+// ------------------------------------------------------------------------------------------
 // Compositing arithmetic shared by the forward and backward kernels.  Both must take the
 // same decisions (skip, clamp, stop) bit for bit, so the sequence is written with explicit
 // intrinsics: the compiler has no freedom to contract it differently in the two kernels.

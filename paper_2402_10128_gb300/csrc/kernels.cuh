@@ -11,9 +11,12 @@ void count_launches(int n);
 // ---- per-primitive kernels (preprocess.cu)
 // VS is FrameViews (table by value) or BatchViews (table in device memory).  grid_total sizes the
 // grid; the kernels loop over the table's total_prims.
+// outputs per primitive: depth key (twice: kept and sort copy), sort value, bounding box of the
+// extent in tiles, record, extent shape (2D covariance and q limit), tiles met (row spans)
 template <class VS>
 void launch_preprocess(const VS& vs, int64_t grid_total, const Params& P, uint32_t* depth_key, uint32_t* sort_keys,
-                       uint32_t* sort_vals, ushort4* rect, Rec* rec, int num_sms, cudaStream_t s);
+                       uint32_t* sort_vals, ushort4* rect, Rec* rec, float4* ext, uint32_t* tprim, int num_sms,
+                       cudaStream_t s);
 template <class VS>
 void launch_preprocess_bwd(const VS& vs, int64_t grid_total, const Params& P, const uint32_t* depth_key,
                            const float4* g2d, int num_sms, cudaStream_t s);
@@ -32,9 +35,9 @@ template <typename TIn, typename TOut>
 void scan_exclusive(const TIn* in, TOut* out, int64_t n, TOut* total, ScanScratch& sc, cudaStream_t s,
                     const unsigned long long* n_dev = nullptr);
 
-// per-primitive tile counts in depth order: touched[j] = area(rect[sorted_vals[j]]) for j < count,
-// 0 for count <= j < n (count = *n_dev if given, else n)
-void launch_gather_touched(const uint32_t* sorted_vals, const ushort4* rect, int64_t n, uint32_t* touched,
+// per-primitive tile counts in depth order: touched[j] = tprim[sorted_vals[j]] for j < count
+// (count = min(*n_dev, n) if n_dev is given, else n)
+void launch_gather_touched(const uint32_t* sorted_vals, const uint32_t* tprim, int64_t n, uint32_t* touched,
                            cudaStream_t s, const unsigned long long* n_dev = nullptr);
 
 // stable LSD radix sort of (u32 key, u32 value) on the low `total_bits` bits.  The element count is
@@ -44,11 +47,14 @@ void radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_
                       int64_t n_cap, int total_bits, uint32_t* hist, int64_t hist_cap, ScanScratch& sc, cudaStream_t s);
 int64_t radix_hist_entries(int64_t n_cap, int total_bits);
 
-// n: primitives (the capacity when n_dev gives the count on the device)
+// n: primitives (the capacity when n_dev gives the count on the device); touched: tiles per
+// primitive in depth order (the scan's input)
 template <class VS>
-void launch_keygen(const VS& vs, const unsigned long long* offsets, const unsigned long long* K_dev,
-                   int64_t n, const uint32_t* sorted_vals, const ushort4* rect, int64_t cap, uint32_t* tile_keys,
-                   uint32_t* tile_vals, uint32_t* flags, cudaStream_t s, const unsigned long long* n_dev = nullptr);
+void launch_keygen(const VS& vs, const unsigned long long* offsets, const uint32_t* touched,
+                   const unsigned long long* K_dev, int64_t n, const uint32_t* sorted_vals, const ushort4* rect,
+                   const float4* ext, const Rec* rec, float margin_abs, int64_t cap,
+                   uint32_t* tile_keys, uint32_t* tile_vals, uint32_t* flags, cudaStream_t s,
+                   const unsigned long long* n_dev = nullptr);
 void launch_ranges(const uint32_t* tile_keys, const unsigned long long* K_dev, int64_t cap, uint2* ranges, int num_sms,
                    cudaStream_t s);
 // materialise the 64-bit keys (tile << 32 | depth key) of a sorted list (inspection only)

@@ -8,17 +8,6 @@ namespace ges {
 // Coefficients of the key-path exp2 series (ln2^k / k!, rounded to float), set by the host.
 __constant__ float c_exp2_coef[8];
 
-// ------------------------------------------------------------------------------------------
-// Key path: FP32 with every operation rounded separately (no contraction), in a fixed order.
-// These values decide integers (visibility, depth order, tile rectangles), so the oracle
-// evaluates the same sequence.
-// ------------------------------------------------------------------------------------------
-__device__ __forceinline__ float kadd(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ float ksub(float a, float b) { return __fsub_rn(a, b); }
-__device__ __forceinline__ float kmul(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ float kdiv(float a, float b) { return __fdiv_rn(a, b); }
-__device__ __forceinline__ float ksqrt(float a) { return __fsqrt_rn(a); }
-
 // 2^x: x = n + f with n = rint(x); 2^f by its degree-7 Taylor series in f (coefficients
 // ln2^k/k!), Horner order, then an exact scaling by 2^n.  x is clamped to [-100, 126].
 __device__ __forceinline__ float key_exp2(float x) {

@@ -9,7 +9,7 @@
 // the caller passes only its inputs (the scene) and its outputs (image, final transmittance,
 // contributor count).
 //
-// The array costs kScratchBytes (about 23 MB) on every GPU that loads this library, for as long
+// The array costs kScratchBytes (about 24 MB) on every GPU that loads this library, for as long
 // as the process lives.  All calls share it and it keeps the last call's contents, so calls whose
 // work overlaps on the GPU (different streams, or different host threads on the same device)
 // race on it and must be serialised by the caller.
@@ -30,7 +30,7 @@ constexpr int64_t kNaScanBytes = 4096;     // multi-level scan scratch for <= 2^
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t depth_key, dk0, dk1, pv0, pv1, rect, rec, touched, offsets;
+  size_t depth_key, dk0, dk1, pv0, pv1, rect, rec, ext, tprim, touched, offsets;
   size_t tk0, tk1, tv0, tv1, hist, scan, ranges, K, flags, total;
 };
 
@@ -49,6 +49,8 @@ constexpr Layout make_layout() {
   L.pv1 = take(4 * kNaMaxPrims);
   L.rect = take(8 * kNaMaxPrims);
   L.rec = take(sizeof(Rec) * kNaMaxPrims);
+  L.ext = take(sizeof(float4) * kNaMaxPrims);
+  L.tprim = take(4 * kNaMaxPrims);
   L.touched = take(4 * kNaMaxPrims);
   L.offsets = take(8 * kNaMaxPrims);
   L.tk0 = take(4 * kNaMaxKeys);
@@ -163,12 +165,15 @@ extern "C" ges_status ges_render_fwd_noalloc(const ges_scene* scene, const ges_c
   // are never written by the ranges kernel)
   if ((e = cudaMemsetAsync(flags, 0, 4, s)) != cudaSuccess) return cuda_fail(e, "clear flags");
   if ((e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * tiles, s)) != cudaSuccess) return cuda_fail(e, "clear ranges");
-  launch_preprocess<FrameViews>(vt, n, P, depth_key, dk[0], pv[0], rect, rec, ds->num_sms, s);
+  float4* ext = at<float4>(b, kL.ext);
+  uint32_t* tprim = at<uint32_t>(b, kL.tprim);
+  launch_preprocess<FrameViews>(vt, n, P, depth_key, dk[0], pv[0], rect, rec, ext, tprim, ds->num_sms, s);
   int cur = 0;
   radix_sort_pairs(dk, pv, cur, n, nullptr, n, 32, hist, kNaHistEntries, scan, s);
-  launch_gather_touched(pv[cur], rect, n, touched, s);
+  launch_gather_touched(pv[cur], tprim, n, touched, s);
   scan_exclusive<uint32_t, unsigned long long>(touched, offsets, n, dK, scan, s);
-  launch_keygen<FrameViews>(vt, offsets, dK, n, pv[cur], rect, kNaMaxKeys, tk[0], tv[0], flags, s);
+  launch_keygen<FrameViews>(vt, offsets, touched, dK, n, pv[cur], rect, ext, rec, P.margin_abs, kNaMaxKeys,
+                            tk[0], tv[0], flags, s);
   int tcur = 0;
   radix_sort_pairs(tk, tv, tcur, 0, dK, kNaMaxKeys, bits_for(tiles), hist, kNaHistEntries, scan, s);
   launch_ranges(tk[tcur], dK, kNaMaxKeys, ranges, ds->num_sms, s);

@@ -168,10 +168,17 @@ template <class VS>
 __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ VS vs, const Params P, uint32_t* __restrict__ depth_key,
                                                     uint32_t* __restrict__ sort_keys,
                                                     uint32_t* __restrict__ sort_vals, ushort4* __restrict__ rect,
-                                                    Rec* __restrict__ rec) {
+                                                    Rec* __restrict__ rec, float4* __restrict__ ext,
+                                                    uint32_t* __restrict__ tprim) {
   const auto& vt = vs.get();
   const int64_t total = (int64_t)vt.total_prims;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+  const unsigned lane = threadIdx.x & 31u;
+  // the loop runs warp by warp (the tile count below is warp-cooperative): lanes past the end work
+  // on the last primitive and store nothing
+  for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); g0 < total;
+       g0 += (int64_t)gridDim.x * blockDim.x) {
+    const bool inb = g0 + lane < total;
+    const int64_t g = inb ? g0 + lane : total - 1;
     const ViewDesc& vd = vt.v[view_of_prim(vt, g)];
     const int64_t i = g - vd.prim_base;
     const float mx = vd.means[3 * i + 0], my = vd.means[3 * i + 1], mz = vd.means[3 * i + 2];
@@ -284,15 +291,46 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ VS v
     fy0 = fminf(fmaxf(fy0, 0.0f), (float)vd.tiles_y);
     fy1 = fminf(fmaxf(fy1, 0.0f), (float)vd.tiles_y);
     int x0 = (int)fx0, x1 = (int)fx1, y0 = (int)fy0, y1 = (int)fy1;
-    bool touched = valid && x1 > x0 && y1 > y0;
+    // tiles the extent meets: the sum of its row spans within the bounding box
+    const float ql = kmul(kmul(qs, onep), onep);
+    const float4 e4 = make_float4(ca, cb, cc, ql);
+    const ushort4 box = make_ushort4((unsigned short)x0, (unsigned short)y0, (unsigned short)x1, (unsigned short)y1);
+    const uint32_t h = (inb && valid && x1 > x0 && y1 > y0) ? (uint32_t)(y1 - y0) : 0u;
+    const RowSpan rs = make_row_span(e4, u, v, P.margin_abs, box);
+    unsigned nslots;
+    const unsigned hex = warp_excl_scan(h, nslots);
+    uint32_t ntiles = 0;
+    for (unsigned cb = 0; cb < nslots; cb += 32) {
+      const unsigned s = cb + lane;
+      const int ow = warp_last_le(hex, s);
+      const RowSpan q = shfl_row_span(rs, ow);
+      const unsigned qy0 = __shfl_sync(0xffffffffu, (unsigned)y0, ow);
+      const unsigned qhex = __shfl_sync(0xffffffffu, hex, ow);
+      unsigned w = 0;
+      if (s < nslots) {
+        int t0, t1;
+        if (tile_row_span(q, (int)(qy0 + (s - qhex)), t0, t1)) w = (unsigned)(t1 - t0 + 1);
+      }
+      unsigned W;
+      const unsigned wex = warp_excl_scan(w, W);
+      // this lane's primitive owns slots [f, l) of the chunk
+      const int f = (int)(hex > cb ? hex : cb) - (int)cb;
+      const int l = (int)(hex + h < cb + 32u ? hex + h : cb + 32u) - (int)cb;
+      const unsigned a = __shfl_sync(0xffffffffu, wex, f < 31 ? f : 31);
+      const unsigned b = __shfl_sync(0xffffffffu, wex + w, l > 0 ? (l - 1 < 31 ? l - 1 : 31) : 0);
+      if (h && f < l) ntiles += b - a;
+    }
+    if (!inb) continue;
+    const bool touched = ntiles > 0;
 
     const uint32_t dkey = touched ? __float_as_uint(tz) : kCulledKey;
     depth_key[g] = dkey;
     sort_keys[g] = dkey;
     sort_vals[g] = (uint32_t)g;
-    rect[g] = touched ? make_ushort4((unsigned short)x0, (unsigned short)y0, (unsigned short)x1, (unsigned short)y1)
-                      : make_ushort4(0, 0, 0, 0);
+    rect[g] = touched ? box : make_ushort4(0, 0, 0, 0);
+    tprim[g] = ntiles;
     if (!touched) continue;
+    ext[g] = e4;
 
     // SH colour (ordinary FP32)
     float dvx = mx - vd.campos[0], dvy = my - vd.campos[1], dvz = mz - vd.campos[2];
@@ -308,7 +346,7 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ VS v
     }
     float idet = 1.0f / det;
     Rec r;
-    r.a = make_float4(u, v, kmul(kmul(qs, onep), onep), P.mode == 0 ? 0.5f * beta : 1.0f);
+    r.a = make_float4(u, v, ql, P.mode == 0 ? 0.5f * beta : 1.0f);
     r.b = make_float4(cc * idet, -cb * idet, ca * idet, kappa);
     r.c = make_float4(col.x, col.y, col.z, 0.f);
     rec[g] = r;
@@ -496,9 +534,11 @@ static int grid_for(int64_t total, int num_sms) {
 
 template <class VS>
 void launch_preprocess(const VS& vs, int64_t grid_total, const Params& P, uint32_t* depth_key, uint32_t* sort_keys,
-                       uint32_t* sort_vals, ushort4* rect, Rec* rec, int num_sms, cudaStream_t s) {
+                       uint32_t* sort_vals, ushort4* rect, Rec* rec, float4* ext, uint32_t* tprim, int num_sms,
+                       cudaStream_t s) {
   if (grid_total <= 0) return;
-  k_preprocess<VS><<<grid_for(grid_total, num_sms), 256, 0, s>>>(vs, P, depth_key, sort_keys, sort_vals, rect, rec);
+  k_preprocess<VS><<<grid_for(grid_total, num_sms), 256, 0, s>>>(vs, P, depth_key, sort_keys, sort_vals, rect, rec, ext,
+                                                                  tprim);
   count_launches(1);
 }
 
@@ -523,9 +563,9 @@ void set_key_constants(cudaStream_t s) {
 }
 
 template void launch_preprocess<FrameViews>(const FrameViews&, int64_t, const Params&, uint32_t*, uint32_t*, uint32_t*,
-                                            ushort4*, Rec*, int, cudaStream_t);
+                                            ushort4*, Rec*, float4*, uint32_t*, int, cudaStream_t);
 template void launch_preprocess<BatchViews>(const BatchViews&, int64_t, const Params&, uint32_t*, uint32_t*, uint32_t*,
-                                            ushort4*, Rec*, int, cudaStream_t);
+                                            ushort4*, Rec*, float4*, uint32_t*, int, cudaStream_t);
 template void launch_preprocess_bwd<FrameViews>(const FrameViews&, int64_t, const Params&, const uint32_t*,
                                                 const float4*, int, cudaStream_t);
 

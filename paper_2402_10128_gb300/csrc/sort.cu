@@ -260,125 +260,107 @@ __global__ void __launch_bounds__(kScThreads) k_radix_scatter(const uint32_t* __
 }
 
 // ---------------------------------------------------------------- K2 input
-// touched[j] for j < len: the tile count of the j-th primitive in depth order, or 0 for j >= the
-// element count (host n, or the device count n_dev when given)
-__global__ void k_gather_touched(const uint32_t* __restrict__ sorted_vals, const ushort4* __restrict__ rect, int64_t len,
-                                 const unsigned long long* __restrict__ n_dev, uint32_t* __restrict__ touched) {
-  const int64_t n = n_dev ? (int64_t)*n_dev : len;
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < len; j += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t t = 0;
-    if (j < n) {
-      const ushort4 r = rect[sorted_vals[j]];
-      t = (uint32_t)(r.z - r.x) * (uint32_t)(r.w - r.y);
-    }
-    touched[j] = t;
-  }
+// touched[j] for j < count: the tile count of the j-th primitive in depth order (count = the
+// device count n_dev when given, else len)
+__global__ void k_gather_touched(const uint32_t* __restrict__ sorted_vals, const uint32_t* __restrict__ tprim,
+                                 int64_t len, const unsigned long long* __restrict__ n_dev,
+                                 uint32_t* __restrict__ touched) {
+  const int64_t n = n_dev ? (int64_t)min((unsigned long long)len, *n_dev) : len;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    touched[j] = tprim[sorted_vals[j]];
 }
 
 // ---------------------------------------------------------------- K3 keygen
-constexpr int kKeygenEntries = 2048;
+// Primitive j (depth order) owns entries [offsets[j], offsets[j] + touched[j]), row span by row
+// span.  A warp takes 32 consecutive primitives, whose entries are one contiguous range: it walks
+// their (primitive, row) slots 32 at a time (one row span per lane), prefix-sums the span widths,
+// and writes the chunk's entries with consecutive lanes on consecutive entries.  Writes stay below
+// K whatever the inputs.
+constexpr int kKeygenThreads = 256;
 
 template <class VS>
-__global__ void __launch_bounds__(kThreads) k_keygen(const __grid_constant__ VS vs,
-                                                     const unsigned long long* __restrict__ offsets,
-                                                     const unsigned long long* __restrict__ K_dev, int64_t n_cap,
-                                                     const unsigned long long* __restrict__ n_dev,
-                                                     const uint32_t* __restrict__ sorted_vals,
-                                                     const ushort4* __restrict__ rect, int64_t cap,
-                                                     uint32_t* __restrict__ tile_keys, uint32_t* __restrict__ tile_vals,
-                                                     uint32_t* __restrict__ flags) {
-  __shared__ uint32_t win[kKeygenEntries + 2];
-  __shared__ int64_t s_jlo, s_jhi;
+__global__ void __launch_bounds__(kKeygenThreads) k_keygen(const __grid_constant__ VS vs,
+                                                           const unsigned long long* __restrict__ offsets,
+                                                           const unsigned long long* __restrict__ K_dev, int64_t n_cap,
+                                                           const unsigned long long* __restrict__ n_dev,
+                                                           const uint32_t* __restrict__ sorted_vals,
+                                                           const uint32_t* __restrict__ touched,
+                                                           const ushort4* __restrict__ rect, const float4* __restrict__ ext,
+                                                           const Rec* __restrict__ rec, float mabs, int64_t cap,
+                                                           uint32_t* __restrict__ tile_keys,
+                                                           uint32_t* __restrict__ tile_vals, uint32_t* __restrict__ flags) {
   const auto& vt = vs.get();
-  const int64_t n = scan_count(n_cap, n_dev);
   const unsigned long long K = *K_dev;
   if ((int64_t)K > cap) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(flags, kFlagOverflow);
     return;
   }
-  for (int64_t e0 = (int64_t)blockIdx.x * kKeygenEntries; e0 < (int64_t)K; e0 += (int64_t)gridDim.x * kKeygenEntries) {
-  const int64_t e1 = min(e0 + (int64_t)kKeygenEntries, (int64_t)K);
-  __syncthreads();  // the previous block of entries is done with the window
-  if (threadIdx.x < 2) {
-    // last j with offsets[j] <= e (for e = e0 and e = e1 - 1)
-    const unsigned long long e = threadIdx.x == 0 ? (unsigned long long)e0 : (unsigned long long)(e1 - 1);
-    int64_t lo = 0, hi = n;  // first j with offsets[j] > e lies in (lo, hi]
-    while (lo < hi) {
-      int64_t mid = (lo + hi) >> 1;
-      if (offsets[mid] <= e) lo = mid + 1; else hi = mid;
+  const int64_t n = scan_count(n_cap, n_dev);
+  const unsigned lane = lane_id();
+  const int64_t wpb = kKeygenThreads / 32;
+  const int64_t stride = (int64_t)gridDim.x * wpb * 32;
+  for (int64_t base = ((int64_t)blockIdx.x * wpb + (threadIdx.x >> 5)) * 32; base < n; base += stride) {
+    const int64_t j = base + lane;
+    const uint32_t t = j < n ? touched[j] : 0u;
+    RowSpan rs{};
+    unsigned g = 0, h = 0, y0 = 0, tb = 0, tw = 0;
+    if (t) {
+      g = sorted_vals[j];
+      const ushort4 r = rect[g];
+      const float4 ra = rec[g].a;
+      rs = make_row_span(ext[g], ra.x, ra.y, mabs, r);
+      const ViewDesc& vd = vt.v[view_of_prim(vt, (int64_t)g)];
+      h = (unsigned)(r.w - r.y);
+      y0 = r.y;
+      tb = (unsigned)vd.tile_base;
+      tw = (unsigned)vd.tiles_x;
     }
-    if (threadIdx.x == 0) s_jlo = lo - 1; else s_jhi = lo - 1;
-  }
-  __syncthreads();
-  const int64_t jlo = s_jlo, jhi = s_jhi;
-  const int wn = (int)(jhi - jlo + 1);  // <= kKeygenEntries (each primitive in the window owns >= 1 entry)
-  for (int k = threadIdx.x; k < wn; k += kThreads) {
-    unsigned long long o = offsets[jlo + k];
-    win[k] = (uint32_t)((o > (unsigned long long)e0 ? o : (unsigned long long)e0) - (unsigned long long)e0);
-  }
-  __syncthreads();
-  // each thread emits a run of kRun consecutive entries: one search for the run's first primitive,
-  // then a walk over the tiles (no division per entry) and 16-byte stores
-  constexpr int kRun = kKeygenEntries / kThreads;
-  const int64_t ea = e0 + (int64_t)threadIdx.x * kRun;
-  if (ea < e1) {
-    const int cnt = (int)min((int64_t)kRun, e1 - ea);
-    const uint32_t rel = (uint32_t)(ea - e0);
-    int lo = 0, hi = wn - 1;  // last k with win[k] <= rel
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (win[mid] <= rel) lo = mid; else hi = mid - 1;
-    }
-    int64_t j = jlo + lo;
-    uint32_t g = sorted_vals[j];
-    ushort4 r = rect[g];
-    uint32_t rw = (uint32_t)(r.z - r.x), area = rw * (uint32_t)(r.w - r.y);
-    uint32_t local = (uint32_t)(ea - (int64_t)offsets[j]);
-    uint32_t ly = local / rw, lx = local - ly * rw;
-    const ViewDesc* vd = &vt.v[view_of_prim(vt, (int64_t)g)];
-    uint32_t kk[kRun], vv[kRun];
-#pragma unroll
-    for (int q = 0; q < kRun; ++q) {
-      kk[q] = (uint32_t)vd->tile_base + ((uint32_t)r.y + ly) * (uint32_t)vd->tiles_x + (uint32_t)r.x + lx;
-      vv[q] = g;
-      if (q + 1 < cnt) {
-        ++local;
-        if (++lx == rw) {
-          lx = 0;
-          ++ly;
-        }
-        if (local == area) {  // the run continues with the next primitive in depth order
-          g = sorted_vals[++j];
-          r = rect[g];
-          rw = (uint32_t)(r.z - r.x);
-          area = rw * (uint32_t)(r.w - r.y);
-          local = lx = ly = 0;
-          vd = &vt.v[view_of_prim(vt, (int64_t)g)];
+    unsigned R;
+    const unsigned hex = warp_excl_scan(h, R);
+    unsigned long long eb = 0;
+    if (lane == 0) eb = offsets[base];
+    eb = __shfl_sync(0xffffffffu, eb, 0);
+    for (unsigned cb = 0; cb < R; cb += 32) {
+      const unsigned s = cb + lane;
+      const int ow = warp_last_le(hex, s);
+      const RowSpan q = shfl_row_span(rs, ow);
+      const unsigned qy0 = __shfl_sync(0xffffffffu, y0, ow);
+      const unsigned qhex = __shfl_sync(0xffffffffu, hex, ow);
+      const unsigned qg = __shfl_sync(0xffffffffu, g, ow);
+      const unsigned qtb = __shfl_sync(0xffffffffu, tb, ow);
+      const unsigned qtw = __shfl_sync(0xffffffffu, tw, ow);
+      unsigned w = 0, kb = 0;
+      if (s < R) {
+        const int ty = (int)(qy0 + (s - qhex));
+        int t0, t1;
+        if (tile_row_span(q, ty, t0, t1)) {
+          w = (unsigned)(t1 - t0 + 1);
+          kb = qtb + (unsigned)ty * qtw + (unsigned)t0;
         }
       }
-    }
-    if (cnt == kRun) {
-      uint4* tk4 = reinterpret_cast<uint4*>(tile_keys + ea);
-      uint4* tv4 = reinterpret_cast<uint4*>(tile_vals + ea);
-#pragma unroll
-      for (int q = 0; q < kRun / 4; ++q) {
-        tk4[q] = make_uint4(kk[4 * q], kk[4 * q + 1], kk[4 * q + 2], kk[4 * q + 3]);
-        tv4[q] = make_uint4(vv[4 * q], vv[4 * q + 1], vv[4 * q + 2], vv[4 * q + 3]);
-      }
-    } else {
-#pragma unroll
-      for (int q = 0; q < kRun; ++q)
-        if (q < cnt) {
-          tile_keys[ea + q] = kk[q];
-          tile_vals[ea + q] = vv[q];
+      unsigned W;
+      const unsigned wex = warp_excl_scan(w, W);
+      for (unsigned x0 = 0; x0 < W; x0 += 32) {
+        const unsigned x = x0 + lane;
+        const int rl = warp_last_le(wex, x);
+        const unsigned rkb = __shfl_sync(0xffffffffu, kb, rl);
+        const unsigned rwex = __shfl_sync(0xffffffffu, wex, rl);
+        const unsigned rg = __shfl_sync(0xffffffffu, qg, rl);
+        const unsigned long long e = eb + x;
+        if (x < W && e < K) {
+          tile_keys[e] = rkb + (x - rwex);
+          tile_vals[e] = rg;
         }
+      }
+      eb += W;
     }
   }
-  }  // entry-block loop
 }
 
 // ---------------------------------------------------------------- K5 ranges
-// one load per element: the neighbours come from the adjacent lanes (the warp's ends load theirs)
+// Four entries per thread (one 16-byte load); a tile starts where an entry differs from its
+// predecessor and ends where it differs from its successor.  Neighbours across threads come from
+// the adjacent lanes; the warp's end lanes load theirs.
 __global__ void k_ranges(const uint32_t* __restrict__ tile_keys, const unsigned long long* __restrict__ K_dev, int64_t cap,
                          uint2* __restrict__ ranges) {
   const int64_t K = (int64_t)*K_dev;
@@ -387,17 +369,28 @@ __global__ void k_ranges(const uint32_t* __restrict__ tile_keys, const unsigned 
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   constexpr uint32_t kNone = 0xffffffffu;  // never a tile id
-  for (int64_t base = wid * 32; base < K; base += nwarps * 32) {
-    const int64_t e = base + lane;
-    const bool ok = e < K;
-    const uint32_t t = ok ? tile_keys[e] : kNone;
-    uint32_t prev = __shfl_up_sync(0xffffffffu, t, 1);
-    uint32_t next = __shfl_down_sync(0xffffffffu, t, 1);
-    if (lane == 0) prev = base > 0 ? tile_keys[base - 1] : kNone;
-    if (lane == 31) next = e + 1 < K ? tile_keys[e + 1] : kNone;
-    if (ok) {
-      if (prev != t) ranges[t].x = (uint32_t)e;
-      if (next != t) ranges[t].y = (uint32_t)(e + 1);
+  const int64_t nq = (K + 3) / 4;
+  for (int64_t base = wid * 32; base < nq; base += nwarps * 32) {
+    const int64_t e = 4 * (base + lane);
+    uint32_t t[4];
+    if (e + 3 < K) {
+      const uint4 v = *reinterpret_cast<const uint4*>(tile_keys + e);
+      t[0] = v.x; t[1] = v.y; t[2] = v.z; t[3] = v.w;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) t[i] = e + i < K ? tile_keys[e + i] : kNone;
+    }
+    uint32_t prev = __shfl_up_sync(0xffffffffu, t[3], 1);
+    uint32_t next = __shfl_down_sync(0xffffffffu, t[0], 1);
+    if (lane == 0) prev = e > 0 && e - 1 < K ? tile_keys[e - 1] : kNone;
+    if (lane == 31) next = e + 4 < K ? tile_keys[e + 4] : kNone;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (e + i >= K) break;
+      const uint32_t p = i == 0 ? prev : t[i - 1];
+      const uint32_t q = i == 3 ? next : t[i + 1];
+      if (p != t[i]) ranges[t[i]].x = (uint32_t)(e + i);
+      if (q != t[i]) ranges[t[i]].y = (uint32_t)(e + i + 1);
     }
   }
 }
@@ -480,12 +473,10 @@ template void scan_exclusive<uint32_t, unsigned long long>(const uint32_t*, unsi
                                                            unsigned long long*, ScanScratch&, cudaStream_t,
                                                            const unsigned long long*);
 
-void launch_gather_touched(const uint32_t* sorted_vals, const ushort4* rect, int64_t n, uint32_t* touched, cudaStream_t s,
-                           const unsigned long long* n_dev) {
+void launch_gather_touched(const uint32_t* sorted_vals, const uint32_t* tprim, int64_t n, uint32_t* touched,
+                           cudaStream_t s, const unsigned long long* n_dev) {
   if (n <= 0) return;
-  int64_t blocks = cdiv(n, 256);
-  if (blocks > 65535 * 8) blocks = 65535 * 8;
-  k_gather_touched<<<(unsigned)blocks, 256, 0, s>>>(sorted_vals, rect, n, n_dev, touched);
+  k_gather_touched<<<grid_cap(cdiv(n, 256), 8), 256, 0, s>>>(sorted_vals, tprim, n, n_dev, touched);
   count_launches(1);
 }
 
@@ -518,20 +509,22 @@ void radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_
 }
 
 template <class VS>
-void launch_keygen(const VS& vs, const unsigned long long* offsets, const unsigned long long* K_dev, int64_t n,
-                   const uint32_t* sorted_vals, const ushort4* rect, int64_t cap, uint32_t* tile_keys, uint32_t* tile_vals,
-                   uint32_t* flags, cudaStream_t s, const unsigned long long* n_dev) {
+void launch_keygen(const VS& vs, const unsigned long long* offsets, const uint32_t* touched,
+                   const unsigned long long* K_dev, int64_t n, const uint32_t* sorted_vals, const ushort4* rect,
+                   const float4* ext, const Rec* rec, float margin_abs, int64_t cap,
+                   uint32_t* tile_keys, uint32_t* tile_vals, uint32_t* flags, cudaStream_t s,
+                   const unsigned long long* n_dev) {
   if (n <= 0 || cap <= 0) return;
-  k_keygen<VS><<<grid_cap(cdiv(cap, kKeygenEntries), 8), kThreads, 0, s>>>(vs, offsets, K_dev, n, n_dev, sorted_vals, rect,
-                                                                        cap, tile_keys, tile_vals, flags);
+  k_keygen<VS><<<grid_cap(cdiv(n, kKeygenThreads), 8), kKeygenThreads, 0, s>>>(
+      vs, offsets, K_dev, n, n_dev, sorted_vals, touched, rect, ext, rec, margin_abs, cap, tile_keys, tile_vals, flags);
   count_launches(1);
 }
 
 void launch_ranges(const uint32_t* tile_keys, const unsigned long long* K_dev, int64_t cap, uint2* ranges, int num_sms,
                    cudaStream_t s) {
   if (cap <= 0) return;
-  int64_t blocks = cdiv(cap, 256);
-  if (blocks > (int64_t)num_sms * 16) blocks = (int64_t)num_sms * 16;
+  int64_t blocks = cdiv(cdiv(cap, 4), 256);
+  if (blocks > (int64_t)num_sms * 8) blocks = (int64_t)num_sms * 8;
   k_ranges<<<(unsigned)blocks, 256, 0, s>>>(tile_keys, K_dev, cap, ranges);
   count_launches(1);
 }
@@ -545,11 +538,13 @@ void launch_make_keys(const uint32_t* tile_keys, const uint32_t* tile_vals, cons
   count_launches(1);
 }
 
-template void launch_keygen<FrameViews>(const FrameViews&, const unsigned long long*, const unsigned long long*, int64_t,
-                                        const uint32_t*, const ushort4*, int64_t, uint32_t*, uint32_t*, uint32_t*,
+template void launch_keygen<FrameViews>(const FrameViews&, const unsigned long long*, const uint32_t*,
+                                        const unsigned long long*, int64_t, const uint32_t*, const ushort4*,
+                                        const float4*, const Rec*, float, int64_t, uint32_t*, uint32_t*, uint32_t*,
                                         cudaStream_t, const unsigned long long*);
-template void launch_keygen<BatchViews>(const BatchViews&, const unsigned long long*, const unsigned long long*, int64_t,
-                                        const uint32_t*, const ushort4*, int64_t, uint32_t*, uint32_t*, uint32_t*,
+template void launch_keygen<BatchViews>(const BatchViews&, const unsigned long long*, const uint32_t*,
+                                        const unsigned long long*, int64_t, const uint32_t*, const ushort4*,
+                                        const float4*, const Rec*, float, int64_t, uint32_t*, uint32_t*, uint32_t*,
                                         cudaStream_t, const unsigned long long*);
 
 }  // namespace ges
