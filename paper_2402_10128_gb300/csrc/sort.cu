@@ -155,11 +155,12 @@ __global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restr
   }
 }
 
-// Stable scatter.  Warp w of the CTA owns chunk elements [w*512, (w+1)*512) and walks them in
-// order, 32 at a time; lanes with equal digits are ranked by lane order (match.any), so ranks
-// preserve input order within each digit.  The chunk is first reordered by digit in shared
-// memory, then written out so that consecutive threads store consecutive positions of one
-// digit's run (coalesced).
+// Stable scatter.  Warp w of the CTA owns chunk elements [w*256, (w+1)*256) and walks them in
+// order, 32 at a time.  Lanes with equal digits (found with one ballot per digit bit) are ranked
+// by lane order; the group's first lane adds the group size to the warp's running count of that
+// digit with a shared-memory atomic and hands the old count to the group with a shuffle, so ranks
+// preserve input order within each digit.  The chunk is then reordered by digit in shared memory
+// and written out so that consecutive threads store consecutive positions of one digit's run.
 constexpr int kScThreads = 512;                 // scatter CTA: twice the warps of the other kernels
 constexpr int kScItems = kChunk / kScThreads;   // 8 items per thread, same chunk
 
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(kScThreads) k_radix_scatter(const uint32_t* __
                                                             int64_t cap, int shift, int bits,
                                                             const uint32_t* __restrict__ hist_scanned) {
   constexpr int kWarps = kScThreads / 32;
-  __shared__ uint16_t wcnt[kWarps][257];  // per warp and digit: at most 256 items, prefixes at most kChunk
+  __shared__ __align__(16) uint32_t wcnt[kWarps][256];  // per warp and digit: running count, then prefix
   __shared__ uint32_t goff[256];
   __shared__ uint32_t bstart[257];
   __shared__ uint32_t wsum[kWarps];
@@ -186,7 +187,10 @@ __global__ void __launch_bounds__(kScThreads) k_radix_scatter(const uint32_t* __
   const int64_t base = c * kChunk;
   const int count = (int)min((int64_t)kChunk, n - base);
   __syncthreads();  // the previous chunk's readers of the shared arrays are done
-  for (int i = threadIdx.x; i < kWarps * 257; i += kScThreads) (&wcnt[0][0])[i] = 0;
+  {
+    uint4* z = reinterpret_cast<uint4*>(&wcnt[0][0]);
+    for (int i = threadIdx.x; i < kWarps * 256 / 4; i += kScThreads) z[i] = make_uint4(0u, 0u, 0u, 0u);
+  }
   for (int b = threadIdx.x; b < nbins; b += kScThreads) goff[b] = hist_scanned[(int64_t)b * nchunks + c];
   __syncthreads();
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -197,12 +201,22 @@ __global__ void __launch_bounds__(kScThreads) k_radix_scatter(const uint32_t* __
     const bool ok = li < count;
     key[r] = ok ? keys_in[base + li] : 0u;
     val[r] = ok ? vals_in[base + li] : 0u;
-    const int d = ok ? (int)((key[r] >> shift) & mask) : 256;
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
-    const uint32_t prev = wcnt[w][d];
-    __syncwarp();
-    if ((peers & lt_mask) == 0) wcnt[w][d] = (uint16_t)(prev + (uint32_t)__popc(peers));
-    __syncwarp();
+  }
+#pragma unroll
+  for (int r = 0; r < kScItems; ++r) {
+    const int li = w * (kScItems * 32) + r * 32 + (int)lane;
+    const bool ok = li < count;
+    const uint32_t d = (key[r] >> shift) & mask;
+    unsigned peers = __ballot_sync(0xffffffffu, ok);
+    for (int b = 0; b < bits; ++b) {
+      const bool bit = (d >> b) & 1u;
+      const unsigned bal = __ballot_sync(0xffffffffu, bit);
+      peers &= bit ? bal : ~bal;
+    }
+    const int leader = peers ? __ffs(peers) - 1 : 0;
+    uint32_t prev = 0;
+    if (ok && (int)lane == leader) prev = atomicAdd(&wcnt[w][d], (uint32_t)__popc(peers));
+    prev = __shfl_sync(0xffffffffu, prev, leader);
     rank[r] = prev + (uint32_t)__popc(peers & lt_mask);
   }
   __syncthreads();
@@ -213,7 +227,7 @@ __global__ void __launch_bounds__(kScThreads) k_radix_scatter(const uint32_t* __
 #pragma unroll
     for (int ww = 0; ww < kWarps; ++ww) {
       uint32_t cw = wcnt[ww][b];
-      wcnt[ww][b] = (uint16_t)total;
+      wcnt[ww][b] = total;
       total += cw;
     }
   }
