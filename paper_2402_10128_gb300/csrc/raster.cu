@@ -140,24 +140,67 @@ __global__ void __launch_bounds__(kFwdThreads) k_render_fwd_persistent(const __g
   }
 }
 
-// Sums 16 per-lane values over the warp with a reduce-scatter butterfly (16 shuffles instead of
-// 16 x 5): at each step a lane keeps half of its values and receives the partner's copy of that
-// half.  On return lane L holds the full sum of value ((L >> 1) & 15) (L and L^1 hold the same).
-__device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16]) {
+// Sums 10 per-lane values over the warp with a reduce-scatter butterfly: at each step a lane keeps
+// half of its values (the odd one out padded with a zero) and receives the partner's copy of that
+// half, 12 shuffles in all.  On return the lane holds the full sum of value reduce10_slot(lane), or
+// of a padding zero where that is -1; lanes L and L^1 hold the same.
+__device__ __forceinline__ float warp_reduce_scatter10(float (&v)[10]) {
   const unsigned lane = threadIdx.x & 31u;
+  const bool u16 = lane & 16u, u8 = lane & 8u, u4 = lane & 4u, u2 = lane & 2u;
 #pragma unroll
-  for (int step = 0; step < 4; ++step) {
-    const int half = 8 >> step;          // values kept after this step
-    const int o = 16 >> step;            // partner distance
-    const bool upper = (lane & (unsigned)o) != 0;
-#pragma unroll
-    for (int k = 0; k < half; ++k) {
-      const float send = upper ? v[k] : v[k + half];
-      const float keep = upper ? v[k + half] : v[k];
-      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-    }
+  for (int k = 0; k < 5; ++k) {  // 10 -> 5: lower half keeps 0..4, upper keeps 5..9
+    const float send = u16 ? v[k] : v[k + 5];
+    const float keep = u16 ? v[k + 5] : v[k];
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
   }
-  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+  float w[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {  // 5 (+1 zero) -> 3
+    const float hi = k + 3 < 5 ? v[k + 3] : 0.0f;
+    const float send = u8 ? v[k] : hi;
+    const float keep = u8 ? hi : v[k];
+    w[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  float x[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {  // 3 (+1 zero) -> 2
+    const float hi = k + 2 < 3 ? w[k + 2] : 0.0f;
+    const float send = u4 ? w[k] : hi;
+    const float keep = u4 ? hi : w[k];
+    x[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  const float send = u2 ? x[0] : x[1];
+  const float keep = u2 ? x[1] : x[0];
+  const float y = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  return y + __shfl_xor_sync(0xffffffffu, y, 1);
+}
+
+// which of the 10 values warp_reduce_scatter10 leaves on a lane (-1: a padding zero)
+__device__ __forceinline__ int reduce10_slot(unsigned lane) {
+  const int t3 = ((lane & 4u) ? 2 : 0) + ((lane & 2u) ? 1 : 0);  // position among the kept three
+  if (t3 > 2) return -1;
+  const int p6 = ((lane & 8u) ? 3 : 0) + t3;                      // position among the kept five
+  if (p6 > 4) return -1;
+  return ((lane & 16u) ? 5 : 0) + p6;
+}
+
+// A fragment's record as the backward composite reads it: every value the two pixels of a thread
+// share is stored twice, so that one 16-byte shared load gives two ready float2 operands.
+struct RecPair {
+  float4 m;    // -mx, -mx, -my, -my
+  float4 e;    // q limit x2, beta/2 x2
+  float4 c0;   // conic a x2, 2 conic b x2
+  float4 c1;   // conic c x2, kappa x2
+  float4 n0;   // -2 conic a x2, -2 conic b x2
+  float4 n1;   // -2 conic c x2, (unused)
+  float4 k0;   // r x2, g x2
+  float4 k1;   // b x2, (unused)
+};
+
+__device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 sel2(bool a, bool b, float2 v, float2 z) {
+  return make_float2(a ? v.x : z.x, b ? v.y : z.y);
 }
 
 // Backward.  Per pixel, walks its contributors back to front, recovering T_i = T_{i+1}/(1-alpha_i)
@@ -166,14 +209,17 @@ __device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16]) {
 //   dalpha/dkappa = G, dalpha/dG = kappa (0 where alpha is clamped)
 //   dG/dp = -G/2,  p = q^hb:  dp/dq = hb p / q,  dp/dhb = p ln q  (0 for q < 1e-12)
 //   q = a dx^2 + 2 b dx dy + c dy^2, dx = px - mx
-// A thread sums its two pixels' terms, the warp sums by a reduce-scatter butterfly, and ten lanes
-// add the ten per-primitive sums with one atomic each.  Reciprocals use the approximate MUFU
-// instruction (about 1 ulp); they only scale gradients, never decide a branch.
+// A thread's two pixels share x and the fragment, so their arithmetic runs as float2 pairs (one
+// packed instruction for both).  The fragment test is eval_fragment's arithmetic, operation for
+// operation, so the skip / clamp / stop decisions equal the forward's bit for bit.  A thread sums
+// its two pixels' terms, the warp sums by a reduce-scatter butterfly, and ten lanes add the ten
+// per-primitive sums with one atomic each.  Reciprocals use the approximate MUFU instruction
+// (about 1 ulp); they only scale gradients, never decide a branch.
 template <class VS>
 __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__ VS vs, const uint2* __restrict__ ranges,
                                                          const uint32_t* __restrict__ vals, const Rec* __restrict__ rec,
                                                          const Params P, float4* __restrict__ g2d) {
-  __shared__ Rec batch[kBatch];
+  __shared__ RecPair batch[kBatch];
   __shared__ uint32_t ids[kBatch];
   __shared__ uint32_t s_max_last;
   const auto& vt = vs.get();
@@ -183,28 +229,32 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
   const uint2 rg = ranges[tile];
   const int64_t plane = (int64_t)vd.W * vd.H;
 
-  float px[2], py[2], T[2], gC0[2], gC1[2], gC2[2], S0[2], S1[2], S2[2];
+  float Tk[2], gc[3][2];
   uint32_t last[2];
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     const int y = wb.y + 4 * k;
     const bool inside = wb.x < vd.W && y < vd.H;
-    px[k] = (float)wb.x + 0.5f;
-    py[k] = (float)y + 0.5f;
-    T[k] = 0.f; gC0[k] = gC1[k] = gC2[k] = 0.f;
+    Tk[k] = 0.f;
+    gc[0][k] = gc[1][k] = gc[2][k] = 0.f;
     last[k] = 0;
     if (inside) {
       const int64_t pix = (int64_t)y * vd.W + wb.x;
-      T[k] = vd.final_T[pix];
+      Tk[k] = vd.final_T[pix];
       last[k] = vd.n_contrib[pix];
-      gC0[k] = vd.dL_dimg[pix];
-      gC1[k] = vd.dL_dimg[plane + pix];
-      gC2[k] = vd.dL_dimg[2 * plane + pix];
+      gc[0][k] = vd.dL_dimg[pix];
+      gc[1][k] = vd.dL_dimg[plane + pix];
+      gc[2][k] = vd.dL_dimg[2 * plane + pix];
     }
-    S0[k] = T[k] * vd.bg[0];
-    S1[k] = T[k] * vd.bg[1];
-    S2[k] = T[k] * vd.bg[2];
   }
+  const float2 PX = make_float2((float)wb.x + 0.5f, (float)wb.x + 0.5f);
+  const float2 PY = make_float2((float)wb.y + 0.5f, (float)(wb.y + 4) + 0.5f);
+  const float2 GC0 = make_float2(gc[0][0], gc[0][1]), GC1 = make_float2(gc[1][0], gc[1][1]),
+               GC2 = make_float2(gc[2][0], gc[2][1]);
+  float2 T = make_float2(Tk[0], Tk[1]);
+  float2 S0 = __fmul2_rn(T, make_float2(vd.bg[0], vd.bg[0]));
+  float2 S1 = __fmul2_rn(T, make_float2(vd.bg[1], vd.bg[1]));
+  float2 S2 = __fmul2_rn(T, make_float2(vd.bg[2], vd.bg[2]));
   if (threadIdx.x == 0) s_max_last = 0;
   __syncthreads();
   atomicMax(&s_max_last, max(last[0], last[1]));
@@ -212,8 +262,12 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
   const uint32_t max_last = s_max_last;
   const uint32_t wlast = __reduce_max_sync(0xffffffffu, max(last[0], last[1]));
   const bool gef = P.mode == 0;
-  const float ln2 = 0.69314718055994531f;
   const unsigned lane = threadIdx.x & 31u;
+  const int slot = reduce10_slot(lane);
+  const bool adder = (lane & 1u) == 0 && slot >= 0;
+  const float2 ONE = make_float2(1.0f, 1.0f), NEG1 = make_float2(-1.0f, -1.0f), ZERO = make_float2(0.f, 0.f);
+  const float2 NHL = make_float2(kNegHalfLog2e, kNegHalfLog2e), NHALF = make_float2(-0.5f, -0.5f);
+  const float2 LN2 = make_float2(0.69314718055994531f, 0.69314718055994531f);
 
   for (uint32_t end = rg.x + max_last; end > rg.x;) {
     const uint32_t start = (end - rg.x > (uint32_t)kBatch) ? end - kBatch : rg.x;
@@ -221,67 +275,97 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
     const uint32_t idx = start + threadIdx.x;
     if (idx < end) {
       const uint32_t g = vals[idx];
+      const Rec r = rec[g];
       ids[threadIdx.x] = g;
-      batch[threadIdx.x] = rec[g];
+      RecPair& d = batch[threadIdx.x];
+      d.m = make_float4(-r.a.x, -r.a.x, -r.a.y, -r.a.y);
+      d.e = make_float4(r.a.z, r.a.z, r.a.w, r.a.w);
+      const float tb = __fmul_rn(2.0f, r.b.y);
+      d.c0 = make_float4(r.b.x, r.b.x, tb, tb);
+      d.c1 = make_float4(r.b.z, r.b.z, r.b.w, r.b.w);
+      d.n0 = make_float4(-2.0f * r.b.x, -2.0f * r.b.x, -tb, -tb);
+      d.n1 = make_float4(-2.0f * r.b.z, -2.0f * r.b.z, 0.f, 0.f);
+      d.k0 = make_float4(r.c.x, r.c.x, r.c.y, r.c.y);
+      d.k1 = make_float4(r.c.z, r.c.z, 0.f, 0.f);
     }
     __syncthreads();
     for (int j = (int)(end - start) - 1; j >= 0; --j) {
       const uint32_t kpos = start - rg.x + (uint32_t)j + 1u;  // 1-based position in the tile's list
       if (kpos > wlast) continue;                             // beyond every pixel of this warp
-      const Rec r = batch[j];
-      float g[16];
-#pragma unroll
-      for (int t = 0; t < 16; ++t) g[t] = 0.f;
-      bool contrib = false;
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        if (kpos > last[k]) continue;
-        FragEval f;
-        eval_fragment(r, px[k], py[k], P.alpha_max, f);
-        if (f.alpha < P.alpha_min) continue;
-        contrib = true;
-        const float inv = rcp_approx(1.0f - f.alpha);
-        T[k] *= inv;
-        const float w = f.alpha * T[k];
-        const float dLda = gC0[k] * (r.c.x * T[k] - S0[k] * inv) + gC1[k] * (r.c.y * T[k] - S1[k] * inv) +
-                           gC2[k] * (r.c.z * T[k] - S2[k] * inv);
-        S0[k] = fmaf(r.c.x, w, S0[k]);
-        S1[k] = fmaf(r.c.y, w, S1[k]);
-        S2[k] = fmaf(r.c.z, w, S2[k]);
-        g[7] += gC0[k] * w;
-        g[8] += gC1[k] * w;
-        g[9] += gC2[k] * w;
-        const float dG = f.clamped ? 0.f : dLda * r.b.w;
-        g[5] += f.clamped ? 0.f : dLda * f.G;
-        const float dp = dG * (-0.5f * f.G);
-        float dq;
-        if (gef) {
-          if (f.q > 1e-12f) {
-            if (r.a.w == 1.0f) {
-              dq = dp;
-              g[6] += dp * f.q * (mufu_lg2(f.q) * ln2);
-            } else {
-              dq = dp * r.a.w * f.p * rcp_approx(f.q);
-              g[6] += dp * f.p * (f.lq * ln2);
-            }
-          } else {
-            dq = 0.f;
-          }
+      const float4 m = batch[j].m, e = batch[j].e, c0 = batch[j].c0, c1 = batch[j].c1;
+      // eval_fragment on both pixels
+      const float2 dx = __fadd2_rn(PX, lo2(m));
+      const float2 dy = __fadd2_rn(PY, hi2(m));
+      const float2 t = __ffma2_rn(hi2(c0), dy, __fmul2_rn(lo2(c0), dx));
+      const float2 q2 = __ffma2_rn(__fmul2_rn(lo2(c1), dy), dy, __fmul2_rn(t, dx));
+      const float q0 = fmaxf(q2.x, 0.0f), q1 = fmaxf(q2.y, 0.0f);
+      const float ql = e.x, hb = e.z;
+      const bool in0 = q0 <= ql, in1 = q1 <= ql;
+      float2 p, lq;
+      if (hb == 1.0f) {
+        p = make_float2(q0, q1);
+        lq = ZERO;
+      } else {
+        lq = make_float2(mufu_lg2(q0), mufu_lg2(q1));
+        const float2 hl = __fmul2_rn(hi2(e), lq);
+        p = make_float2(mufu_ex2(hl.x), mufu_ex2(hl.y));
+      }
+      const float2 ge = __fmul2_rn(NHL, p);
+      const float2 G = make_float2(mufu_ex2(ge.x), mufu_ex2(ge.y));
+      const float2 a = __fmul2_rn(hi2(c1), G);
+      const bool cl0 = a.x > P.alpha_max, cl1 = a.y > P.alpha_max;
+      const float al0 = cl0 ? P.alpha_max : a.x, al1 = cl1 ? P.alpha_max : a.y;
+      const bool act0 = kpos <= last[0] && in0 && al0 >= P.alpha_min;
+      const bool act1 = kpos <= last[1] && in1 && al1 >= P.alpha_min;
+      if (!__any_sync(0xffffffffu, act0 || act1)) continue;
+      // gradient terms of both pixels (zero for an inactive one, whose T and S stay as they are)
+      const float4 n0 = batch[j].n0, n1 = batch[j].n1, k0 = batch[j].k0, k1 = batch[j].k1;
+      const float2 alpha = make_float2(act0 ? al0 : 0.f, act1 ? al1 : 0.f);
+      const float2 om = __ffma2_rn(alpha, NEG1, ONE);
+      const float2 inv = make_float2(act0 ? rcp_approx(om.x) : 1.0f, act1 ? rcp_approx(om.y) : 1.0f);
+      T = __fmul2_rn(T, inv);
+      const float2 w = __fmul2_rn(alpha, T);
+      const float2 ninv = __fmul2_rn(inv, NEG1);
+      const float2 B0 = __ffma2_rn(S0, ninv, __fmul2_rn(lo2(k0), T));
+      const float2 B1 = __ffma2_rn(S1, ninv, __fmul2_rn(hi2(k0), T));
+      const float2 B2 = __ffma2_rn(S2, ninv, __fmul2_rn(lo2(k1), T));
+      float2 dLda = __ffma2_rn(GC2, B2, __ffma2_rn(GC1, B1, __fmul2_rn(GC0, B0)));
+      dLda = sel2(act0, act1, dLda, ZERO);
+      S0 = __ffma2_rn(lo2(k0), w, S0);
+      S1 = __ffma2_rn(hi2(k0), w, S1);
+      S2 = __ffma2_rn(lo2(k1), w, S2);
+      const float2 gr = __fmul2_rn(GC0, w), gg = __fmul2_rn(GC1, w), gbl = __fmul2_rn(GC2, w);
+      const float2 kG = sel2(!cl0, !cl1, hi2(c1), ZERO);
+      const float2 Gm = sel2(!cl0, !cl1, G, ZERO);
+      const float2 dG = __fmul2_rn(dLda, kG);
+      const float2 gk = __fmul2_rn(dLda, Gm);
+      const float2 dp = __fmul2_rn(dG, __fmul2_rn(NHALF, G));
+      float2 dq, gbeta = ZERO;
+      if (gef) {
+        const bool m0 = act0 && q0 > 1e-12f, m1 = act1 && q1 > 1e-12f;
+        if (hb == 1.0f) {
+          dq = sel2(m0, m1, dp, ZERO);
+          const float2 l2 = make_float2(m0 ? mufu_lg2(q0) : 0.f, m1 ? mufu_lg2(q1) : 0.f);
+          gbeta = __fmul2_rn(__fmul2_rn(dq, make_float2(q0, q1)), __fmul2_rn(l2, LN2));
         } else {
-          dq = dp;
+          const float2 pm = sel2(m0, m1, p, ZERO);
+          const float2 rq = make_float2(m0 ? rcp_approx(q0) : 0.f, m1 ? rcp_approx(q1) : 0.f);
+          dq = __fmul2_rn(__fmul2_rn(dp, hi2(e)), __fmul2_rn(pm, rq));
+          gbeta = __fmul2_rn(__fmul2_rn(dp, pm), __fmul2_rn(sel2(m0, m1, lq, ZERO), LN2));
         }
-        const float dqdx = dq * f.dx, dqdy = dq * f.dy;
-        g[0] -= 2.f * (r.b.x * dqdx + r.b.y * dqdy);
-        g[1] -= 2.f * (r.b.y * dqdx + r.b.z * dqdy);
-        g[2] += dqdx * f.dx;
-        g[3] += 2.f * dqdx * f.dy;
-        g[4] += dqdy * f.dy;
+      } else {
+        dq = dp;
       }
-      if (__any_sync(0xffffffffu, contrib)) {
-        const float sum = warp_reduce_scatter16(g);
-        const unsigned slot = (lane >> 1) & 15u;
-        if ((lane & 1u) == 0 && slot < 10u) atomicAdd(reinterpret_cast<float*>(g2d + 3 * (int64_t)ids[j]) + slot, sum);
-      }
+      const float2 dqdx = __fmul2_rn(dq, dx), dqdy = __fmul2_rn(dq, dy);
+      const float2 gmx = __ffma2_rn(dqdy, hi2(n0), __fmul2_rn(dqdx, lo2(n0)));
+      const float2 gmy = __ffma2_rn(dqdy, lo2(n1), __fmul2_rn(dqdx, hi2(n0)));
+      const float2 ga = __fmul2_rn(dqdx, dx);
+      const float2 gb = __fmul2_rn(dqdx, __fadd2_rn(dy, dy));
+      const float2 gcc = __fmul2_rn(dqdy, dy);
+      float v[10] = {gmx.x + gmx.y, gmy.x + gmy.y, ga.x + ga.y,   gb.x + gb.y,   gcc.x + gcc.y,
+                     gk.x + gk.y,   gbeta.x + gbeta.y, gr.x + gr.y, gg.x + gg.y, gbl.x + gbl.y};
+      const float sum = warp_reduce_scatter10(v);
+      if (adder) atomicAdd(reinterpret_cast<float*>(g2d + 3 * (int64_t)ids[j]) + slot, sum);
     }
     end = start;
   }
