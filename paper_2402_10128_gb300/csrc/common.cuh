@@ -233,38 +233,6 @@ __device__ __forceinline__ float mufu_lg2(float x) {
 
 constexpr float kNegHalfLog2e = -0.72134752044448170f;  // -1/2 log2(e): exp(-p/2) = 2^(kNegHalfLog2e p)
 
-struct FragEval {
-  float dx, dy, q, p, G, alpha, lq;  // lq = log2 q (GEF exponent path only)
-  bool in_range, clamped;
-};
-
-// q = d^T conic d with d = pixel - mean; p = q^hb; G = exp(-p/2); alpha = min(alpha_max, kappa G)
-__device__ __forceinline__ void eval_fragment(const Rec& r, float px, float py, float alpha_max, FragEval& f) {
-  f.dx = __fsub_rn(px, r.a.x);
-  f.dy = __fsub_rn(py, r.a.y);
-  // q = (a dx + 2 b dy) dx + c dy dy
-  float t = __fmaf_rn(__fmul_rn(2.0f, r.b.y), f.dy, __fmul_rn(r.b.x, f.dx));
-  f.q = __fmaf_rn(__fmul_rn(r.b.z, f.dy), f.dy, __fmul_rn(t, f.dx));
-  f.q = fmaxf(f.q, 0.0f);
-  f.in_range = f.q <= r.a.z;  // beyond the extent alpha < alpha_min; decided without the MUFU work
-  if (!f.in_range) {
-    f.p = f.G = f.alpha = f.lq = 0.0f;
-    f.clamped = false;
-    return;
-  }
-  if (r.a.w == 1.0f) {
-    f.p = f.q;
-    f.lq = 0.f;
-  } else {
-    f.lq = mufu_lg2(f.q);
-    f.p = mufu_ex2(__fmul_rn(r.a.w, f.lq));
-  }
-  f.G = mufu_ex2(__fmul_rn(kNegHalfLog2e, f.p));
-  float a = __fmul_rn(r.b.w, f.G);
-  f.clamped = a > alpha_max;
-  f.alpha = f.clamped ? alpha_max : a;
-}
-
 // Real SH basis (l-major, m = -l..l, Condon-Shortley phase), Cartesian polynomial forms on
 // the unit direction; normalisations K_lm = sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) (times
 // sqrt 2 for m != 0) folded into the constants below.

@@ -5,12 +5,12 @@
 // with alpha_i = min(alpha_max, kappa_i G_i) and the GES falloff G = exp(-1/2 q^(beta/2))
 // (Sec. 3.1, Eq. ges) or the paper's Gaussian-form rasterizer G = exp(-1/2 q).
 //
-// Forward: one CTA of 256 threads per 16x16 tile, one pixel per thread, warps on 8x4 blocks.
-// Backward: one CTA of 128 threads per tile, two pixels per thread, (x, y) and (x, y + 4), so a
-// warp covers an 8x8 block and its per-fragment gradient sum is shared by 64 pixels.  The tile's
-// list is staged in shared memory one record per thread per round.  Both kernels evaluate every
-// (fragment, pixel) pair with eval_fragment, so they take the same skip / clamp / stop decisions
-// bit for bit whatever their thread layout.
+// Both kernels run one CTA of 128 threads per 16x16 tile, two pixels per thread, (x, y) and
+// (x, y + 4), so a warp covers an 8x8 block (and, backward, its per-fragment gradient sum is shared
+// by 64 pixels).  The two pixels share x and every fragment, so their arithmetic runs as packed
+// float2 pairs, one instruction for both.  The tile's list is staged in shared memory one record
+// per thread per round.  Both kernels evaluate every (fragment, pixel) pair with eval_pair, so
+// they take the same skip / clamp / stop decisions bit for bit.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -20,13 +20,77 @@ namespace {
 
 constexpr int kThreads = 128;  // backward, per tile
 constexpr int kBatch = kThreads;
-constexpr int kFwdThreads = 256;
+constexpr int kFwdThreads = 128;
 constexpr int kFwdBatch = kFwdThreads;
 
 __device__ __forceinline__ float rcp_approx(float x) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
+}
+
+// A fragment's record as the composite kernels read it: every value the two pixels of a thread
+// share is stored twice, so that one 16-byte shared load gives two ready float2 operands.
+struct RecPair {
+  float4 m;    // -mx, -mx, -my, -my
+  float4 e;    // q limit x2, beta/2 x2
+  float4 c0;   // conic a x2, 2 conic b x2
+  float4 c1;   // conic c x2, kappa x2
+  float4 k0;   // r x2, g x2
+  float4 k1;   // b x2, (unused)
+};
+// the backward's copy adds the conic terms of the mean gradient
+struct RecPairB : RecPair {
+  float4 n0;   // -2 conic a x2, -2 conic b x2
+  float4 n1;   // -2 conic c x2, (unused)
+};
+
+__device__ __forceinline__ void stage_pair(RecPair& d, const Rec& r) {
+  d.m = make_float4(-r.a.x, -r.a.x, -r.a.y, -r.a.y);
+  d.e = make_float4(r.a.z, r.a.z, r.a.w, r.a.w);
+  const float tb = __fmul_rn(2.0f, r.b.y);
+  d.c0 = make_float4(r.b.x, r.b.x, tb, tb);
+  d.c1 = make_float4(r.b.z, r.b.z, r.b.w, r.b.w);
+  d.k0 = make_float4(r.c.x, r.c.x, r.c.y, r.c.y);
+  d.k1 = make_float4(r.c.z, r.c.z, 0.f, 0.f);
+}
+
+__device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 sel2(bool a, bool b, float2 v, float2 z) {
+  return make_float2(a ? v.x : z.x, b ? v.y : z.y);
+}
+
+// The fragment test on a thread's two pixels (PX, PY; both share x), with explicit round-to-
+// nearest intrinsics so that the compiler cannot contract it differently in the two kernels:
+//   d = pixel - mean, q = max(0, (a dx + 2 b dy) dx + c dy dy),
+//   p = q^hb = 2^(hb log2 q) (p = q at hb = 1), G = exp(-p/2) = 2^(-p log2(e)/2), a = kappa G;
+// the caller takes alpha = min(alpha_max, a) and skips the fragment where alpha < alpha_min.
+// No separate test against the extent's q limit is needed: beyond it kappa G < alpha_min by
+// construction of the extent.
+struct PairEval {
+  float2 dx, dy, p, lq, G, a;
+  float q0, q1;
+};
+__device__ __forceinline__ void eval_pair(const RecPair& r, float2 PX, float2 PY, PairEval& f) {
+  const float4 m = r.m, e = r.e, c0 = r.c0, c1 = r.c1;
+  f.dx = __fadd2_rn(PX, lo2(m));
+  f.dy = __fadd2_rn(PY, hi2(m));
+  const float2 t = __ffma2_rn(hi2(c0), f.dy, __fmul2_rn(lo2(c0), f.dx));
+  const float2 q2 = __ffma2_rn(__fmul2_rn(lo2(c1), f.dy), f.dy, __fmul2_rn(t, f.dx));
+  f.q0 = fmaxf(q2.x, 0.0f);
+  f.q1 = fmaxf(q2.y, 0.0f);
+  if (e.z == 1.0f) {
+    f.p = make_float2(f.q0, f.q1);
+    f.lq = make_float2(0.f, 0.f);
+  } else {
+    f.lq = make_float2(mufu_lg2(f.q0), mufu_lg2(f.q1));
+    const float2 hl = __fmul2_rn(hi2(e), f.lq);
+    f.p = make_float2(mufu_ex2(hl.x), mufu_ex2(hl.y));
+  }
+  const float2 ge = __fmul2_rn(make_float2(kNegHalfLog2e, kNegHalfLog2e), f.p);
+  f.G = make_float2(mufu_ex2(ge.x), mufu_ex2(ge.y));
+  f.a = __fmul2_rn(hi2(c1), f.G);
 }
 
 struct WarpBlock {
@@ -44,55 +108,76 @@ __device__ __forceinline__ WarpBlock warp_block(int lt, int tiles_x) {
 }
 
 template <int MAXV, bool STATS>
-__device__ __forceinline__ void render_tile_fwd(const ViewTable<MAXV>& vt, int64_t tile, Rec* batch,
+__device__ __forceinline__ void render_tile_fwd(const ViewTable<MAXV>& vt, int64_t tile, RecPair* batch,
                                                 const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                                                 const Rec* __restrict__ rec, const Params& P,
                                                 unsigned long long* __restrict__ stats) {
   const ViewDesc& vd = vt.v[view_of_tile(vt, tile)];
-  const int lt = (int)(tile - vd.tile_base);
-  const int tx = lt % vd.tiles_x, ty = lt / vd.tiles_x;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int x = tx * kTile + (w & 1) * 8 + (lane & 7);
-  const int y = ty * kTile + (w >> 1) * 4 + (lane >> 3);
-  const bool inside = x < vd.W && y < vd.H;
-  const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+  const WarpBlock wb = warp_block((int)(tile - vd.tile_base), vd.tiles_x);
+  const bool inside0 = wb.x < vd.W && wb.y < vd.H, inside1 = wb.x < vd.W && wb.y + 4 < vd.H;
+  const float2 PX = make_float2((float)wb.x + 0.5f, (float)wb.x + 0.5f);
+  const float2 PY = make_float2((float)wb.y + 0.5f, (float)(wb.y + 4) + 0.5f);
+  const float2 ONE = make_float2(1.0f, 1.0f), NEG1 = make_float2(-1.0f, -1.0f), ZERO = make_float2(0.f, 0.f);
   const uint2 rg = ranges[tile];
-  float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-  uint32_t last = 0, n_eval = 0, n_range = 0, n_comp = 0;
-  bool done = !inside;
+  float2 T = ONE, C0 = ZERO, C1 = ZERO, C2 = ZERO;
+  uint32_t last0 = 0, last1 = 0, n_eval = 0, n_range = 0, n_comp = 0;
+  bool done0 = !inside0, done1 = !inside1;
   for (uint32_t base = rg.x; base < rg.y; base += kFwdBatch) {
-    if (__syncthreads_count(done) == kFwdThreads) break;
+    if (__syncthreads_count(done0 && done1) == kFwdThreads) break;
     const uint32_t idx = base + threadIdx.x;
-    if (idx < rg.y) batch[threadIdx.x] = rec[vals[idx]];
+    if (idx < rg.y) stage_pair(batch[threadIdx.x], rec[vals[idx]]);
     __syncthreads();
     const int cnt = (int)min((uint32_t)kFwdBatch, rg.y - base);
-    if (!__all_sync(0xffffffffu, done)) {
+    if (!__all_sync(0xffffffffu, done0 && done1)) {
       for (int j = 0; j < cnt; ++j) {
-        if (done) break;
-        const Rec r = batch[j];
-        FragEval f;
-        eval_fragment(r, px, py, P.alpha_max, f);
-        if (STATS) { ++n_eval; n_range += f.in_range ? 1u : 0u; }
-        if (f.alpha < P.alpha_min) continue;
-        const float Tn = T * (1.0f - f.alpha);
-        if (Tn < P.t_min) { done = true; break; }
-        const float wgt = f.alpha * T;
-        C0 = fmaf(r.c.x, wgt, C0);
-        C1 = fmaf(r.c.y, wgt, C1);
-        C2 = fmaf(r.c.z, wgt, C2);
-        T = Tn;
-        last = base - rg.x + (uint32_t)j + 1u;
-        if (STATS) ++n_comp;
+        if (done0 && done1) break;
+        PairEval f;
+        eval_pair(batch[j], PX, PY, f);
+        if (STATS) {
+          const float ql = batch[j].e.x;
+          n_eval += (done0 ? 0u : 1u) + (done1 ? 0u : 1u);
+          n_range += (!done0 && f.q0 <= ql ? 1u : 0u) + (!done1 && f.q1 <= ql ? 1u : 0u);
+        }
+        const float2 al = make_float2(fminf(f.a.x, P.alpha_max), fminf(f.a.y, P.alpha_max));
+        const float2 Tn = __fmul2_rn(T, __ffma2_rn(al, NEG1, ONE));
+        bool c0 = !done0 && al.x >= P.alpha_min;
+        bool c1 = !done1 && al.y >= P.alpha_min;
+        const bool s0 = c0 && Tn.x < P.t_min, s1 = c1 && Tn.y < P.t_min;
+        done0 = done0 || s0;
+        done1 = done1 || s1;
+        c0 = c0 && !s0;
+        c1 = c1 && !s1;
+        // composite: alpha is zero for a pixel that does not take this fragment, so T and C stay
+        const float2 alpha = make_float2(c0 ? al.x : 0.f, c1 ? al.y : 0.f);
+        const float2 wgt = __fmul2_rn(alpha, T);
+        T = __fmul2_rn(T, __ffma2_rn(alpha, NEG1, ONE));
+        const float4 k0 = batch[j].k0, k1 = batch[j].k1;
+        C0 = __ffma2_rn(lo2(k0), wgt, C0);
+        C1 = __ffma2_rn(hi2(k0), wgt, C1);
+        C2 = __ffma2_rn(lo2(k1), wgt, C2);
+        const uint32_t kpos = base - rg.x + (uint32_t)j + 1u;
+        last0 = c0 ? kpos : last0;
+        last1 = c1 ? kpos : last1;
+        if (STATS) n_comp += (c0 ? 1u : 0u) + (c1 ? 1u : 0u);
       }
     }
   }
-  if (inside) {
-    const int64_t pix = (int64_t)y * vd.W + x, plane = (int64_t)vd.W * vd.H;
-    vd.img[pix] = C0 + T * vd.bg[0];
-    vd.img[plane + pix] = C1 + T * vd.bg[1];
-    vd.img[2 * plane + pix] = C2 + T * vd.bg[2];
-    vd.final_T[pix] = T;
-    vd.n_contrib[pix] = last;
+  const int64_t plane = (int64_t)vd.W * vd.H;
+  if (inside0) {
+    const int64_t pix = (int64_t)wb.y * vd.W + wb.x;
+    vd.img[pix] = C0.x + T.x * vd.bg[0];
+    vd.img[plane + pix] = C1.x + T.x * vd.bg[1];
+    vd.img[2 * plane + pix] = C2.x + T.x * vd.bg[2];
+    vd.final_T[pix] = T.x;
+    vd.n_contrib[pix] = last0;
+  }
+  if (inside1) {
+    const int64_t pix = (int64_t)(wb.y + 4) * vd.W + wb.x;
+    vd.img[pix] = C0.y + T.y * vd.bg[0];
+    vd.img[plane + pix] = C1.y + T.y * vd.bg[1];
+    vd.img[2 * plane + pix] = C2.y + T.y * vd.bg[2];
+    vd.final_T[pix] = T.y;
+    vd.n_contrib[pix] = last1;
   }
   if (STATS) {
     unsigned long long a = n_eval, b = n_range, c = n_comp;
@@ -111,22 +196,22 @@ __device__ __forceinline__ void render_tile_fwd(const ViewTable<MAXV>& vt, int64
 }
 
 template <class VS, bool STATS>
-__global__ void __launch_bounds__(kFwdThreads) k_render_fwd(const __grid_constant__ VS vs, const uint2* __restrict__ ranges,
+__global__ void __launch_bounds__(kFwdThreads, 8) k_render_fwd(const __grid_constant__ VS vs, const uint2* __restrict__ ranges,
                                                          const uint32_t* __restrict__ vals, const Rec* __restrict__ rec,
                                                          const Params P, unsigned long long* __restrict__ stats) {
-  __shared__ Rec batch[kFwdBatch];
+  __shared__ RecPair batch[kFwdBatch];
   render_tile_fwd<VS::kMax, STATS>(vs.get(), (int64_t)blockIdx.x, batch, ranges, vals, rec, P, stats);
 }
 
 // Persistent form: CTAs take tiles from a work counter until the table's total_tiles are done, so
 // a fixed grid serves batches of any size (the launch can be replayed from a captured graph).
 template <class VS>
-__global__ void __launch_bounds__(kFwdThreads) k_render_fwd_persistent(const __grid_constant__ VS vs,
+__global__ void __launch_bounds__(kFwdThreads, 8) k_render_fwd_persistent(const __grid_constant__ VS vs,
                                                                     const uint2* __restrict__ ranges,
                                                                     const uint32_t* __restrict__ vals,
                                                                     const Rec* __restrict__ rec, const Params P,
                                                                     unsigned int* __restrict__ tile_counter) {
-  __shared__ Rec batch[kFwdBatch];
+  __shared__ RecPair batch[kFwdBatch];
   __shared__ unsigned int s_tile;
   const auto& vt = vs.get();
   const long long total = vt.total_tiles;
@@ -184,25 +269,6 @@ __device__ __forceinline__ int reduce10_slot(unsigned lane) {
   return ((lane & 16u) ? 5 : 0) + p6;
 }
 
-// A fragment's record as the backward composite reads it: every value the two pixels of a thread
-// share is stored twice, so that one 16-byte shared load gives two ready float2 operands.
-struct RecPair {
-  float4 m;    // -mx, -mx, -my, -my
-  float4 e;    // q limit x2, beta/2 x2
-  float4 c0;   // conic a x2, 2 conic b x2
-  float4 c1;   // conic c x2, kappa x2
-  float4 n0;   // -2 conic a x2, -2 conic b x2
-  float4 n1;   // -2 conic c x2, (unused)
-  float4 k0;   // r x2, g x2
-  float4 k1;   // b x2, (unused)
-};
-
-__device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
-__device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
-__device__ __forceinline__ float2 sel2(bool a, bool b, float2 v, float2 z) {
-  return make_float2(a ? v.x : z.x, b ? v.y : z.y);
-}
-
 // Backward.  Per pixel, walks its contributors back to front, recovering T_i = T_{i+1}/(1-alpha_i)
 // from the saved final transmittance; S is the colour composited behind the current fragment.
 //   dC/dalpha_i = c_i T_i - S_i / (1 - alpha_i)
@@ -210,8 +276,8 @@ __device__ __forceinline__ float2 sel2(bool a, bool b, float2 v, float2 z) {
 //   dG/dp = -G/2,  p = q^hb:  dp/dq = hb p / q,  dp/dhb = p ln q  (0 for q < 1e-12)
 //   q = a dx^2 + 2 b dx dy + c dy^2, dx = px - mx
 // A thread's two pixels share x and the fragment, so their arithmetic runs as float2 pairs (one
-// packed instruction for both).  The fragment test is eval_fragment's arithmetic, operation for
-// operation, so the skip / clamp / stop decisions equal the forward's bit for bit.  A thread sums
+// packed instruction for both).  The fragment test is eval_pair, as in the forward, so the skip /
+// clamp / stop decisions equal the forward's bit for bit.  A thread sums
 // its two pixels' terms, the warp sums by a reduce-scatter butterfly, and ten lanes add the ten
 // per-primitive sums with one atomic each.  Reciprocals use the approximate MUFU instruction
 // (about 1 ulp); they only scale gradients, never decide a branch.
@@ -219,7 +285,7 @@ template <class VS>
 __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__ VS vs, const uint2* __restrict__ ranges,
                                                          const uint32_t* __restrict__ vals, const Rec* __restrict__ rec,
                                                          const Params P, float4* __restrict__ g2d) {
-  __shared__ RecPair batch[kBatch];
+  __shared__ RecPairB batch[kBatch];
   __shared__ uint32_t ids[kBatch];
   __shared__ uint32_t s_max_last;
   const auto& vt = vs.get();
@@ -266,7 +332,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
   const int slot = reduce10_slot(lane);
   const bool adder = (lane & 1u) == 0 && slot >= 0;
   const float2 ONE = make_float2(1.0f, 1.0f), NEG1 = make_float2(-1.0f, -1.0f), ZERO = make_float2(0.f, 0.f);
-  const float2 NHL = make_float2(kNegHalfLog2e, kNegHalfLog2e), NHALF = make_float2(-0.5f, -0.5f);
+  const float2 NHALF = make_float2(-0.5f, -0.5f);
   const float2 LN2 = make_float2(0.69314718055994531f, 0.69314718055994531f);
 
   for (uint32_t end = rg.x + max_last; end > rg.x;) {
@@ -277,49 +343,27 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
       const uint32_t g = vals[idx];
       const Rec r = rec[g];
       ids[threadIdx.x] = g;
-      RecPair& d = batch[threadIdx.x];
-      d.m = make_float4(-r.a.x, -r.a.x, -r.a.y, -r.a.y);
-      d.e = make_float4(r.a.z, r.a.z, r.a.w, r.a.w);
-      const float tb = __fmul_rn(2.0f, r.b.y);
-      d.c0 = make_float4(r.b.x, r.b.x, tb, tb);
-      d.c1 = make_float4(r.b.z, r.b.z, r.b.w, r.b.w);
-      d.n0 = make_float4(-2.0f * r.b.x, -2.0f * r.b.x, -tb, -tb);
+      RecPairB& d = batch[threadIdx.x];
+      stage_pair(d, r);
+      d.n0 = make_float4(-2.0f * r.b.x, -2.0f * r.b.x, -2.0f * r.b.y, -2.0f * r.b.y);
       d.n1 = make_float4(-2.0f * r.b.z, -2.0f * r.b.z, 0.f, 0.f);
-      d.k0 = make_float4(r.c.x, r.c.x, r.c.y, r.c.y);
-      d.k1 = make_float4(r.c.z, r.c.z, 0.f, 0.f);
     }
     __syncthreads();
     for (int j = (int)(end - start) - 1; j >= 0; --j) {
       const uint32_t kpos = start - rg.x + (uint32_t)j + 1u;  // 1-based position in the tile's list
       if (kpos > wlast) continue;                             // beyond every pixel of this warp
-      const float4 m = batch[j].m, e = batch[j].e, c0 = batch[j].c0, c1 = batch[j].c1;
-      // eval_fragment on both pixels
-      const float2 dx = __fadd2_rn(PX, lo2(m));
-      const float2 dy = __fadd2_rn(PY, hi2(m));
-      const float2 t = __ffma2_rn(hi2(c0), dy, __fmul2_rn(lo2(c0), dx));
-      const float2 q2 = __ffma2_rn(__fmul2_rn(lo2(c1), dy), dy, __fmul2_rn(t, dx));
-      const float q0 = fmaxf(q2.x, 0.0f), q1 = fmaxf(q2.y, 0.0f);
-      const float ql = e.x, hb = e.z;
-      const bool in0 = q0 <= ql, in1 = q1 <= ql;
-      float2 p, lq;
-      if (hb == 1.0f) {
-        p = make_float2(q0, q1);
-        lq = ZERO;
-      } else {
-        lq = make_float2(mufu_lg2(q0), mufu_lg2(q1));
-        const float2 hl = __fmul2_rn(hi2(e), lq);
-        p = make_float2(mufu_ex2(hl.x), mufu_ex2(hl.y));
-      }
-      const float2 ge = __fmul2_rn(NHL, p);
-      const float2 G = make_float2(mufu_ex2(ge.x), mufu_ex2(ge.y));
-      const float2 a = __fmul2_rn(hi2(c1), G);
-      const bool cl0 = a.x > P.alpha_max, cl1 = a.y > P.alpha_max;
-      const float al0 = cl0 ? P.alpha_max : a.x, al1 = cl1 ? P.alpha_max : a.y;
-      const bool act0 = kpos <= last[0] && in0 && al0 >= P.alpha_min;
-      const bool act1 = kpos <= last[1] && in1 && al1 >= P.alpha_min;
+      PairEval f;
+      eval_pair(batch[j], PX, PY, f);
+      const bool cl0 = f.a.x > P.alpha_max, cl1 = f.a.y > P.alpha_max;
+      const float al0 = cl0 ? P.alpha_max : f.a.x, al1 = cl1 ? P.alpha_max : f.a.y;
+      const bool act0 = kpos <= last[0] && al0 >= P.alpha_min;
+      const bool act1 = kpos <= last[1] && al1 >= P.alpha_min;
       if (!__any_sync(0xffffffffu, act0 || act1)) continue;
       // gradient terms of both pixels (zero for an inactive one, whose T and S stay as they are)
       const float4 n0 = batch[j].n0, n1 = batch[j].n1, k0 = batch[j].k0, k1 = batch[j].k1;
+      const float4 e = batch[j].e, c1 = batch[j].c1;
+      const float2 dx = f.dx, dy = f.dy, p = f.p, lq = f.lq, G = f.G;
+      const float q0 = f.q0, q1 = f.q1, hb = e.z;
       const float2 alpha = make_float2(act0 ? al0 : 0.f, act1 ? al1 : 0.f);
       const float2 om = __ffma2_rn(alpha, NEG1, ONE);
       const float2 inv = make_float2(act0 ? rcp_approx(om.x) : 1.0f, act1 ? rcp_approx(om.y) : 1.0f);
