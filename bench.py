@@ -45,7 +45,8 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons, sampled every 100 ms while running.  Entering waits
+    (up to 5 s) for the first sample, so that sampling is live when the timed region starts."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
@@ -58,10 +59,14 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.monotonic()
+            while not self.lines and time.monotonic() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.01)
+            self.lines.clear()  # keep only samples taken after entry
         except OSError:
             self.proc = None
         return self
@@ -271,7 +276,7 @@ def serving_bench(n_requests, rate_mults, slots, dev, seed=40):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-pixels", type=int, default=4096)
@@ -360,13 +365,15 @@ def main():
         if events:
             events[4].record(stream)
 
-    def timed(fn_steps, bwd):
+    def timed(fn_steps, bwd, trace=False):
         for i in range(args.warmup):
             step(i, bwd=bwd)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
+        if trace:
+            ges.ges_trace_enable(ctx.handle, True)  # starts an empty record
         l0 = ges.ges_kernel_launches()
         s0 = torch.cuda.Event(enable_timing=True)
         s1 = torch.cuda.Event(enable_timing=True)
@@ -388,7 +395,10 @@ def main():
         print(json.dumps({"profile_run": True, "K": Ks[0]}))
         return
     with ClockSampler(local) as clk:
-        ms_fb, launches = timed(args.steps, bwd=True)
+        # per-kernel device times of the timed fwd+bwd steps: library tracing (events on `stream`)
+        ms_fb, launches = timed(args.steps, bwd=True, trace=True)
+        trace = ges.ges_trace_read(ctx.handle)
+        ges.ges_trace_enable(ctx.handle, False)
         stage = np.array([[ev[i][k].elapsed_time(ev[i][k + 1]) for k in range(nst - 1)] for i in range(args.steps)])
         ms_f, _ = timed(args.steps, bwd=False)
     clocks = clk.summary()
@@ -426,9 +436,11 @@ def main():
                                 f"(ex2 {r_ex2:.1f}, lg2 {r_lg2:.1f}, rcp {r_rcp:.1f}; sfu_rates microbenchmark) "
                                 f"weighted by the kernel's instruction mix")}
 
-    bwd_ms = float(st_mean[3])
-    fwd_ms = float(st_mean[2])
-    roofline = mufu_roofline("k_render_bwd + k_preprocess_bwd (backward; k_render_bwd is 94% of it)", bwd_ms,
+    # average device time per launch of each traced kernel over the timed steps
+    kernel_ms = {k: ms / n for k, (n, ms) in trace.items()}
+    bwd_ms = kernel_ms["k_render_bwd"]
+    fwd_ms = kernel_ms["k_render_fwd"]
+    roofline = mufu_roofline("k_render_bwd (backward composite)", bwd_ms,
                              mean_inr, 2 * mean_inr, 2 * mean_comp,
                              f"per frame: lg2 + 2 ex2 per in-extent pair ({mean_inr:.3e}) + 2 rcp per composited "
                              f"pair ({mean_comp:.3e})")
@@ -436,7 +448,7 @@ def main():
                                  f"per frame: lg2 + 2 ex2 per in-extent pair ({mean_inr:.3e})")
     # preprocess: HBM bytes per primitive (read 240 B at SH3, write 68 B)
     pre_bytes = sc.n * (240 + 68)
-    pre_gbs = pre_bytes / (float(st_mean[0]) / 1e3) / 1e9
+    pre_gbs = pre_bytes / (kernel_ms["k_preprocess"] / 1e3) / 1e9
     hbm = float(peaks.get("hbm_gbs", 6800.0))
 
     out = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
@@ -453,8 +465,9 @@ def main():
            "frame_stats": {"K_mean": mean_K, "evaluated_pairs_mean": mean_eval, "in_extent_pairs_mean": mean_inr,
                            "composited_pairs_mean": mean_comp},
            "roofline": roofline, "roofline_fwd": roofline_fwd, "sfu_rates": sfu,
-           "preprocess_hbm": {"achieved_gbs": pre_gbs, "peak_gbs": hbm, "frac": pre_gbs / hbm,
-                              "bytes_per_prim": 308, "note": "includes the depth-key copy launch"},
+           "preprocess_hbm": {"kernel": "k_preprocess", "achieved_gbs": pre_gbs, "peak_gbs": hbm, "frac": pre_gbs / hbm,
+                              "bytes_per_prim": 308},
+           "kernel_ms": kernel_ms,
            "gpu_launches": int(launches), "clocks": clocks}
 
     if not args.no_e2e:

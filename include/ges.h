@@ -189,6 +189,22 @@ ges_status ges_frame_count_work(ges_frame* frame, void* stream, int64_t* evaluat
 /* Number of CUDA kernels this process has launched through libges (all threads). */
 uint64_t ges_kernel_launches(void);
 
+/* Kernel tracing (a measurement aid; no counterpart in the paper).  While tracing is on, every
+   kernel launch or launch group that the frame calls of this context make (ges_preprocess,
+   ges_bin_sort, ges_render_fwd, ges_render_bwd) is bracketed by two CUDA events recorded on the
+   caller's stream.  The names are the kernel names, or for a group its stage:
+   "k_preprocess", "depth_sort", "gather_touched", "scan_touched", "k_keygen", "tile_sort",
+   "k_ranges", "k_render_fwd", "k_render_bwd", "k_preprocess_bwd".
+   ges_trace_enable(ctx, 1) starts a new record (0 stops recording and keeps the record).
+   ges_trace_read synchronises with the recorded events and writes, per name in first-launch
+   order, at most `capacity` entries: names[32*i..] (NUL-terminated), launches[i], total_ms[i]
+   (the summed device time).  *n_out receives the number of distinct names.  The record is then
+   cleared.  Errors: GES_ERR_INVALID_ARG for a NULL ctx/n_out or capacity < 0 with non-NULL
+   outputs; GES_ERR_CUDA if an event fails.  Host cost: two event records per launch. */
+ges_status ges_trace_enable(ges_ctx* ctx, int on);
+ges_status ges_trace_read(ges_ctx* ctx, int32_t capacity, char* names, int64_t* launches, double* total_ms,
+                          int32_t* n_out);
+
 /* Forward render that allocates no device memory (no counterpart in the paper; it exists for
    callers that cannot allocate).  Some callers cannot call cudaMalloc: code running under another
    runtime's memory manager that has already reserved the device's memory for its own pool, or

@@ -219,7 +219,113 @@ ges_status ges_ctx_create(int device, size_t hbm_budget_bytes, ges_ctx** out) {
   return GES_OK;
 }
 
-void ges_ctx_destroy(ges_ctx* ctx) { delete ctx; }
+void ges_ctx_destroy(ges_ctx* ctx) {
+  if (!ctx) return;
+  for (auto& r : ctx->trace) {
+    ctx->event_pool.push_back(r.a);
+    ctx->event_pool.push_back(r.b);
+  }
+  for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+  delete ctx;
+}
+
+// ---------------------------------------------------------------- tracing
+namespace {
+
+cudaEvent_t trace_event(ges_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// brackets the launches made in its lifetime with two events on stream s, when tracing is on
+struct TraceScope {
+  ges_ctx* c;
+  const char* name;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  TraceScope(ges_ctx* c_, const char* name_, cudaStream_t s_) : c(c_), name(name_), s(s_) {
+    if (!c->trace_on) return;
+    std::lock_guard<std::mutex> lk(c->mu);
+    a = trace_event(c);
+    if (a && cudaEventRecord(a, s) != cudaSuccess) {
+      c->event_pool.push_back(a);
+      a = nullptr;
+    }
+  }
+  ~TraceScope() {
+    if (!a) return;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaEvent_t b = trace_event(c);
+    if (b && cudaEventRecord(b, s) == cudaSuccess) {
+      c->trace.push_back({name, a, b});
+    } else {
+      c->event_pool.push_back(a);
+      if (b) c->event_pool.push_back(b);
+    }
+  }
+};
+
+}  // namespace
+
+ges_status ges_trace_enable(ges_ctx* ctx, int on) {
+  if (!ctx) return fail(GES_ERR_INVALID_ARG, "ctx is NULL");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (on) {
+    for (auto& r : ctx->trace) {
+      ctx->event_pool.push_back(r.a);
+      ctx->event_pool.push_back(r.b);
+    }
+    ctx->trace.clear();
+  }
+  ctx->trace_on = on != 0;
+  return GES_OK;
+}
+
+ges_status ges_trace_read(ges_ctx* ctx, int32_t capacity, char* names, int64_t* launches, double* total_ms,
+                          int32_t* n_out) {
+  if (!ctx || !n_out) return fail(GES_ERR_INVALID_ARG, "ctx/n_out is NULL");
+  if (capacity < 0) return fail(GES_ERR_INVALID_ARG, "capacity < 0");
+  if (capacity > 0 && (!names || !launches || !total_ms)) return fail(GES_ERR_INVALID_ARG, "output is NULL");
+  ges_status st = use_device(ctx->device);
+  if (st != GES_OK) return st;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  std::vector<const char*> order;
+  std::vector<int64_t> cnt;
+  std::vector<double> ms;
+  ges_status result = GES_OK;
+  for (auto& r : ctx->trace) {
+    float t = 0.f;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+    if (e != cudaSuccess && result == GES_OK) result = cuda_fail(e, "trace event");
+    size_t k = 0;
+    while (k < order.size() && std::strcmp(order[k], r.name) != 0) ++k;
+    if (k == order.size()) {
+      order.push_back(r.name);
+      cnt.push_back(0);
+      ms.push_back(0.0);
+    }
+    cnt[k] += 1;
+    ms[k] += (double)t;
+    ctx->event_pool.push_back(r.a);
+    ctx->event_pool.push_back(r.b);
+  }
+  ctx->trace.clear();
+  *n_out = (int32_t)order.size();
+  for (size_t k = 0; k < order.size() && (int64_t)k < capacity; ++k) {
+    std::strncpy(names + 32 * k, order[k], 31);
+    names[32 * k + 31] = '\0';
+    launches[k] = cnt[k];
+    total_ms[k] = ms[k];
+  }
+  return result;
+}
 
 ges_status ges_frame_create(ges_ctx* ctx, int64_t n_capacity, int32_t width, int32_t height, int64_t key_capacity,
                             ges_frame** out) {
@@ -322,8 +428,11 @@ ges_status ges_preprocess(ges_frame* f, const ges_scene* scene, const ges_camera
   f->P = to_params(*params);
   f->n = scene->n;
   f->sh_degree = scene->sh_degree;
-  launch_preprocess<FrameViews>(f->vt, f->n, f->P, f->depth_key, f->dk[0], f->pv[0], f->rect, f->rec, f->ext, f->tprim,
-                                f->ctx->num_sms, s);
+  {
+    TraceScope tr(f->ctx, "k_preprocess", s);
+    launch_preprocess<FrameViews>(f->vt, f->n, f->P, f->depth_key, f->dk[0], f->pv[0], f->rect, f->rec, f->ext,
+                                  f->tprim, f->ctx->num_sms, s);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "preprocess launch");
   f->have_pre = true;
@@ -341,11 +450,20 @@ ges_status ges_bin_sort(ges_frame* f, void* stream) {
   if ((e = cudaMemsetAsync(f->d_flags, 0, 4, s)) != cudaSuccess) return cuda_fail(e, "memset flags");
   // depth sort of the primitives (32-bit keys)
   int cur = 0;
-  radix_sort_pairs(f->dk, f->pv, cur, f->n, nullptr, f->n, 32, f->hist, f->hist_cap, f->scan, s);
+  {
+    TraceScope tr(f->ctx, "depth_sort", s);
+    radix_sort_pairs(f->dk, f->pv, cur, f->n, nullptr, f->n, 32, f->hist, f->hist_cap, f->scan, s);
+  }
   f->sorted_prims = f->pv[cur];
   // tiles touched in depth order, exclusive scan -> offsets, K
-  launch_gather_touched(f->sorted_prims, f->tprim, f->n, f->touched, s);
-  scan_exclusive<uint32_t, unsigned long long>(f->touched, f->offsets, f->n, f->d_K, f->scan, s);
+  {
+    TraceScope tr(f->ctx, "gather_touched", s);
+    launch_gather_touched(f->sorted_prims, f->tprim, f->n, f->touched, s);
+  }
+  {
+    TraceScope tr(f->ctx, "scan_touched", s);
+    scan_exclusive<uint32_t, unsigned long long>(f->touched, f->offsets, f->n, f->d_K, f->scan, s);
+  }
   if (f->auto_cap) {
     if ((e = cudaMemcpyAsync(f->h_K, f->d_K, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(e, "read K");
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "sync for K");
@@ -358,14 +476,24 @@ ges_status ges_bin_sort(ges_frame* f, void* stream) {
       if ((st = frame_alloc_keys(f, cap)) != GES_OK) return st;
     }
   }
-  launch_keygen<FrameViews>(f->vt, f->offsets, f->touched, f->d_K, f->n, f->sorted_prims, f->rect, f->ext, f->rec,
-                            f->P.margin_abs, f->key_cap, f->tk[0], f->tv[0], f->d_flags, s);
+  {
+    TraceScope tr(f->ctx, "k_keygen", s);
+    launch_keygen<FrameViews>(f->vt, f->offsets, f->touched, f->d_K, f->n, f->sorted_prims, f->rect, f->ext, f->rec,
+                              f->P.margin_abs, f->key_cap, f->tk[0], f->tv[0], f->d_flags, s);
+  }
   int tcur = 0;
-  radix_sort_pairs(f->tk, f->tv, tcur, 0, f->d_K, f->key_cap, bits_for(f->n_tiles), f->hist, f->hist_cap, f->scan, s);
+  {
+    TraceScope tr(f->ctx, "tile_sort", s);
+    radix_sort_pairs(f->tk, f->tv, tcur, 0, f->d_K, f->key_cap, bits_for(f->n_tiles), f->hist, f->hist_cap, f->scan,
+                     s);
+  }
   f->tile_keys = f->tk[tcur];
   f->tile_vals = f->tv[tcur];
   if ((e = cudaMemsetAsync(f->ranges, 0, sizeof(uint2) * f->n_tiles, s)) != cudaSuccess) return cuda_fail(e, "memset ranges");
-  launch_ranges(f->tile_keys, f->d_K, f->key_cap, f->ranges, f->ctx->num_sms, s);
+  {
+    TraceScope tr(f->ctx, "k_ranges", s);
+    launch_ranges(f->tile_keys, f->d_K, f->key_cap, f->ranges, f->ctx->num_sms, s);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "bin_sort launch");
   f->have_sort = true;
   return GES_OK;
@@ -379,7 +507,10 @@ ges_status ges_render_fwd(ges_frame* f, float* img, float* final_T, uint32_t* n_
   f->vt.t.v[0].img = img;
   f->vt.t.v[0].final_T = final_T;
   f->vt.t.v[0].n_contrib = n_contrib;
-  launch_render_fwd<FrameViews>(f->vt, f->n_tiles, f->ranges, f->tile_vals, f->rec, f->P, (cudaStream_t)stream);
+  {
+    TraceScope tr(f->ctx, "k_render_fwd", (cudaStream_t)stream);
+    launch_render_fwd<FrameViews>(f->vt, f->n_tiles, f->ranges, f->tile_vals, f->rec, f->P, (cudaStream_t)stream);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "render_fwd launch");
   return GES_OK;
@@ -410,8 +541,14 @@ ges_status ges_render_bwd(ges_frame* f, const ges_scene* scene, const float* fin
   cudaError_t e;
   if (f->n > 0 && (e = cudaMemsetAsync(f->g2d, 0, sizeof(float4) * 3 * f->n, s)) != cudaSuccess)
     return cuda_fail(e, "memset g2d");
-  launch_render_bwd<FrameViews>(f->vt, f->n_tiles, f->ranges, f->tile_vals, f->rec, f->P, f->g2d, s);
-  launch_preprocess_bwd<FrameViews>(f->vt, f->n, f->P, f->depth_key, f->g2d, f->ctx->num_sms, s);
+  {
+    TraceScope tr(f->ctx, "k_render_bwd", s);
+    launch_render_bwd<FrameViews>(f->vt, f->n_tiles, f->ranges, f->tile_vals, f->rec, f->P, f->g2d, s);
+  }
+  {
+    TraceScope tr(f->ctx, "k_preprocess_bwd", s);
+    launch_preprocess_bwd<FrameViews>(f->vt, f->n, f->P, f->depth_key, f->g2d, f->ctx->num_sms, s);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "render_bwd launch");
   return GES_OK;
 }

@@ -4,10 +4,16 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <vector>
 
 #include "ges.h"
 #include "common.cuh"
 #include "kernels.cuh"
+
+struct ges_trace_rec {
+  const char* name;  // static string
+  cudaEvent_t a, b;
+};
 
 struct ges_ctx {
   int device = 0;
@@ -15,6 +21,10 @@ struct ges_ctx {
   size_t used = 0;
   int num_sms = 0;
   std::mutex mu;
+  // kernel tracing (ges_trace_enable / ges_trace_read)
+  bool trace_on = false;
+  std::vector<ges_trace_rec> trace;
+  std::vector<cudaEvent_t> event_pool;
 };
 
 struct ges_frame {

@@ -37,7 +37,8 @@ GES_FALLOFF_PAPER_APPROX = 1
 EXPORTED = ["ges_last_error", "ges_params_default", "ges_ctx_create", "ges_ctx_destroy", "ges_frame_create",
             "ges_frame_destroy", "ges_preprocess", "ges_bin_sort", "ges_render_fwd", "ges_render_bwd",
             "ges_frame_status", "ges_frame_keys", "ges_frame_inspect", "ges_frame_count_work",
-            "ges_kernel_launches", "ges_render_fwd_noalloc", "ges_serve_create", "ges_serve_add_scene",
+            "ges_kernel_launches", "ges_trace_enable", "ges_trace_read", "ges_render_fwd_noalloc",
+            "ges_serve_create", "ges_serve_add_scene",
             "ges_serve_submit", "ges_serve_poll", "ges_serve_destroy"]
 
 
@@ -93,6 +94,8 @@ def _load():
         "ges_frame_inspect": ([P, P, P, P, P, P, P], i32),
         "ges_frame_count_work": ([P, P, P, P, P, P], i32),
         "ges_kernel_launches": ([], u64),
+        "ges_trace_enable": ([P, ctypes.c_int], i32),
+        "ges_trace_read": ([P, i32, P, P, P, P], i32),
         "ges_render_fwd_noalloc": ([P, P, P, P, P, P, P], i32),
         "ges_serve_create": ([P, P, i32, P], i32),
         "ges_serve_add_scene": ([P, P, P], i32),
@@ -269,6 +272,24 @@ def ges_frame_count_work(frame: int, stream=None):
 
 def ges_kernel_launches() -> int:
     return int(_lib.ges_kernel_launches())
+
+
+def ges_trace_enable(ctx: int, on: bool) -> None:
+    _check(_lib.ges_trace_enable(ctx, int(bool(on))))
+
+
+def ges_trace_read(ctx: int, capacity: int = 32):
+    """{name: (launches, total device ms)} of the launches traced since the last read (synchronises)."""
+    names = ctypes.create_string_buffer(32 * capacity)
+    launches = np.zeros(capacity, np.int64)
+    total = np.zeros(capacity, np.float64)
+    n = ctypes.c_int32(0)
+    _check(_lib.ges_trace_read(ctx, capacity, names, _addr(launches), _addr(total), ctypes.byref(n)))
+    out = {}
+    for k in range(min(n.value, capacity)):
+        name = names.raw[32 * k:32 * k + 32].split(b"\0", 1)[0].decode()
+        out[name] = (int(launches[k]), float(total[k]))
+    return out
 
 
 def ges_render_fwd_noalloc(scene: ges_scene, cam: ges_camera, params: ges_params, img, final_T, n_contrib,
