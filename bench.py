@@ -104,6 +104,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def _traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when the kernel's
+    sources have changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    try:
+        rec = json.load(open(path))[kernel]
+        h = hashlib.sha1()
+        for f in rec["sources"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        return float(rec["dram_bytes_per_launch"]) if h.hexdigest() == rec["sources_sha1"] else None
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -431,7 +446,7 @@ def main():
         peak = ops / t_peak / 1e12
         achieved = ops / (ms / 1e3) / 1e12
         return {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (MUFU)",
-                "frac": achieved / peak, "traffic": None, "work": work,
+                "frac": achieved / peak, "traffic": _traffic(kernel.split()[0]), "work": work,
                 "peak_source": (f"{nsm} SMs x {sm_mhz:.0f} MHz ({src} max clock) x measured MUFU rates per SM per clock "
                                 f"(ex2 {r_ex2:.1f}, lg2 {r_lg2:.1f}, rcp {r_rcp:.1f}; sfu_rates microbenchmark) "
                                 f"weighted by the kernel's instruction mix")}
@@ -446,8 +461,9 @@ def main():
                              f"pair ({mean_comp:.3e})")
     roofline_fwd = mufu_roofline("k_render_fwd (forward composite)", fwd_ms, mean_inr, 2 * mean_inr, 0,
                                  f"per frame: lg2 + 2 ex2 per in-extent pair ({mean_inr:.3e})")
-    # preprocess: HBM bytes per primitive (read 240 B at SH3, write 68 B)
-    pre_bytes = sc.n * (240 + 68)
+    # preprocess: HBM bytes per primitive (read 240 B at SH3; write 88 B: depth key x2, sort value,
+    # rect, 48-B record, extent shape, tile count)
+    pre_bytes = sc.n * (240 + 88)
     pre_gbs = pre_bytes / (kernel_ms["k_preprocess"] / 1e3) / 1e9
     hbm = float(peaks.get("hbm_gbs", 6800.0))
 
@@ -466,7 +482,7 @@ def main():
                            "composited_pairs_mean": mean_comp},
            "roofline": roofline, "roofline_fwd": roofline_fwd, "sfu_rates": sfu,
            "preprocess_hbm": {"kernel": "k_preprocess", "achieved_gbs": pre_gbs, "peak_gbs": hbm, "frac": pre_gbs / hbm,
-                              "bytes_per_prim": 308},
+                              "bytes_per_prim": 328},
            "kernel_ms": kernel_ms,
            "gpu_launches": int(launches), "clocks": clocks}
 

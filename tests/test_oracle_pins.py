@@ -340,6 +340,65 @@ def test_key_list_structure():
     assert np.all(d > 0.2)
 
 
+def _qmin_over_box(conic, u, v, x0, x1, y0, y1):
+    """min of q(d) = d^T conic d, d = (x - u, y - v), over the box [x0,x1] x [y0,y1] (FP64): zero if
+    the centre is inside, else the smallest of the four edges' 1D minima (closed form, clamped)."""
+    if x0 <= u <= x1 and y0 <= v <= y1:
+        return 0.0
+    A, B, C = conic
+    best = math.inf
+    for x in (x0, x1):            # vertical edges: minimise over y
+        dx = x - u
+        dy = min(max(-B * dx / C, y0 - v), y1 - v)
+        best = min(best, A * dx * dx + 2 * B * dx * dy + C * dy * dy)
+    for y in (y0, y1):            # horizontal edges: minimise over x
+        dy = y - v
+        dx = min(max(-B * dy / A, x0 - u), x1 - u)
+        best = min(best, A * dx * dx + 2 * B * dx * dy + C * dy * dy)
+    return best
+
+
+@pytest.mark.parametrize("which", ["tiny", "wide_beta"])
+def test_tile_lists_follow_the_extent_ellipse(which):
+    """Each primitive's tiles are exactly those its extent ellipse {d^T cov^-1 d <= q_lim} meets,
+    up to the 1e-2 px horizontal margin: checked against a geometric test written independently of
+    the row-span formula (the minimum of the quadratic form over each tile's box)."""
+    if which == "tiny":
+        sc, cam = scenes.tiny_workload()
+    else:
+        sc = scenes.cube_scene(300, seed=7, sh_degree=0, beta_range=(0.3, 16.0), beta_log=True)
+        cam = scenes.tiny_camera(45, 37)
+    k = oracle.keys(sc, cam)
+    kk, vv = oracle.sorted_keys(sc, cam, key_info=k)
+    tx = (cam.width + 15) // 16
+    listed = {}
+    for key, g in zip(kk, vv):
+        listed.setdefault(int(g), set()).add(int(key >> np.uint64(32)))
+    margin_abs, margin_rel = 1e-2, float(np.float32(1e-3))
+    n_checked = 0
+    for g in np.nonzero(k["touched"])[0]:
+        a, b, c = (float(x) for x in k["cov2d"][g])
+        det = a * c - b * b
+        conic = (c / det, -b / det, a / det)
+        u, v = (float(x) for x in k["mean2d"][g])
+        qlim = float(k["qstar"][g]) * (1 + margin_rel) ** 2
+        r = k["rect"][g]
+        tiles = listed.get(int(g), set())
+        assert len(tiles) == int(k["touched"][g])
+        for ty in range(r[1], r[3]):
+            for tx_ in range(r[0], r[2]):
+                t = ty * tx + tx_
+                x0, y0 = 16.0 * tx_, 16.0 * ty
+                if t in tiles:   # the ellipse, widened by the margin in x, meets the tile
+                    q = _qmin_over_box(conic, u, v, x0 - margin_abs - 1e-3, x0 + 16 + margin_abs + 1e-3, y0, y0 + 16)
+                    assert q <= qlim * (1 + 1e-4), (g, t, q, qlim)
+                else:            # it does not meet the tile
+                    q = _qmin_over_box(conic, u, v, x0, x0 + 16, y0, y0 + 16)
+                    assert q >= qlim * (1 - 1e-4), (g, t, q, qlim)
+                n_checked += 1
+    assert n_checked > 1000
+
+
 # ---------------------------------------------------------------- gradients
 def _fd_check(sc, cam, params, seed, n_check_prims=None, h=1e-6):
     rng = np.random.default_rng(seed)
