@@ -302,6 +302,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=100)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the differentiation and stress legs")
     ap.add_argument("--profile", action="store_true",
                     help="minimal run for ncu: no work counters, e2e or CPU baseline; warmup + steps fwd+bwd")
     args = ap.parse_args()
@@ -490,6 +491,11 @@ def main():
         out["e2e"] = e2e(args, sc, gcam, frame, params, dev, stream, ws, dist)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sc, cams, args.cpu_pixels, os.cpu_count() or 1)
+    if not args.no_extra:
+        out["differentiation"] = differentiation_bench(20, 3, dev)
+        torch.cuda.empty_cache()
+        out["stress_beta2"] = stress_bench(5, 3, dev)
+        torch.cuda.empty_cache()
     if not args.no_serve:
         del t, grads
         frame.close()
@@ -499,6 +505,116 @@ def main():
         print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
+
+
+def _ssim(x, y):
+    """Mean SSIM of two [3,H,W] images: 11x11 Gaussian window (sigma 1.5), C1 = 0.01^2, C2 = 0.03^2."""
+    import torch
+    import torch.nn.functional as F
+    g = torch.exp(-((torch.arange(11, device=x.device, dtype=torch.float32) - 5.0) ** 2) / (2 * 1.5 ** 2))
+    g = g / g.sum()
+    w = (g[:, None] * g[None, :]).expand(3, 1, 11, 11).contiguous()
+
+    def blur(a):
+        return F.conv2d(a[None], w, padding=5, groups=3)[0]
+
+    mx, my = blur(x), blur(y)
+    sxx, syy, sxy = blur(x * x) - mx * mx, blur(y * y) - my * my, blur(x * y) - mx * my
+    c1, c2 = 0.01 ** 2, 0.03 ** 2
+    s = ((2 * mx * my + c1) * (2 * sxy + c2)) / ((mx * mx + my * my + c1) * (sxx + syy + c2))
+    return s.mean()
+
+
+def differentiation_bench(steps, warmup, dev):
+    """fwd+bwd through the torch.autograd.Function on the differentiation workload (cube
+    distribution, 1.5M primitives, SH0, 1245x825).  The upstream gradient is that of
+    0.8 L1 + 0.2 (1 - SSIM) against a seeded uniform target, computed once by torch outside the
+    timed region; each timed step is rasterize() + torch.autograd.grad() (K1-K8)."""
+    import torch
+    from paper_2402_10128_gb300 import render, scenes
+    sc, cam = scenes.differentiation_workload()
+    params = [p.requires_grad_(True) for p in render.scene_tensors(sc, dev)]
+    probe = render.Frame(sc.n, cam.width, cam.height, key_capacity=0)
+    probe.forward(tuple(p.detach() for p in params), sc.sh_degree, cam)
+    K = probe.status()[1]
+    probe.close()
+    frame = render.Frame(sc.n, cam.width, cam.height, key_capacity=int(K * 1.05) + 4096)
+    gen = torch.Generator(device=dev).manual_seed(3)
+    target = torch.rand((3, cam.height, cam.width), device=dev, generator=gen)
+    img, _, _ = render.rasterize(*params, sc.sh_degree, cam, frame=frame)
+    loss = 0.8 * (img - target).abs().mean() + 0.2 * (1.0 - _ssim(img, target))
+    dL = torch.autograd.grad(loss, img)[0].detach().contiguous()
+    for p in params:
+        p.grad = None
+
+    def step():
+        im, _, _ = render.rasterize(*params, sc.sh_degree, cam, frame=frame)
+        return torch.autograd.grad(im, params, grad_outputs=dL)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        grads = step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    st, _ = frame.status()
+    assert st == 0 and all(torch.isfinite(g).all() for g in grads)
+    frame.close()
+    return {"workload": "differentiation: cube distribution, 1.5M primitives, SH0, 1245x825; upstream gradient of "
+                        "0.8 L1 + 0.2 (1 - SSIM) vs a seeded uniform target; step = rasterize + autograd.grad",
+            "fwd_bwd_mpix_s": cam.width * cam.height / (ms / 1e3) / 1e6, "ms_per_step": ms, "steps": steps,
+            "K": int(K), "loss": float(loss.detach())}
+
+
+def stress_bench(steps, warmup, dev):
+    """The stress view with beta = 2 everywhere (6M cube primitives, SH3, 3840x2160): fwd and
+    fwd+bwd.  The beta log-U[0.3,16] form of this configuration needs about 3.3e10 duplicates and
+    does not fit any exact per-tile binning."""
+    import torch
+    from paper_2402_10128_gb300 import ges, render, scenes
+    sc, cam = scenes.stress_beta2_workload()
+    t = render.scene_tensors(sc, dev)
+    probe = render.Frame(sc.n, cam.width, cam.height, key_capacity=0)
+    probe.forward(t, sc.sh_degree, cam)
+    K = probe.status()[1]
+    probe.close()
+    frame = render.Frame(sc.n, cam.width, cam.height, key_capacity=int(K * 1.02) + 4096)
+    gcam, params = ges.make_camera(cam), ges.params_default()
+    H, W = cam.height, cam.width
+    img = torch.empty((3, H, W), device=dev)
+    T = torch.empty((H, W), device=dev)
+    nc = torch.empty((H, W), dtype=torch.int32, device=dev)
+    dL = torch.full((3, H, W), 1.0 / (W * H), device=dev)
+    grads = tuple(torch.empty_like(a) for a in t)
+    scene_c, grads_c = ges.make_scene(*t, sc.sh_degree), ges.make_grads(*grads)
+
+    def step(bwd):
+        ges.ges_preprocess(frame.handle, scene_c, gcam, params)
+        ges.ges_bin_sort(frame.handle)
+        ges.ges_render_fwd(frame.handle, img, T, nc)
+        if bwd:
+            ges.ges_render_bwd(frame.handle, scene_c, T, nc, dL, grads_c)
+
+    out = {}
+    for bwd in (False, True):
+        for _ in range(warmup):
+            step(bwd)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            step(bwd)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out["fwd_bwd" if bwd else "fwd"] = {"mpix_s": W * H / (ms / 1e3) / 1e6, "ms_per_frame": ms}
+    assert frame.status()[0] == 0
+    frame.close()
+    return {"workload": "stress, beta = 2: 6M cube primitives, SH3, 3840x2160", "K": int(K), "steps": steps, **out}
 
 
 def e2e(args, sc, gcam, frame, params, dev, stream, ws, dist):

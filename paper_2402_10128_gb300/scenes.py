@@ -219,3 +219,10 @@ def stress_workload(n: int = 6_000_000, seed: int = 4):
     """6M cube primitives, beta log-uniform [0.3,16], SH3, 3840x2160."""
     return (cube_scene(n, seed=seed, sh_degree=3, beta_range=(0.3, 16.0), beta_log=True),
             tiny_camera(3840, 2160))
+
+
+def stress_beta2_workload(n: int = 6_000_000, seed: int = 4):
+    """The stress scene and view with every beta set to 2 (the Gaussian degenerate case)."""
+    sc, cam = stress_workload(n, seed)
+    sc.betas[:] = 2.0
+    return sc, cam
