@@ -303,6 +303,7 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the differentiation and stress legs")
+    ap.add_argument("--segment-tiles", type=int, default=16, help="binning granularity (ges_params.segment_tiles)")
     ap.add_argument("--profile", action="store_true",
                     help="minimal run for ncu: no work counters, e2e or CPU baseline; warmup + steps fwd+bwd")
     args = ap.parse_args()
@@ -337,7 +338,7 @@ def main():
     probe = render.Frame(sc.n, WIDTH, HEIGHT, key_capacity=0, ctx=ctx)
     Ks, Fs = [], []
     for cam in (cams[:1] if args.profile else cams):
-        probe.forward(t, sc.sh_degree, cam)
+        probe.forward(t, sc.sh_degree, cam, {"segment_tiles": args.segment_tiles})
         if args.profile:
             Ks.append(int(ges.ges_frame_status(probe.handle)[1] * 1.3))
             Fs.append((0, 0, 0))
@@ -351,6 +352,7 @@ def main():
     frame = render.Frame(sc.n, WIDTH, HEIGHT, key_capacity=cap, ctx=ctx)
     gcam = [ges.make_camera(c) for c in cams]
     params = ges.params_default()
+    params.segment_tiles = args.segment_tiles
     img = torch.empty((3, HEIGHT, WIDTH), device=dev)
     T = torch.empty((HEIGHT, WIDTH), device=dev)
     nc = torch.empty((HEIGHT, WIDTH), dtype=torch.int32, device=dev)
@@ -494,7 +496,9 @@ def main():
     if not args.no_extra:
         out["differentiation"] = differentiation_bench(20, 3, dev)
         torch.cuda.empty_cache()
-        out["stress_beta2"] = stress_bench(5, 3, dev)
+        out["stress"] = stress_bench(5, 3, dev, beta2=False, segment_tiles=256)
+        torch.cuda.empty_cache()
+        out["stress_beta2"] = stress_bench(5, 3, dev, beta2=True, segment_tiles=args.segment_tiles)
         torch.cuda.empty_cache()
     if not args.no_serve:
         del t, grads
@@ -570,20 +574,21 @@ def differentiation_bench(steps, warmup, dev):
             "K": int(K), "loss": float(loss.detach())}
 
 
-def stress_bench(steps, warmup, dev):
-    """The stress view with beta = 2 everywhere (6M cube primitives, SH3, 3840x2160): fwd and
-    fwd+bwd.  The beta log-U[0.3,16] form of this configuration needs about 3.3e10 duplicates and
-    does not fit any exact per-tile binning."""
+def stress_bench(steps, warmup, dev, beta2, segment_tiles):
+    """The stress configuration (6M cube primitives, SH3, 3840x2160): fwd and fwd+bwd, either with
+    beta log-U[0.3,16] (very sharp and very wide kernels; listed per tile row, segment_tiles =
+    256) or with beta = 2 everywhere (the Gaussian degenerate case)."""
     import torch
     from paper_2402_10128_gb300 import ges, render, scenes
-    sc, cam = scenes.stress_beta2_workload()
+    sc, cam = scenes.stress_beta2_workload() if beta2 else scenes.stress_workload()
     t = render.scene_tensors(sc, dev)
     probe = render.Frame(sc.n, cam.width, cam.height, key_capacity=0)
-    probe.forward(t, sc.sh_degree, cam)
+    probe.forward(t, sc.sh_degree, cam, {"segment_tiles": segment_tiles})
     K = probe.status()[1]
     probe.close()
     frame = render.Frame(sc.n, cam.width, cam.height, key_capacity=int(K * 1.02) + 4096)
     gcam, params = ges.make_camera(cam), ges.params_default()
+    params.segment_tiles = segment_tiles
     H, W = cam.height, cam.width
     img = torch.empty((3, H, W), device=dev)
     T = torch.empty((H, W), device=dev)
@@ -614,7 +619,9 @@ def stress_bench(steps, warmup, dev):
         out["fwd_bwd" if bwd else "fwd"] = {"mpix_s": W * H / (ms / 1e3) / 1e6, "ms_per_frame": ms}
     assert frame.status()[0] == 0
     frame.close()
-    return {"workload": "stress, beta = 2: 6M cube primitives, SH3, 3840x2160", "K": int(K), "steps": steps, **out}
+    form = "beta = 2" if beta2 else "beta log-U[0.3,16]"
+    return {"workload": f"stress, {form}: 6M cube primitives, SH3, 3840x2160", "segment_tiles": segment_tiles,
+            "K_entries": int(K), "steps": steps, **out}
 
 
 def e2e(args, sc, gcam, frame, params, dev, stream, ws, dist):

@@ -81,6 +81,12 @@ typedef struct ges_params {
   float extent_margin_rel;/* relative safety margin on the tile extent (1e-3) */
   float extent_margin_abs;/* absolute safety margin on the tile extent, px (1e-2) */
   float clamp_fov;        /* tangent clamp of the EWA Jacobian, in half-image units (1.3) */
+  int32_t segment_tiles;  /* binning granularity: tiles per list segment along x, a power of two
+                             in [1, 1024] (16).  Each tile row is cut into segments of this many
+                             tiles and a primitive is listed once per segment its extent meets
+                             (1 lists every tile separately).  Larger segments mean fewer entries
+                             to sort and more entries for the composite to skip; the images do
+                             not depend on it. */
 } ges_params;
 
 typedef struct ges_scene {
@@ -119,7 +125,7 @@ ges_status ges_ctx_create(int device, size_t hbm_budget_bytes, ges_ctx** out);
 void ges_ctx_destroy(ges_ctx* ctx);
 
 /* Per-frame workspace for up to n_capacity primitives at width x height.
-   key_capacity: maximum number of (tile, primitive) duplicates K.  0 selects
+   key_capacity: maximum number of (segment, primitive) entries K (see ges_bin_sort).  0 selects
    automatic growth: ges_bin_sort then synchronises the stream once per call to read
    K and reallocates when needed.  With key_capacity > 0 ges_bin_sort never
    synchronises (the sequence is graph-capturable); when K exceeds it the frame is
@@ -137,18 +143,20 @@ void ges_frame_destroy(ges_frame* frame);
 ges_status ges_preprocess(ges_frame* frame, const ges_scene* scene, const ges_camera* cam,
                           const ges_params* params, void* stream);
 
-/* Binning: depth sort of the primitives (radix, 32-bit float keys), exclusive scan of
-   the tiles each meets (per tile row, the columns its elliptical extent spans), duplicate
-   generation in depth order, stable radix sort by tile id, and per-tile [start,end) ranges.
-   The result equals a stable sort of the 64-bit keys (tile << 32 | depth bits) with
-   values = primitive index. */
+/* Binning: depth sort of the primitives (radix, 32-bit float keys); per primitive and tile row,
+   the columns its elliptical extent spans; an exclusive scan of the entries each primitive makes
+   (one per segment of params->segment_tiles tiles that its spans meet); entry generation in
+   depth order; a stable radix sort by segment id; per-segment [start,end) ranges.  An entry
+   carries the columns of its span inside the segment, so a tile's list (the entries of its
+   segment whose span contains the tile, in order) equals a stable sort of the 64-bit keys
+   (tile << 32 | depth bits) with values = primitive index, restricted to that tile. */
 ges_status ges_bin_sort(ges_frame* frame, void* stream);
 
 /* Forward composite (Sec. 3.2): per pixel, front to back over its tile's list,
    q = d^T conic d, G = exp(-1/2 q^(beta/2)) (or exp(-1/2 q)), alpha = min(alpha_max, kappa G),
    skip alpha < alpha_min, stop before T drops below t_min.  Outputs (device, caller-owned):
    img [3,H,W] = colour + T * bg, final_T [H,W], n_contrib [H,W] (1-based position, in the
-   tile's list, of the last fragment composited; 0 if none). */
+   list of the tile's segment, of the last entry composited; 0 if none). */
 ges_status ges_render_fwd(ges_frame* frame, float* img, float* final_T, uint32_t* n_contrib, void* stream);
 
 /* Backward: gradients of L with respect to every scene parameter, given dL/dimg [3,H,W].
@@ -160,12 +168,13 @@ ges_status ges_render_bwd(ges_frame* frame, const ges_scene* scene, const float*
                           void* stream);
 
 /* Synchronises `stream` and reports GES_ERR_CAPACITY if the last ges_bin_sort overflowed,
-   else GES_OK.  *num_keys (optional) receives K. */
+   else GES_OK.  *num_keys (optional) receives K, the number of (segment, primitive) entries. */
 ges_status ges_frame_status(ges_frame* frame, void* stream, int64_t* num_keys);
 
-/* Inspection (tests, tools).  Synchronises `stream`.  Copies to HOST buffers:
-   the sorted 64-bit keys (tile << 32 | depth bits) and values (primitive index) of the
-   last ges_bin_sort, max_keys entries at most; *num_keys receives K. */
+/* Inspection (tests, tools).  Synchronises `stream`.  Expands the segment lists of the last
+   ges_bin_sort into per-tile lists and copies to HOST buffers the sorted 64-bit keys
+   (tile << 32 | depth bits) and values (primitive index), max_keys entries at most;
+   *num_keys receives the number of (tile, primitive) entries. */
 ges_status ges_frame_keys(ges_frame* frame, void* stream, uint64_t* keys, uint32_t* vals,
                           int64_t max_keys, int64_t* num_keys);
 
@@ -173,7 +182,8 @@ ges_status ges_frame_keys(ges_frame* frame, void* stream, uint64_t* keys, uint32
    ges_preprocess to HOST buffers (any may be NULL): depth_key [n] (float bits of the camera
    depth, 0xFFFFFFFF if culled), rect [n,4] int32 (x0,y0,x1,y1 tiles, end-exclusive),
    record [n,12] fp32 (mean x, mean y, q limit, beta exponent, conic a, b, c, opacity,
-   r, g, b, 0), tile ranges [tiles,2] uint32.  Also the intermediate 2D gradients of the
+   r, g, b, 0), tile ranges [tiles,2] uint32 (into the expanded list of ges_frame_keys; empty
+   tiles hold [0,0]).  Also the intermediate 2D gradients of the
    last ges_render_bwd, grad2d [n,12] (mx, my, conic a, b, c, opacity, beta exponent, r, g, b). */
 ges_status ges_frame_inspect(ges_frame* frame, void* stream, uint32_t* depth_key, int32_t* rect,
                              float* record, uint32_t* ranges, float* grad2d);
@@ -182,7 +192,8 @@ ges_status ges_frame_inspect(ges_frame* frame, void* stream, uint32_t* depth_key
    buffers while counting work, then synchronises `stream`: *evaluated receives the number of
    (fragment, pixel) pairs tested before each pixel stopped, *in_extent those whose q was within
    the primitive's extent (the pairs that evaluate the falloff), *composited those that were
-   composited (alpha >= alpha_min), *num_keys K.  Any output pointer may be NULL. */
+   composited (alpha >= alpha_min), *num_keys K (segment entries).  Any output pointer may be
+   NULL. */
 ges_status ges_frame_count_work(ges_frame* frame, void* stream, int64_t* evaluated, int64_t* in_extent,
                                 int64_t* composited, int64_t* num_keys);
 

@@ -82,6 +82,10 @@ Params to_params(const ges_params& p) {
   P.margin_abs = p.extent_margin_abs;
   P.clamp_fov = p.clamp_fov;
   P.mode = p.falloff;
+  int l = 0;
+  while ((1 << l) < p.segment_tiles) ++l;
+  P.seg_log2 = l;
+  P.seg_bits = 0;  // set once the segment count is known
   return P;
 }
 
@@ -95,6 +99,8 @@ ges_status check_params(const ges_params* p) {
   if (!(p->dilation >= 0.f) || !(p->rho >= 0.f) || !(p->extent_margin_rel >= 0.f) || !(p->extent_margin_abs >= 0.f) ||
       !(p->clamp_fov > 0.f))
     return fail(GES_ERR_INVALID_ARG, "dilation, rho and margins must be >= 0, clamp_fov > 0");
+  if (p->segment_tiles < 1 || p->segment_tiles > 1024 || (p->segment_tiles & (p->segment_tiles - 1)))
+    return fail(GES_ERR_INVALID_ARG, "segment_tiles %d is not a power of two in [1, 1024]", p->segment_tiles);
   return GES_OK;
 }
 
@@ -119,7 +125,8 @@ ges_status check_scene(const ges_scene* s) {
   return GES_OK;
 }
 
-void fill_view(ViewDesc& v, const ges_camera& c, const ges_scene& s, int64_t prim_base, int32_t tile_base) {
+void fill_view(ViewDesc& v, const ges_camera& c, const ges_scene& s, int64_t prim_base, int32_t tile_base,
+               int32_t seg_base, int seg_log2) {
   std::memset(&v, 0, sizeof(v));
   for (int r = 0; r < 3; ++r)
     for (int k = 0; k < 4; ++k) v.V[4 * r + k] = c.viewmat[4 * r + k];
@@ -130,6 +137,8 @@ void fill_view(ViewDesc& v, const ges_camera& c, const ges_scene& s, int64_t pri
   v.tiles_x = (c.width + kTile - 1) / kTile;
   v.tiles_y = (c.height + kTile - 1) / kTile;
   v.tile_base = tile_base;
+  v.seg_base = seg_base;
+  v.segs_x = (v.tiles_x + (1 << seg_log2) - 1) >> seg_log2;
   v.sh_degree = s.sh_degree;
   v.prim_base = prim_base;
   v.n = s.n;
@@ -142,6 +151,14 @@ int bits_for(int64_t count) {
   return b;
 }
 
+ges_status set_segment_bits(Params& P, int64_t total_segs) {
+  P.seg_bits = bits_for(total_segs > 1 ? total_segs : 2);
+  if (P.seg_bits + 2 * P.seg_log2 > 32)
+    return fail(GES_ERR_INVALID_ARG, "%lld segments of %d tiles do not fit a 32-bit list key; use fewer tiles per segment",
+                (long long)total_segs, 1 << P.seg_log2);
+  return GES_OK;
+}
+
 // ---------------------------------------------------------------- frame buffers
 static void frame_free_keys(ges_frame* f) {
   for (int i = 0; i < 2; ++i) {
@@ -151,11 +168,8 @@ static void frame_free_keys(ges_frame* f) {
   }
   ctx_free(f->ctx, f->hist, sizeof(uint32_t) * f->hist_cap);
   ctx_free(f->ctx, f->scan.buf, f->scan.bytes);
-  ctx_free(f->ctx, f->keys64, sizeof(unsigned long long) * f->keys64_cap);
   f->hist = nullptr;
   f->scan.buf = nullptr;
-  f->keys64 = nullptr;
-  f->keys64_cap = 0;
 }
 
 static ges_status frame_alloc_keys(ges_frame* f, int64_t key_cap) {
@@ -178,6 +192,48 @@ static ges_status frame_alloc_keys(ges_frame* f, int64_t key_cap) {
 
 using namespace ges;
 
+// The per-tile lists of the last binning, expanded on the host from the segment lists: tiles in
+// id order; for each, the entries of its segment whose span covers it, in list order.  Calls
+// emit(tile, list entry index) for each (tile, entry) and returns the per-tile [start, end) in
+// the expanded order through tile_ranges (optional, 2 per tile).
+template <class Emit>
+static ges_status walk_tile_lists(ges_frame* f, cudaStream_t s, std::vector<uint32_t>& tk, Emit emit,
+                                  uint32_t* tile_ranges) {
+  int64_t K = 0;
+  ges_status st = ges_frame_status(f, s, &K);
+  if (st != GES_OK) return st;
+  tk.resize((size_t)K);
+  std::vector<uint2> rg((size_t)f->n_segs);
+  cudaError_t e;
+  if (K && (e = cudaMemcpy(tk.data(), f->tile_keys, 4 * (size_t)K, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "copy list keys");
+  if ((e = cudaMemcpy(rg.data(), f->ranges, sizeof(uint2) * f->n_segs, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "copy ranges");
+  const int L = f->P.seg_log2, sb = f->P.seg_bits;
+  const uint32_t m = (1u << L) - 1u;
+  const int32_t sx = f->vt.t.v[0].segs_x;
+  uint64_t pos = 0;
+  for (int32_t ty = 0; ty < f->tiles_y; ++ty)
+    for (int32_t tx = 0; tx < f->tiles_x; ++tx) {
+      const int64_t tile = (int64_t)ty * f->tiles_x + tx;
+      const uint2 r = rg[(size_t)ty * sx + (tx >> L)];
+      const uint32_t to = (uint32_t)tx & m;
+      const uint64_t start = pos;
+      for (uint32_t i = r.x; i < r.y; ++i) {
+        const uint32_t key = tk[i];
+        if (((key >> sb) & m) <= to && to <= ((key >> (sb + L)) & m)) {
+          emit(tile, i);
+          ++pos;
+        }
+      }
+      if (tile_ranges) {
+        tile_ranges[2 * tile] = pos > start ? (uint32_t)start : 0u;
+        tile_ranges[2 * tile + 1] = pos > start ? (uint32_t)pos : 0u;
+      }
+    }
+  return GES_OK;
+}
+
 extern "C" {
 
 const char* ges_last_error(void) { return g_last_error.c_str(); }
@@ -193,6 +249,7 @@ ges_status ges_params_default(ges_params* out) {
   out->extent_margin_rel = 1e-3f;
   out->extent_margin_abs = 1e-2f;
   out->clamp_fov = 1.3f;
+  out->segment_tiles = 16;
   return GES_OK;
 }
 
@@ -421,11 +478,14 @@ ges_status ges_preprocess(ges_frame* f, const ges_scene* scene, const ges_camera
     return fail(GES_ERR_INVALID_ARG, "camera %dx%d != frame %dx%d", cam->width, cam->height, f->W, f->H);
   if ((st = use_device(f->ctx->device)) != GES_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
+  f->P = to_params(*params);
   f->vt.t.n = 1;
-  fill_view(f->vt.t.v[0], *cam, *scene, 0, 0);
+  fill_view(f->vt.t.v[0], *cam, *scene, 0, 0, 0, f->P.seg_log2);
   f->vt.t.total_prims = (unsigned long long)scene->n;
   f->vt.t.total_tiles = f->n_tiles;
-  f->P = to_params(*params);
+  f->n_segs = (int64_t)f->vt.t.v[0].segs_x * f->tiles_y;
+  f->vt.t.total_segs = f->n_segs;
+  if ((st = set_segment_bits(f->P, f->n_segs)) != GES_OK) return st;
   f->n = scene->n;
   f->sh_degree = scene->sh_degree;
   {
@@ -452,7 +512,8 @@ ges_status ges_bin_sort(ges_frame* f, void* stream) {
   int cur = 0;
   {
     TraceScope tr(f->ctx, "depth_sort", s);
-    radix_sort_pairs(f->dk, f->pv, cur, f->n, nullptr, f->n, 32, f->hist, f->hist_cap, f->scan, s);
+    if (!radix_sort_pairs(f->dk, f->pv, cur, f->n, nullptr, f->n, 32, f->hist, f->hist_cap, f->scan, s))
+      return fail(GES_ERR_CUDA, "internal: depth-sort histogram exceeds its buffer");
   }
   f->sorted_prims = f->pv[cur];
   // tiles touched in depth order, exclusive scan -> offsets, K
@@ -479,20 +540,21 @@ ges_status ges_bin_sort(ges_frame* f, void* stream) {
   {
     TraceScope tr(f->ctx, "k_keygen", s);
     launch_keygen<FrameViews>(f->vt, f->offsets, f->touched, f->d_K, f->n, f->sorted_prims, f->rect, f->ext, f->rec,
-                              f->P.margin_abs, f->key_cap, f->tk[0], f->tv[0], f->d_flags, s);
+                              f->P, f->key_cap, f->tk[0], f->tv[0], f->d_flags, s);
   }
   int tcur = 0;
   {
     TraceScope tr(f->ctx, "tile_sort", s);
-    radix_sort_pairs(f->tk, f->tv, tcur, 0, f->d_K, f->key_cap, bits_for(f->n_tiles), f->hist, f->hist_cap, f->scan,
-                     s);
+    if (!radix_sort_pairs(f->tk, f->tv, tcur, 0, f->d_K, f->key_cap, f->P.seg_bits, f->hist, f->hist_cap, f->scan, s))
+      return fail(GES_ERR_CUDA, "internal: list-sort histogram exceeds its buffer");
   }
   f->tile_keys = f->tk[tcur];
   f->tile_vals = f->tv[tcur];
-  if ((e = cudaMemsetAsync(f->ranges, 0, sizeof(uint2) * f->n_tiles, s)) != cudaSuccess) return cuda_fail(e, "memset ranges");
+  if ((e = cudaMemsetAsync(f->ranges, 0, sizeof(uint2) * f->n_segs, s)) != cudaSuccess) return cuda_fail(e, "memset ranges");
   {
     TraceScope tr(f->ctx, "k_ranges", s);
-    launch_ranges(f->tile_keys, f->d_K, f->key_cap, f->ranges, f->ctx->num_sms, s);
+    launch_ranges(f->tile_keys, f->d_K, f->key_cap, (uint32_t)((1ull << f->P.seg_bits) - 1), f->ranges, f->ctx->num_sms,
+                  s);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "bin_sort launch");
   f->have_sort = true;
@@ -509,7 +571,8 @@ ges_status ges_render_fwd(ges_frame* f, float* img, float* final_T, uint32_t* n_
   f->vt.t.v[0].n_contrib = n_contrib;
   {
     TraceScope tr(f->ctx, "k_render_fwd", (cudaStream_t)stream);
-    launch_render_fwd<FrameViews>(f->vt, f->n_tiles, f->ranges, f->tile_vals, f->rec, f->P, (cudaStream_t)stream);
+    launch_render_fwd<FrameViews>(f->vt, f->n_tiles, f->ranges, f->tile_keys, f->tile_vals, f->rec, f->P,
+                                  (cudaStream_t)stream);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "render_fwd launch");
@@ -543,7 +606,7 @@ ges_status ges_render_bwd(ges_frame* f, const ges_scene* scene, const float* fin
     return cuda_fail(e, "memset g2d");
   {
     TraceScope tr(f->ctx, "k_render_bwd", s);
-    launch_render_bwd<FrameViews>(f->vt, f->n_tiles, f->ranges, f->tile_vals, f->rec, f->P, f->g2d, s);
+    launch_render_bwd<FrameViews>(f->vt, f->n_tiles, f->ranges, f->tile_keys, f->tile_vals, f->rec, f->P, f->g2d, s);
   }
   {
     TraceScope tr(f->ctx, "k_preprocess_bwd", s);
@@ -573,27 +636,34 @@ ges_status ges_frame_status(ges_frame* f, void* stream, int64_t* num_keys) {
 ges_status ges_frame_keys(ges_frame* f, void* stream, uint64_t* keys, uint32_t* vals, int64_t max_keys, int64_t* num_keys) {
   if (!f) return fail(GES_ERR_INVALID_ARG, "frame is NULL");
   if (!f->have_sort) return fail(GES_ERR_INVALID_ARG, "no sorted keys yet");
-  int64_t K = 0;
-  ges_status st = ges_frame_status(f, stream, &K);
-  if (num_keys) *num_keys = K;
+  ges_status st = use_device(f->ctx->device);
   if (st != GES_OK) return st;
-  int64_t m = K < max_keys ? K : max_keys;
-  if (m <= 0) return GES_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  if (f->keys64_cap < f->key_cap) {
-    ctx_free(f->ctx, f->keys64, sizeof(unsigned long long) * f->keys64_cap);
-    f->keys64_cap = 0;
-    if ((st = ctx_alloc(f->ctx, (void**)&f->keys64, sizeof(unsigned long long) * f->key_cap)) != GES_OK) return st;
-    f->keys64_cap = f->key_cap;
+  std::vector<uint32_t> tv, dk;
+  const bool copy = (keys || vals) && max_keys > 0;
+  if (copy) {
+    int64_t K = 0;
+    if ((st = ges_frame_status(f, stream, &K)) != GES_OK) return st;
+    tv.resize((size_t)K);
+    dk.resize((size_t)f->n);
+    cudaError_t e;
+    if (K && (e = cudaMemcpy(tv.data(), f->tile_vals, 4 * (size_t)K, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(e, "copy list values");
+    if (f->n && (e = cudaMemcpy(dk.data(), f->depth_key, 4 * (size_t)f->n, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(e, "copy depth keys");
   }
-  launch_make_keys(f->tile_keys, f->tile_vals, f->depth_key, f->d_K, f->key_cap, f->keys64, s);
-  cudaError_t e;
-  if (keys && (e = cudaMemcpyAsync(keys, f->keys64, 8 * m, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-    return cuda_fail(e, "copy keys");
-  if (vals && (e = cudaMemcpyAsync(vals, f->tile_vals, 4 * m, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-    return cuda_fail(e, "copy vals");
-  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "sync");
-  return GES_OK;
+  std::vector<uint32_t> tk;
+  int64_t count = 0;
+  st = walk_tile_lists(f, s, tk, [&](int64_t tile, uint32_t i) {
+    if (copy && count < max_keys) {
+      const uint32_t g = tv[i];
+      if (keys) keys[count] = ((uint64_t)tile << 32) | dk[g];
+      if (vals) vals[count] = g;
+    }
+    ++count;
+  }, nullptr);
+  if (num_keys) *num_keys = count;
+  return st;
 }
 
 ges_status ges_frame_inspect(ges_frame* f, void* stream, uint32_t* depth_key, int32_t* rect, float* record,
@@ -617,8 +687,14 @@ ges_status ges_frame_inspect(ges_frame* f, void* stream, uint32_t* depth_key, in
   }
   if (record && n && (e = cudaMemcpy(record, f->rec, sizeof(Rec) * n, cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_fail(e, "copy records");
-  if (ranges && (e = cudaMemcpy(ranges, f->ranges, sizeof(uint2) * f->n_tiles, cudaMemcpyDeviceToHost)) != cudaSuccess)
-    return cuda_fail(e, "copy ranges");
+  if (ranges) {
+    if (!f->have_sort) {
+      std::memset(ranges, 0, sizeof(uint32_t) * 2 * f->n_tiles);
+    } else {
+      std::vector<uint32_t> tk;
+      if ((st = walk_tile_lists(f, s, tk, [](int64_t, uint32_t) {}, ranges)) != GES_OK) return st;
+    }
+  }
   if (grad2d && n && (e = cudaMemcpy(grad2d, f->g2d, sizeof(float4) * 3 * n, cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_fail(e, "copy grad2d");
   return GES_OK;
@@ -644,7 +720,7 @@ ges_status ges_frame_count_work(ges_frame* f, void* stream, int64_t* evaluated, 
   vt.t.v[0].n_contrib = reinterpret_cast<uint32_t*>(f->work_img + 4 * npx);
   cudaError_t e;
   if ((e = cudaMemsetAsync(f->work_stats, 0, 32, s)) != cudaSuccess) return cuda_fail(e, "memset stats");
-  launch_render_fwd<FrameViews>(vt, f->n_tiles, f->ranges, f->tile_vals, f->rec, f->P, s, f->work_stats);
+  launch_render_fwd<FrameViews>(vt, f->n_tiles, f->ranges, f->tile_keys, f->tile_vals, f->rec, f->P, s, f->work_stats);
   unsigned long long h[3] = {0, 0, 0};
   if ((e = cudaMemcpyAsync(h, f->work_stats, 24, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(e, "copy stats");
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "sync");

@@ -32,6 +32,7 @@ struct ges_frame {
   int64_t n_cap = 0;
   int32_t W = 0, H = 0, tiles_x = 0, tiles_y = 0;
   int64_t n_tiles = 0;
+  int64_t n_segs = 0;              // list segments of the current parameters (<= n_tiles)
   int64_t key_cap = 0;
   bool auto_cap = false;
   // per primitive
@@ -50,8 +51,6 @@ struct ges_frame {
   uint32_t* tv[2] = {nullptr, nullptr};
   uint32_t* hist = nullptr;
   int64_t hist_cap = 0;
-  unsigned long long* keys64 = nullptr;
-  int64_t keys64_cap = 0;
   ges::ScanScratch scan;
   // per tile
   uint2* ranges = nullptr;
@@ -83,6 +82,8 @@ Params to_params(const ges_params& p);
 ges_status check_params(const ges_params* p);
 ges_status check_camera(const ges_camera* c);
 ges_status check_scene(const ges_scene* s);
-void fill_view(ViewDesc& v, const ges_camera& c, const ges_scene& s, int64_t prim_base, int32_t tile_base);
+void fill_view(ViewDesc& v, const ges_camera& c, const ges_scene& s, int64_t prim_base, int32_t tile_base,
+               int32_t seg_base, int seg_log2);
+ges_status set_segment_bits(Params& P, int64_t total_segs);
 int bits_for(int64_t count);
 }  // namespace ges

@@ -13,7 +13,9 @@ constexpr int kServeMaxViews = 32;  // views per batched (serving) launch
 constexpr uint32_t kCulledKey = 0xffffffffu;
 
 // One view of one scene inside a batched launch.  Global primitive ids of the
-// view are [prim_base, prim_base + n); global tile ids [tile_base, tile_base + tiles_x*tiles_y).
+// view are [prim_base, prim_base + n); global tile ids [tile_base, tile_base + tiles_x*tiles_y);
+// global segment ids [seg_base, seg_base + segs_x*tiles_y), where a segment is a run of
+// 2^seg_log2 tiles of one tile row (segs_x = ceil(tiles_x / 2^seg_log2)).
 struct ViewDesc {
   float V[12];                 // world -> camera, rows of the 3x4 upper block
   float fx, fy, cx, cy;
@@ -22,6 +24,7 @@ struct ViewDesc {
   float bg[3];
   int32_t W, H, tiles_x, tiles_y;
   int32_t tile_base;
+  int32_t seg_base, segs_x;
   int32_t sh_degree;
   int64_t prim_base;
   int64_t n;
@@ -52,6 +55,7 @@ struct ViewTable {
   int32_t pad;
   unsigned long long total_prims;  // sum of the views' n
   long long total_tiles;           // sum of the views' tiles
+  long long total_segs;            // sum of the views' segments
   ViewDesc v[MAXV];
 };
 
@@ -98,7 +102,22 @@ __device__ __forceinline__ int view_of_tile(const ViewTable<MAXV>& vt, int64_t t
 struct Params {
   float rho, dilation, alpha_max, alpha_min, t_min, margin_rel, margin_abs, clamp_fov;
   int32_t mode;                // 0 GEF falloff, 1 Gaussian-form (paper's rasterizer)
+  int32_t seg_log2;            // log2 of the tiles per segment
+  int32_t seg_bits;            // bits of a global segment id (the radix sort's key width)
 };
+
+// A list entry's key: the global segment id in the low seg_bits bits, then the first and last
+// tile of the primitive's span inside the segment, relative to the segment's first tile
+// (seg_log2 bits each).  The sort orders by the segment bits only.
+__device__ __forceinline__ uint32_t seg_key(uint32_t seg, uint32_t off0, uint32_t off1, const Params& P) {
+  return seg | (off0 << P.seg_bits) | (off1 << (P.seg_bits + P.seg_log2));
+}
+// does the entry's span contain tile offset `to` (0 .. 2^seg_log2 - 1) of its segment?
+__device__ __forceinline__ bool seg_key_covers(uint32_t key, uint32_t to, const Params& P) {
+  const uint32_t m = (1u << P.seg_log2) - 1u;
+  const uint32_t off0 = (key >> P.seg_bits) & m, off1 = (key >> (P.seg_bits + P.seg_log2)) & m;
+  return off0 <= to && to <= off1;
+}
 
 // Projected primitive as the compositing kernels read it (48 bytes, gathered by id).
 //   a = (mean x, mean y, q limit, beta exponent hb)    hb = beta/2 (GEF) or 1

@@ -42,38 +42,39 @@ void launch_gather_touched(const uint32_t* sorted_vals, const uint32_t* tprim, i
 
 // stable LSD radix sort of (u32 key, u32 value) on the low `total_bits` bits.  The element count is
 // n_dev (device) if non-null, else n_host; buffers hold n_cap elements.  keys[cur]/vals[cur] hold the
-// input; on return `cur` indexes the sorted output.
-void radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_host, const unsigned long long* n_dev,
+// input; on return `cur` indexes the sorted output.  hist holds hist_cap entries; returns false,
+// launching nothing, if a pass's histogram would not fit (radix_hist_entries gives the need).
+bool radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_host, const unsigned long long* n_dev,
                       int64_t n_cap, int total_bits, uint32_t* hist, int64_t hist_cap, ScanScratch& sc, cudaStream_t s);
-int64_t radix_hist_entries(int64_t n_cap, int total_bits);
+int64_t radix_hist_entries(int64_t n_cap, int max_bits);
 
 // n: primitives (the capacity when n_dev gives the count on the device); touched: tiles per
 // primitive in depth order (the scan's input)
 template <class VS>
 void launch_keygen(const VS& vs, const unsigned long long* offsets, const uint32_t* touched,
                    const unsigned long long* K_dev, int64_t n, const uint32_t* sorted_vals, const ushort4* rect,
-                   const float4* ext, const Rec* rec, float margin_abs, int64_t cap,
+                   const float4* ext, const Rec* rec, const Params& P, int64_t cap,
                    uint32_t* tile_keys, uint32_t* tile_vals, uint32_t* flags, cudaStream_t s,
                    const unsigned long long* n_dev = nullptr);
-void launch_ranges(const uint32_t* tile_keys, const unsigned long long* K_dev, int64_t cap, uint2* ranges, int num_sms,
-                   cudaStream_t s);
-// materialise the 64-bit keys (tile << 32 | depth key) of a sorted list (inspection only)
-void launch_make_keys(const uint32_t* tile_keys, const uint32_t* tile_vals, const uint32_t* depth_key,
-                      const unsigned long long* K_dev, int64_t cap, unsigned long long* keys64, cudaStream_t s);
+// [start, end) per segment of the sorted list (segment id = key & seg_mask); ranges of empty
+// segments are left as they are (the caller zeroes them)
+void launch_ranges(const uint32_t* tile_keys, const unsigned long long* K_dev, int64_t cap, uint32_t seg_mask,
+                   uint2* ranges, int num_sms, cudaStream_t s);
 
 constexpr uint32_t kFlagOverflow = 1u;
 
 // ---- compositing (raster.cu)
-// stats (optional, device u64[2]): number of (fragment, pixel) pairs evaluated before the stop, and of
-// those within the primitive's extent (the ones that reach the falloff's transcendentals)
+// ranges: per segment; keys, vals: the sorted list (segment key, primitive id).
+// stats (optional, device u64[3]): numbers of (fragment, pixel) pairs evaluated before the stop, of
+// those within the primitive's extent, and of those composited.
 // One CTA per tile (grid = total_tiles), or, with tile_counter, a persistent grid whose CTAs take
 // tiles from *tile_counter (zeroed by the caller) until the table's total_tiles are done.
 template <class VS>
-void launch_render_fwd(const VS& vs, int64_t total_tiles, const uint2* ranges, const uint32_t* vals, const Rec* rec,
-                       const Params& P, cudaStream_t s, unsigned long long* stats = nullptr,
-                       unsigned int* tile_counter = nullptr, int num_sms = 0);
+void launch_render_fwd(const VS& vs, int64_t total_tiles, const uint2* ranges, const uint32_t* keys,
+                       const uint32_t* vals, const Rec* rec, const Params& P, cudaStream_t s,
+                       unsigned long long* stats = nullptr, unsigned int* tile_counter = nullptr, int num_sms = 0);
 template <class VS>
-void launch_render_bwd(const VS& vs, int64_t total_tiles, const uint2* ranges, const uint32_t* vals, const Rec* rec,
-                       const Params& P, float4* g2d, cudaStream_t s);
+void launch_render_bwd(const VS& vs, int64_t total_tiles, const uint2* ranges, const uint32_t* keys,
+                       const uint32_t* vals, const Rec* rec, const Params& P, float4* g2d, cudaStream_t s);
 
 }  // namespace ges

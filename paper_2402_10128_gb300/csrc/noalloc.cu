@@ -138,12 +138,15 @@ extern "C" ges_status ges_render_fwd_noalloc(const ges_scene* scene, const ges_c
   cudaStream_t s = (cudaStream_t)stream;
   unsigned char* b = ds->base;
   const int64_t n = scene->n;
+  Params P = to_params(*params);
   FrameViews vt;
   vt.t.n = 1;
-  fill_view(vt.t.v[0], *cam, *scene, 0, 0);
+  fill_view(vt.t.v[0], *cam, *scene, 0, 0, 0, P.seg_log2);
   vt.t.total_prims = (unsigned long long)scene->n;
   vt.t.total_tiles = tiles;
-  const Params P = to_params(*params);
+  const int64_t segs = (int64_t)vt.t.v[0].segs_x * vt.t.v[0].tiles_y;
+  vt.t.total_segs = segs;
+  if ((st = set_segment_bits(P, segs)) != GES_OK) return st;
   uint32_t* dk[2] = {at<uint32_t>(b, kL.dk0), at<uint32_t>(b, kL.dk1)};
   uint32_t* pv[2] = {at<uint32_t>(b, kL.pv0), at<uint32_t>(b, kL.pv1)};
   uint32_t* tk[2] = {at<uint32_t>(b, kL.tk0), at<uint32_t>(b, kL.tk1)};
@@ -161,26 +164,28 @@ extern "C" ges_status ges_render_fwd_noalloc(const ges_scene* scene, const ges_c
   scan.buf = b + kL.scan;
   scan.bytes = kNaScanBytes;
 
-  // what must start at zero on every call: the overflow flag and the tile ranges (empty tiles
-  // are never written by the ranges kernel)
+  // what must start at zero on every call: the overflow flag and the segment ranges (empty
+  // segments are never written by the ranges kernel)
   if ((e = cudaMemsetAsync(flags, 0, 4, s)) != cudaSuccess) return cuda_fail(e, "clear flags");
-  if ((e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * tiles, s)) != cudaSuccess) return cuda_fail(e, "clear ranges");
+  if ((e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * segs, s)) != cudaSuccess) return cuda_fail(e, "clear ranges");
   float4* ext = at<float4>(b, kL.ext);
   uint32_t* tprim = at<uint32_t>(b, kL.tprim);
   launch_preprocess<FrameViews>(vt, n, P, depth_key, dk[0], pv[0], rect, rec, ext, tprim, ds->num_sms, s);
   int cur = 0;
-  radix_sort_pairs(dk, pv, cur, n, nullptr, n, 32, hist, kNaHistEntries, scan, s);
+  if (!radix_sort_pairs(dk, pv, cur, n, nullptr, n, 32, hist, kNaHistEntries, scan, s))
+    return fail(GES_ERR_CUDA, "internal: depth-sort histogram exceeds its buffer");
   launch_gather_touched(pv[cur], tprim, n, touched, s);
   scan_exclusive<uint32_t, unsigned long long>(touched, offsets, n, dK, scan, s);
-  launch_keygen<FrameViews>(vt, offsets, touched, dK, n, pv[cur], rect, ext, rec, P.margin_abs, kNaMaxKeys,
+  launch_keygen<FrameViews>(vt, offsets, touched, dK, n, pv[cur], rect, ext, rec, P, kNaMaxKeys,
                             tk[0], tv[0], flags, s);
   int tcur = 0;
-  radix_sort_pairs(tk, tv, tcur, 0, dK, kNaMaxKeys, bits_for(tiles), hist, kNaHistEntries, scan, s);
-  launch_ranges(tk[tcur], dK, kNaMaxKeys, ranges, ds->num_sms, s);
+  if (!radix_sort_pairs(tk, tv, tcur, 0, dK, kNaMaxKeys, P.seg_bits, hist, kNaHistEntries, scan, s))
+    return fail(GES_ERR_CUDA, "internal: list-sort histogram exceeds its buffer");
+  launch_ranges(tk[tcur], dK, kNaMaxKeys, (uint32_t)((1ull << P.seg_bits) - 1), ranges, ds->num_sms, s);
   vt.t.v[0].img = img;
   vt.t.v[0].final_T = final_T;
   vt.t.v[0].n_contrib = n_contrib;
-  launch_render_fwd<FrameViews>(vt, tiles, ranges, tv[tcur], rec, P, s);
+  launch_render_fwd<FrameViews>(vt, tiles, ranges, tk[tcur], tv[tcur], rec, P, s);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "no-alloc render launch");
   // the duplicate count is known only on the device: wait for it to report an overflow
   uint32_t h_flags = 0;

@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ VS v
     fy0 = fminf(fmaxf(fy0, 0.0f), (float)vd.tiles_y);
     fy1 = fminf(fmaxf(fy1, 0.0f), (float)vd.tiles_y);
     int x0 = (int)fx0, x1 = (int)fx1, y0 = (int)fy0, y1 = (int)fy1;
-    // tiles the extent meets: the sum of its row spans within the bounding box
+    // list entries: per tile row of the bounding box, the segments its span of the extent meets
     const float ql = kmul(kmul(qs, onep), onep);
     const float4 e4 = make_float4(ca, cb, cc, ql);
     const ushort4 box = make_ushort4((unsigned short)x0, (unsigned short)y0, (unsigned short)x1, (unsigned short)y1);
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ VS v
     const RowSpan rs = make_row_span(e4, u, v, P.margin_abs, box);
     unsigned nslots;
     const unsigned hex = warp_excl_scan(h, nslots);
-    uint32_t ntiles = 0;
+    uint32_t nentries = 0;
     for (unsigned cb = 0; cb < nslots; cb += 32) {
       const unsigned s = cb + lane;
       const int ow = warp_last_le(hex, s);
@@ -309,7 +309,8 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ VS v
       unsigned w = 0;
       if (s < nslots) {
         int t0, t1;
-        if (tile_row_span(q, (int)(qy0 + (s - qhex)), t0, t1)) w = (unsigned)(t1 - t0 + 1);
+        if (tile_row_span(q, (int)(qy0 + (s - qhex)), t0, t1))
+          w = (unsigned)((t1 >> P.seg_log2) - (t0 >> P.seg_log2) + 1);  // segments the span meets
       }
       unsigned W;
       const unsigned wex = warp_excl_scan(w, W);
@@ -318,17 +319,17 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ VS v
       const int l = (int)(hex + h < cb + 32u ? hex + h : cb + 32u) - (int)cb;
       const unsigned a = __shfl_sync(0xffffffffu, wex, f < 31 ? f : 31);
       const unsigned b = __shfl_sync(0xffffffffu, wex + w, l > 0 ? (l - 1 < 31 ? l - 1 : 31) : 0);
-      if (h && f < l) ntiles += b - a;
+      if (h && f < l) nentries += b - a;
     }
     if (!inb) continue;
-    const bool touched = ntiles > 0;
+    const bool touched = nentries > 0;
 
     const uint32_t dkey = touched ? __float_as_uint(tz) : kCulledKey;
     depth_key[g] = dkey;
     sort_keys[g] = dkey;
     sort_vals[g] = (uint32_t)g;
     rect[g] = touched ? box : make_ushort4(0, 0, 0, 0);
-    tprim[g] = ntiles;
+    tprim[g] = nentries;
     if (!touched) continue;
     ext[g] = e4;
 

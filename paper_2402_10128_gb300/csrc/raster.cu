@@ -93,6 +93,44 @@ __device__ __forceinline__ void eval_pair(const RecPair& r, float2 PX, float2 PY
   f.a = __fmul2_rn(hi2(c1), f.G);
 }
 
+// The shared memory a composite CTA stages one round of its segment's list in: the entries whose
+// span covers the CTA's tile, in list order (rec pairs, 1-based list positions, primitive ids).
+template <class RecT, int N>
+struct Stage {
+  RecT rec[N];
+  uint32_t pos[N];
+  uint32_t id[N];
+  uint32_t warp_count[N / 32];
+};
+
+// Keeps, in order, the round's candidates (one per thread: list entry idx, valid if `keep`) into
+// st.rec / st.pos / st.id [0, count) and returns count.  Every thread of the CTA calls it; it
+// contains two barriers, the second after the staging writes.
+template <int N, class RecT, class StageFn>
+__device__ __forceinline__ int stage_kept(Stage<RecT, N>& st, bool keep, uint32_t idx, uint32_t list_start,
+                                          const uint32_t* __restrict__ vals, StageFn stage_rec) {
+  const unsigned lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+  const unsigned m = __ballot_sync(0xffffffffu, keep);
+  if (lane == 0) st.warp_count[w] = (uint32_t)__popc(m);
+  __syncthreads();
+  uint32_t off = 0, total = 0;
+#pragma unroll
+  for (int k = 0; k < N / 32; ++k) {
+    const uint32_t c = st.warp_count[k];
+    off += k < (int)w ? c : 0u;
+    total += c;
+  }
+  if (keep) {
+    const uint32_t at = off + (uint32_t)__popc(m & ((1u << lane) - 1u));
+    const uint32_t g = vals[idx];
+    stage_rec(st.rec[at], g);
+    st.pos[at] = idx - list_start + 1u;
+    st.id[at] = g;
+  }
+  __syncthreads();
+  return (int)total;
+}
+
 struct WarpBlock {
   int x, y;  // first pixel of this thread (the second is at y + 4)
 };
@@ -107,34 +145,40 @@ __device__ __forceinline__ WarpBlock warp_block(int lt, int tiles_x) {
   return b;
 }
 
+using FwdStage = Stage<RecPair, kFwdBatch>;
+
 template <int MAXV, bool STATS>
-__device__ __forceinline__ void render_tile_fwd(const ViewTable<MAXV>& vt, int64_t tile, RecPair* batch,
-                                                const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
-                                                const Rec* __restrict__ rec, const Params& P,
-                                                unsigned long long* __restrict__ stats) {
+__device__ __forceinline__ void render_tile_fwd(const ViewTable<MAXV>& vt, int64_t tile, FwdStage& st,
+                                                const uint2* __restrict__ ranges, const uint32_t* __restrict__ keys,
+                                                const uint32_t* __restrict__ vals, const Rec* __restrict__ rec,
+                                                const Params& P, unsigned long long* __restrict__ stats) {
   const ViewDesc& vd = vt.v[view_of_tile(vt, tile)];
-  const WarpBlock wb = warp_block((int)(tile - vd.tile_base), vd.tiles_x);
+  const int lt = (int)(tile - vd.tile_base);
+  const int tx = lt % vd.tiles_x, ty = lt / vd.tiles_x;
+  const WarpBlock wb = warp_block(lt, vd.tiles_x);
   const bool inside0 = wb.x < vd.W && wb.y < vd.H, inside1 = wb.x < vd.W && wb.y + 4 < vd.H;
+  // this tile's list: the entries of its segment whose span covers tile offset `to`
+  const uint2 rg = ranges[vd.seg_base + ty * vd.segs_x + (tx >> P.seg_log2)];
+  const uint32_t to = (uint32_t)tx & ((1u << P.seg_log2) - 1u);
   const float2 PX = make_float2((float)wb.x + 0.5f, (float)wb.x + 0.5f);
   const float2 PY = make_float2((float)wb.y + 0.5f, (float)(wb.y + 4) + 0.5f);
   const float2 ONE = make_float2(1.0f, 1.0f), NEG1 = make_float2(-1.0f, -1.0f), ZERO = make_float2(0.f, 0.f);
-  const uint2 rg = ranges[tile];
   float2 T = ONE, C0 = ZERO, C1 = ZERO, C2 = ZERO;
   uint32_t last0 = 0, last1 = 0, n_eval = 0, n_range = 0, n_comp = 0;
   bool done0 = !inside0, done1 = !inside1;
   for (uint32_t base = rg.x; base < rg.y; base += kFwdBatch) {
     if (__syncthreads_count(done0 && done1) == kFwdThreads) break;
     const uint32_t idx = base + threadIdx.x;
-    if (idx < rg.y) stage_pair(batch[threadIdx.x], rec[vals[idx]]);
-    __syncthreads();
-    const int cnt = (int)min((uint32_t)kFwdBatch, rg.y - base);
+    const bool keep = idx < rg.y && seg_key_covers(keys[idx], to, P);
+    const int cnt = stage_kept<kFwdBatch>(st, keep, idx, rg.x, vals,
+                                          [&](RecPair& d, uint32_t g) { stage_pair(d, rec[g]); });
     if (!__all_sync(0xffffffffu, done0 && done1)) {
       for (int j = 0; j < cnt; ++j) {
         if (done0 && done1) break;
         PairEval f;
-        eval_pair(batch[j], PX, PY, f);
+        eval_pair(st.rec[j], PX, PY, f);
         if (STATS) {
-          const float ql = batch[j].e.x;
+          const float ql = st.rec[j].e.x;
           n_eval += (done0 ? 0u : 1u) + (done1 ? 0u : 1u);
           n_range += (!done0 && f.q0 <= ql ? 1u : 0u) + (!done1 && f.q1 <= ql ? 1u : 0u);
         }
@@ -151,11 +195,11 @@ __device__ __forceinline__ void render_tile_fwd(const ViewTable<MAXV>& vt, int64
         const float2 alpha = make_float2(c0 ? al.x : 0.f, c1 ? al.y : 0.f);
         const float2 wgt = __fmul2_rn(alpha, T);
         T = __fmul2_rn(T, __ffma2_rn(alpha, NEG1, ONE));
-        const float4 k0 = batch[j].k0, k1 = batch[j].k1;
+        const float4 k0 = st.rec[j].k0, k1 = st.rec[j].k1;
         C0 = __ffma2_rn(lo2(k0), wgt, C0);
         C1 = __ffma2_rn(hi2(k0), wgt, C1);
         C2 = __ffma2_rn(lo2(k1), wgt, C2);
-        const uint32_t kpos = base - rg.x + (uint32_t)j + 1u;
+        const uint32_t kpos = st.pos[j];
         last0 = c0 ? kpos : last0;
         last1 = c1 ? kpos : last1;
         if (STATS) n_comp += (c0 ? 1u : 0u) + (c1 ? 1u : 0u);
@@ -197,10 +241,11 @@ __device__ __forceinline__ void render_tile_fwd(const ViewTable<MAXV>& vt, int64
 
 template <class VS, bool STATS>
 __global__ void __launch_bounds__(kFwdThreads, 8) k_render_fwd(const __grid_constant__ VS vs, const uint2* __restrict__ ranges,
-                                                         const uint32_t* __restrict__ vals, const Rec* __restrict__ rec,
-                                                         const Params P, unsigned long long* __restrict__ stats) {
-  __shared__ RecPair batch[kFwdBatch];
-  render_tile_fwd<VS::kMax, STATS>(vs.get(), (int64_t)blockIdx.x, batch, ranges, vals, rec, P, stats);
+                                                            const uint32_t* __restrict__ keys,
+                                                            const uint32_t* __restrict__ vals, const Rec* __restrict__ rec,
+                                                            const Params P, unsigned long long* __restrict__ stats) {
+  __shared__ FwdStage st;
+  render_tile_fwd<VS::kMax, STATS>(vs.get(), (int64_t)blockIdx.x, st, ranges, keys, vals, rec, P, stats);
 }
 
 // Persistent form: CTAs take tiles from a work counter until the table's total_tiles are done, so
@@ -208,20 +253,21 @@ __global__ void __launch_bounds__(kFwdThreads, 8) k_render_fwd(const __grid_cons
 template <class VS>
 __global__ void __launch_bounds__(kFwdThreads, 8) k_render_fwd_persistent(const __grid_constant__ VS vs,
                                                                     const uint2* __restrict__ ranges,
+                                                                    const uint32_t* __restrict__ keys,
                                                                     const uint32_t* __restrict__ vals,
                                                                     const Rec* __restrict__ rec, const Params P,
                                                                     unsigned int* __restrict__ tile_counter) {
-  __shared__ RecPair batch[kFwdBatch];
+  __shared__ FwdStage st;
   __shared__ unsigned int s_tile;
   const auto& vt = vs.get();
   const long long total = vt.total_tiles;
   for (;;) {
-    __syncthreads();  // previous tile's readers of s_tile and batch are done
+    __syncthreads();  // previous tile's readers of s_tile and the staged list are done
     if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
     __syncthreads();
     const unsigned int tile = s_tile;
     if ((long long)tile >= total) break;
-    render_tile_fwd<VS::kMax, false>(vt, (int64_t)tile, batch, ranges, vals, rec, P, nullptr);
+    render_tile_fwd<VS::kMax, false>(vt, (int64_t)tile, st, ranges, keys, vals, rec, P, nullptr);
   }
 }
 
@@ -283,16 +329,19 @@ __device__ __forceinline__ int reduce10_slot(unsigned lane) {
 // (about 1 ulp); they only scale gradients, never decide a branch.
 template <class VS>
 __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__ VS vs, const uint2* __restrict__ ranges,
+                                                         const uint32_t* __restrict__ keys,
                                                          const uint32_t* __restrict__ vals, const Rec* __restrict__ rec,
                                                          const Params P, float4* __restrict__ g2d) {
-  __shared__ RecPairB batch[kBatch];
-  __shared__ uint32_t ids[kBatch];
+  __shared__ Stage<RecPairB, kBatch> st;
   __shared__ uint32_t s_max_last;
   const auto& vt = vs.get();
   const int64_t tile = blockIdx.x;
   const ViewDesc& vd = vt.v[view_of_tile(vt, tile)];
-  const WarpBlock wb = warp_block((int)(tile - vd.tile_base), vd.tiles_x);
-  const uint2 rg = ranges[tile];
+  const int lt = (int)(tile - vd.tile_base);
+  const int tx = lt % vd.tiles_x, ty = lt / vd.tiles_x;
+  const WarpBlock wb = warp_block(lt, vd.tiles_x);
+  const uint2 rg = ranges[vd.seg_base + ty * vd.segs_x + (tx >> P.seg_log2)];
+  const uint32_t to = (uint32_t)tx & ((1u << P.seg_log2) - 1u);
   const int64_t plane = (int64_t)vd.W * vd.H;
 
   float Tk[2], gc[3][2];
@@ -337,31 +386,28 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
 
   for (uint32_t end = rg.x + max_last; end > rg.x;) {
     const uint32_t start = (end - rg.x > (uint32_t)kBatch) ? end - kBatch : rg.x;
-    __syncthreads();
+    __syncthreads();  // the previous round's readers of the staged list are done
     const uint32_t idx = start + threadIdx.x;
-    if (idx < end) {
-      const uint32_t g = vals[idx];
+    const bool keep = idx < end && seg_key_covers(keys[idx], to, P);
+    const int cnt = stage_kept<kBatch>(st, keep, idx, rg.x, vals, [&](RecPairB& d, uint32_t g) {
       const Rec r = rec[g];
-      ids[threadIdx.x] = g;
-      RecPairB& d = batch[threadIdx.x];
       stage_pair(d, r);
       d.n0 = make_float4(-2.0f * r.b.x, -2.0f * r.b.x, -2.0f * r.b.y, -2.0f * r.b.y);
       d.n1 = make_float4(-2.0f * r.b.z, -2.0f * r.b.z, 0.f, 0.f);
-    }
-    __syncthreads();
-    for (int j = (int)(end - start) - 1; j >= 0; --j) {
-      const uint32_t kpos = start - rg.x + (uint32_t)j + 1u;  // 1-based position in the tile's list
-      if (kpos > wlast) continue;                             // beyond every pixel of this warp
+    });
+    for (int j = cnt - 1; j >= 0; --j) {
+      const uint32_t kpos = st.pos[j];  // 1-based position in the segment's list
+      if (kpos > wlast) continue;       // beyond every pixel of this warp
       PairEval f;
-      eval_pair(batch[j], PX, PY, f);
+      eval_pair(st.rec[j], PX, PY, f);
       const bool cl0 = f.a.x > P.alpha_max, cl1 = f.a.y > P.alpha_max;
       const float al0 = cl0 ? P.alpha_max : f.a.x, al1 = cl1 ? P.alpha_max : f.a.y;
       const bool act0 = kpos <= last[0] && al0 >= P.alpha_min;
       const bool act1 = kpos <= last[1] && al1 >= P.alpha_min;
       if (!__any_sync(0xffffffffu, act0 || act1)) continue;
       // gradient terms of both pixels (zero for an inactive one, whose T and S stay as they are)
-      const float4 n0 = batch[j].n0, n1 = batch[j].n1, k0 = batch[j].k0, k1 = batch[j].k1;
-      const float4 e = batch[j].e, c1 = batch[j].c1;
+      const float4 n0 = st.rec[j].n0, n1 = st.rec[j].n1, k0 = st.rec[j].k0, k1 = st.rec[j].k1;
+      const float4 e = st.rec[j].e, c1 = st.rec[j].c1;
       const float2 dx = f.dx, dy = f.dy, p = f.p, lq = f.lq, G = f.G;
       const float q0 = f.q0, q1 = f.q1, hb = e.z;
       const float2 alpha = make_float2(act0 ? al0 : 0.f, act1 ? al1 : 0.f);
@@ -409,7 +455,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
       float v[10] = {gmx.x + gmx.y, gmy.x + gmy.y, ga.x + ga.y,   gb.x + gb.y,   gcc.x + gcc.y,
                      gk.x + gk.y,   gbeta.x + gbeta.y, gr.x + gr.y, gg.x + gg.y, gbl.x + gbl.y};
       const float sum = warp_reduce_scatter10(v);
-      if (adder) atomicAdd(reinterpret_cast<float*>(g2d + 3 * (int64_t)ids[j]) + slot, sum);
+      if (adder) atomicAdd(reinterpret_cast<float*>(g2d + 3 * (int64_t)st.id[j]) + slot, sum);
     }
     end = start;
   }
@@ -418,37 +464,39 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
 }  // namespace
 
 template <class VS>
-void launch_render_fwd(const VS& vs, int64_t total_tiles, const uint2* ranges, const uint32_t* vals, const Rec* rec,
-                       const Params& P, cudaStream_t s, unsigned long long* stats, unsigned int* tile_counter,
-                       int num_sms) {
+void launch_render_fwd(const VS& vs, int64_t total_tiles, const uint2* ranges, const uint32_t* keys,
+                       const uint32_t* vals, const Rec* rec, const Params& P, cudaStream_t s,
+                       unsigned long long* stats, unsigned int* tile_counter, int num_sms) {
   if (total_tiles <= 0) return;
   if (tile_counter) {
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_fwd_persistent<VS>, kFwdThreads, 0);
     const int64_t grid = (int64_t)num_sms * (per_sm > 0 ? per_sm : 1);
     k_render_fwd_persistent<VS><<<(unsigned)(grid < total_tiles ? grid : total_tiles), kFwdThreads, 0, s>>>(
-        vs, ranges, vals, rec, P, tile_counter);
+        vs, ranges, keys, vals, rec, P, tile_counter);
   } else if (stats) {
-    k_render_fwd<VS, true><<<(unsigned)total_tiles, kFwdThreads, 0, s>>>(vs, ranges, vals, rec, P, stats);
+    k_render_fwd<VS, true><<<(unsigned)total_tiles, kFwdThreads, 0, s>>>(vs, ranges, keys, vals, rec, P, stats);
   } else {
-    k_render_fwd<VS, false><<<(unsigned)total_tiles, kFwdThreads, 0, s>>>(vs, ranges, vals, rec, P, nullptr);
+    k_render_fwd<VS, false><<<(unsigned)total_tiles, kFwdThreads, 0, s>>>(vs, ranges, keys, vals, rec, P, nullptr);
   }
   count_launches(1);
 }
 
 template <class VS>
-void launch_render_bwd(const VS& vs, int64_t total_tiles, const uint2* ranges, const uint32_t* vals, const Rec* rec,
-                       const Params& P, float4* g2d, cudaStream_t s) {
+void launch_render_bwd(const VS& vs, int64_t total_tiles, const uint2* ranges, const uint32_t* keys,
+                       const uint32_t* vals, const Rec* rec, const Params& P, float4* g2d, cudaStream_t s) {
   if (total_tiles <= 0) return;
-  k_render_bwd<VS><<<(unsigned)total_tiles, kThreads, 0, s>>>(vs, ranges, vals, rec, P, g2d);
+  k_render_bwd<VS><<<(unsigned)total_tiles, kThreads, 0, s>>>(vs, ranges, keys, vals, rec, P, g2d);
   count_launches(1);
 }
 
-template void launch_render_fwd<FrameViews>(const FrameViews&, int64_t, const uint2*, const uint32_t*, const Rec*,
-                                            const Params&, cudaStream_t, unsigned long long*, unsigned int*, int);
-template void launch_render_fwd<BatchViews>(const BatchViews&, int64_t, const uint2*, const uint32_t*, const Rec*,
-                                            const Params&, cudaStream_t, unsigned long long*, unsigned int*, int);
-template void launch_render_bwd<FrameViews>(const FrameViews&, int64_t, const uint2*, const uint32_t*, const Rec*,
-                                            const Params&, float4*, cudaStream_t);
+template void launch_render_fwd<FrameViews>(const FrameViews&, int64_t, const uint2*, const uint32_t*, const uint32_t*,
+                                            const Rec*, const Params&, cudaStream_t, unsigned long long*, unsigned int*,
+                                            int);
+template void launch_render_fwd<BatchViews>(const BatchViews&, int64_t, const uint2*, const uint32_t*, const uint32_t*,
+                                            const Rec*, const Params&, cudaStream_t, unsigned long long*, unsigned int*,
+                                            int);
+template void launch_render_bwd<FrameViews>(const FrameViews&, int64_t, const uint2*, const uint32_t*, const uint32_t*,
+                                            const Rec*, const Params&, float4*, cudaStream_t);
 
 }  // namespace ges

@@ -133,7 +133,10 @@ ges_status ws_alloc(ges_server* S, Workspace& w, int64_t P_cap, int64_t T_cap, i
   w.T_cap = T_cap;
   w.X_cap = X_cap;
   w.K_cap = K_cap;
-  const int tile_bits = bits_for(T_cap);
+  // segment ids of a batch stay below T_cap (a view has at most as many segments as tiles)
+  ges_status sst = set_segment_bits(S->P, T_cap);
+  if (sst != GES_OK) return sst;
+  const int tile_bits = S->P.seg_bits;
   const int64_t h1 = radix_hist_entries(P_cap, 32), h2 = radix_hist_entries(K_cap, tile_bits);
   w.hist_cap = h1 > h2 ? h1 : h2;
   A((void**)&w.d_vt, sizeof(Table));
@@ -183,18 +186,23 @@ ges_status ws_alloc(ges_server* S, Workspace& w, int64_t P_cap, int64_t T_cap, i
   launch_preprocess<BatchViews>(vs, P_cap, S->P, w.depth_key, w.dk[0], w.pv[0], w.rect, w.rec, w.ext, w.tprim, S->num_sms,
                                 s);
   int cur = 0;
-  radix_sort_pairs(w.dk, w.pv, cur, 0, n_dev, P_cap, 32, w.hist, w.hist_cap, w.scan, s);
+  bool fits = radix_sort_pairs(w.dk, w.pv, cur, 0, n_dev, P_cap, 32, w.hist, w.hist_cap, w.scan, s);
   launch_gather_touched(w.pv[cur], w.tprim, P_cap, w.touched, s, n_dev);
   scan_exclusive<uint32_t, unsigned long long>(w.touched, w.offsets, P_cap, dK, w.scan, s, n_dev);
-  launch_keygen<BatchViews>(vs, w.offsets, w.touched, dK, P_cap, w.pv[cur], w.rect, w.ext, w.rec, S->P.margin_abs, K_cap,
+  launch_keygen<BatchViews>(vs, w.offsets, w.touched, dK, P_cap, w.pv[cur], w.rect, w.ext, w.rec, S->P, K_cap,
                             w.tk[0], w.tv[0], flags, s, n_dev);
   int tcur = 0;
-  radix_sort_pairs(w.tk, w.tv, tcur, 0, dK, K_cap, tile_bits, w.hist, w.hist_cap, w.scan, s);
-  launch_ranges(w.tk[tcur], dK, K_cap, w.ranges, S->num_sms, s);
-  launch_render_fwd<BatchViews>(vs, T_cap, w.ranges, w.tv[tcur], w.rec, S->P, s, nullptr, counter, S->num_sms);
+  fits = radix_sort_pairs(w.tk, w.tv, tcur, 0, dK, K_cap, tile_bits, w.hist, w.hist_cap, w.scan, s) && fits;
+  launch_ranges(w.tk[tcur], dK, K_cap, (uint32_t)((1ull << tile_bits) - 1), w.ranges, S->num_sms, s);
+  launch_render_fwd<BatchViews>(vs, T_cap, w.ranges, w.tk[tcur], w.tv[tcur], w.rec, S->P, s, nullptr, counter,
+                                S->num_sms);
   cudaGraph_t g = nullptr;
   e = cudaStreamEndCapture(s, &g);
   if (e != cudaSuccess) return cuda_fail(e, "end capture");
+  if (!fits) {
+    cudaGraphDestroy(g);
+    return fail(GES_ERR_CUDA, "internal: a radix histogram exceeds its buffer");
+  }
   e = cudaGraphInstantiate(&w.graph, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
@@ -257,12 +265,13 @@ ges_status setup_workspaces(ges_server* S) {
 ges_status ws_launch(ges_server* S, Workspace& w) {
   Table& t = *w.h_vt;
   std::memset(&t, 0, sizeof(Table));
-  int64_t prim = 0, tile = 0, pix = 0;
+  int64_t prim = 0, tile = 0, seg = 0, pix = 0;
   w.pix_off.clear();
   for (size_t i = 0; i < w.reqs.size(); ++i) {
     Request* r = w.reqs[i];
     const ResidentScene& sc = S->scenes[r->scene];
-    fill_view(t.v[i], r->cam, sc.dev, prim, (int32_t)tile);
+    fill_view(t.v[i], r->cam, sc.dev, prim, (int32_t)tile, (int32_t)seg, S->P.seg_log2);
+    seg += (int64_t)t.v[i].segs_x * t.v[i].tiles_y;
     t.v[i].img = w.img + 3 * pix;
     t.v[i].final_T = w.T + pix;
     t.v[i].n_contrib = w.nc + pix;
@@ -274,6 +283,7 @@ ges_status ws_launch(ges_server* S, Workspace& w) {
   t.n = (int32_t)w.reqs.size();
   t.total_prims = (unsigned long long)prim;
   t.total_tiles = tile;
+  t.total_segs = seg;
   cudaError_t e;
   if ((e = cudaGraphLaunch(w.graph, w.stream)) != cudaSuccess) return cuda_fail(e, "graph launch");
   if ((e = cudaMemcpyAsync(w.h_img, w.img, sizeof(float) * 3 * pix, cudaMemcpyDeviceToHost, w.stream)) != cudaSuccess)

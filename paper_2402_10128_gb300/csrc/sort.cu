@@ -285,22 +285,23 @@ __global__ void k_gather_touched(const uint32_t* __restrict__ sorted_vals, const
 }
 
 // ---------------------------------------------------------------- K3 keygen
-// Primitive j (depth order) owns entries [offsets[j], offsets[j] + touched[j]), row span by row
-// span.  A warp takes 32 consecutive primitives, whose entries are one contiguous range: it walks
-// their (primitive, row) slots 32 at a time (one row span per lane), prefix-sums the span widths,
-// and writes the chunk's entries with consecutive lanes on consecutive entries.  Writes stay below
-// K whatever the inputs.
+// Primitive j (depth order) owns entries [offsets[j], offsets[j] + touched[j]): per tile row of
+// its bounding box, one entry per segment that the row's span meets, keyed seg_key(segment,
+// span columns inside the segment).  A warp takes 32 consecutive primitives, whose entries are
+// one contiguous range: it walks their (primitive, row) slots 32 at a time (one row span per
+// lane), prefix-sums the entry counts, and writes with consecutive lanes on consecutive entries.
+// Writes stay below K whatever the inputs.
 constexpr int kKeygenThreads = 256;
 
 template <class VS>
-__global__ void __launch_bounds__(kKeygenThreads) k_keygen(const __grid_constant__ VS vs,
+__global__ void __launch_bounds__(kKeygenThreads, 4) k_keygen(const __grid_constant__ VS vs,
                                                            const unsigned long long* __restrict__ offsets,
                                                            const unsigned long long* __restrict__ K_dev, int64_t n_cap,
                                                            const unsigned long long* __restrict__ n_dev,
                                                            const uint32_t* __restrict__ sorted_vals,
                                                            const uint32_t* __restrict__ touched,
                                                            const ushort4* __restrict__ rect, const float4* __restrict__ ext,
-                                                           const Rec* __restrict__ rec, float mabs, int64_t cap,
+                                                           const Rec* __restrict__ rec, const Params P, int64_t cap,
                                                            uint32_t* __restrict__ tile_keys,
                                                            uint32_t* __restrict__ tile_vals, uint32_t* __restrict__ flags) {
   const auto& vt = vs.get();
@@ -311,23 +312,24 @@ __global__ void __launch_bounds__(kKeygenThreads) k_keygen(const __grid_constant
   }
   const int64_t n = scan_count(n_cap, n_dev);
   const unsigned lane = lane_id();
+  const int L = P.seg_log2;
   const int64_t wpb = kKeygenThreads / 32;
   const int64_t stride = (int64_t)gridDim.x * wpb * 32;
   for (int64_t base = ((int64_t)blockIdx.x * wpb + (threadIdx.x >> 5)) * 32; base < n; base += stride) {
     const int64_t j = base + lane;
     const uint32_t t = j < n ? touched[j] : 0u;
     RowSpan rs{};
-    unsigned g = 0, h = 0, y0 = 0, tb = 0, tw = 0;
+    unsigned g = 0, h = 0, y0 = 0, sb = 0, sx = 0;
     if (t) {
       g = sorted_vals[j];
       const ushort4 r = rect[g];
       const float4 ra = rec[g].a;
-      rs = make_row_span(ext[g], ra.x, ra.y, mabs, r);
+      rs = make_row_span(ext[g], ra.x, ra.y, P.margin_abs, r);
       const ViewDesc& vd = vt.v[view_of_prim(vt, (int64_t)g)];
       h = (unsigned)(r.w - r.y);
       y0 = r.y;
-      tb = (unsigned)vd.tile_base;
-      tw = (unsigned)vd.tiles_x;
+      sb = (unsigned)vd.seg_base;
+      sx = (unsigned)vd.segs_x;
     }
     unsigned R;
     const unsigned hex = warp_excl_scan(h, R);
@@ -341,15 +343,16 @@ __global__ void __launch_bounds__(kKeygenThreads) k_keygen(const __grid_constant
       const unsigned qy0 = __shfl_sync(0xffffffffu, y0, ow);
       const unsigned qhex = __shfl_sync(0xffffffffu, hex, ow);
       const unsigned qg = __shfl_sync(0xffffffffu, g, ow);
-      const unsigned qtb = __shfl_sync(0xffffffffu, tb, ow);
-      const unsigned qtw = __shfl_sync(0xffffffffu, tw, ow);
-      unsigned w = 0, kb = 0;
+      const unsigned qsb = __shfl_sync(0xffffffffu, sb, ow);
+      const unsigned qsx = __shfl_sync(0xffffffffu, sx, ow);
+      unsigned w = 0, kb = 0, tt = 0;
       if (s < R) {
         const int ty = (int)(qy0 + (s - qhex));
         int t0, t1;
         if (tile_row_span(q, ty, t0, t1)) {
-          w = (unsigned)(t1 - t0 + 1);
-          kb = qtb + (unsigned)ty * qtw + (unsigned)t0;
+          w = (unsigned)((t1 >> L) - (t0 >> L) + 1);
+          kb = qsb + (unsigned)ty * qsx + (unsigned)(t0 >> L);  // the span's first segment
+          tt = (unsigned)t0 | ((unsigned)t1 << 16);
         }
       }
       unsigned W;
@@ -360,9 +363,16 @@ __global__ void __launch_bounds__(kKeygenThreads) k_keygen(const __grid_constant
         const unsigned rkb = __shfl_sync(0xffffffffu, kb, rl);
         const unsigned rwex = __shfl_sync(0xffffffffu, wex, rl);
         const unsigned rg = __shfl_sync(0xffffffffu, qg, rl);
+        const unsigned rtt = __shfl_sync(0xffffffffu, tt, rl);
         const unsigned long long e = eb + x;
         if (x < W && e < K) {
-          tile_keys[e] = rkb + (x - rwex);
+          const unsigned i = x - rwex;                     // segment of the span, counted from its first
+          const unsigned t0 = rtt & 0xffffu, t1 = rtt >> 16;
+          const unsigned lo = ((t0 >> L) + i) << L;        // first tile of that segment
+          const unsigned off0 = (t0 > lo ? t0 : lo) - lo;
+          const unsigned hi = lo + (1u << L) - 1u;
+          const unsigned off1 = (t1 < hi ? t1 : hi) - lo;
+          tile_keys[e] = seg_key(rkb + i, off0, off1, P);
           tile_vals[e] = rg;
         }
       }
@@ -372,32 +382,33 @@ __global__ void __launch_bounds__(kKeygenThreads) k_keygen(const __grid_constant
 }
 
 // ---------------------------------------------------------------- K5 ranges
-// Four entries per thread (one 16-byte load); a tile starts where an entry differs from its
-// predecessor and ends where it differs from its successor.  Neighbours across threads come from
-// the adjacent lanes; the warp's end lanes load theirs.
+// Four entries per thread (one 16-byte load); a segment starts where an entry's segment id (the
+// key's low bits, seg_mask) differs from its predecessor's and ends where it differs from its
+// successor's.  Neighbours across threads come from the adjacent lanes; the warp's end lanes load
+// theirs.
 __global__ void k_ranges(const uint32_t* __restrict__ tile_keys, const unsigned long long* __restrict__ K_dev, int64_t cap,
-                         uint2* __restrict__ ranges) {
+                         uint32_t seg_mask, uint2* __restrict__ ranges) {
   const int64_t K = (int64_t)*K_dev;
   if (K > cap) return;
   const unsigned lane = lane_id();
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  constexpr uint32_t kNone = 0xffffffffu;  // never a tile id
+  constexpr uint32_t kNone = 0xffffffffu;  // never a segment id
   const int64_t nq = (K + 3) / 4;
   for (int64_t base = wid * 32; base < nq; base += nwarps * 32) {
     const int64_t e = 4 * (base + lane);
     uint32_t t[4];
     if (e + 3 < K) {
       const uint4 v = *reinterpret_cast<const uint4*>(tile_keys + e);
-      t[0] = v.x; t[1] = v.y; t[2] = v.z; t[3] = v.w;
+      t[0] = v.x & seg_mask; t[1] = v.y & seg_mask; t[2] = v.z & seg_mask; t[3] = v.w & seg_mask;
     } else {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) t[i] = e + i < K ? tile_keys[e + i] : kNone;
+      for (int i = 0; i < 4; ++i) t[i] = e + i < K ? (tile_keys[e + i] & seg_mask) : kNone;
     }
     uint32_t prev = __shfl_up_sync(0xffffffffu, t[3], 1);
     uint32_t next = __shfl_down_sync(0xffffffffu, t[0], 1);
-    if (lane == 0) prev = e > 0 && e - 1 < K ? tile_keys[e - 1] : kNone;
-    if (lane == 31) next = e + 4 < K ? tile_keys[e + 4] : kNone;
+    if (lane == 0) prev = e > 0 && e - 1 < K ? (tile_keys[e - 1] & seg_mask) : kNone;
+    if (lane == 31) next = e + 4 < K ? (tile_keys[e + 4] & seg_mask) : kNone;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       if (e + i >= K) break;
@@ -407,15 +418,6 @@ __global__ void k_ranges(const uint32_t* __restrict__ tile_keys, const unsigned 
       if (q != t[i]) ranges[t[i]].y = (uint32_t)(e + i + 1);
     }
   }
-}
-
-__global__ void k_make_keys(const uint32_t* __restrict__ tile_keys, const uint32_t* __restrict__ tile_vals,
-                            const uint32_t* __restrict__ depth_key, const unsigned long long* __restrict__ K_dev,
-                            int64_t cap, unsigned long long* __restrict__ keys64) {
-  const int64_t K = (int64_t)*K_dev;
-  if (K > cap) return;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < K; e += (int64_t)gridDim.x * blockDim.x)
-    keys64[e] = ((unsigned long long)tile_keys[e] << 32) | depth_key[tile_vals[e]];
 }
 
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -494,24 +496,24 @@ void launch_gather_touched(const uint32_t* sorted_vals, const uint32_t* tprim, i
   count_launches(1);
 }
 
-int64_t radix_hist_entries(int64_t n_cap, int total_bits) {
-  int passes = (total_bits + 7) / 8;
-  if (passes < 1) passes = 1;
-  int bits = (total_bits + passes - 1) / passes;
+// histogram entries that a sort of n_cap keys on up to max_bits bits may need in one pass: the
+// digit of a pass is at most 8 bits wide (and at most max_bits)
+int64_t radix_hist_entries(int64_t n_cap, int max_bits) {
+  const int bits = max_bits < 1 ? 1 : (max_bits > 8 ? 8 : max_bits);
   return ((int64_t)1 << bits) * cdiv(n_cap > 0 ? n_cap : 1, kChunk);
 }
 
-void radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_host, const unsigned long long* n_dev,
+bool radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_host, const unsigned long long* n_dev,
                       int64_t n_cap, int total_bits, uint32_t* hist, int64_t hist_cap, ScanScratch& sc, cudaStream_t s) {
-  if (n_cap <= 0 || total_bits <= 0) return;
+  if (n_cap <= 0 || total_bits <= 0) return true;
   const int passes = (total_bits + 7) / 8;
   const int bits_per = (total_bits + passes - 1) / passes;
   const int64_t nchunks = cdiv(n_cap, kChunk);
+  if (((int64_t)1 << bits_per) * nchunks > hist_cap) return false;  // the histogram would not fit
   for (int p = 0; p < passes; ++p) {
     const int shift = p * bits_per;
     const int bits = (total_bits - shift) < bits_per ? (total_bits - shift) : bits_per;
     const int64_t entries = ((int64_t)1 << bits) * nchunks;  // capacity of the matrix
-    (void)hist_cap;
     unsigned long long* n_entries = reinterpret_cast<unsigned long long*>(sc.buf);
     k_radix_hist<<<grid_cap(nchunks, 8), kThreads, 0, s>>>(keys[cur], n_host, n_dev, n_cap, shift, bits, hist, n_entries);
     scan_exclusive<uint32_t, uint32_t>(hist, hist, entries, (uint32_t*)nullptr, sc, s, n_entries);
@@ -520,45 +522,37 @@ void radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_
     count_launches(2);
     cur ^= 1;
   }
+  return true;
 }
 
 template <class VS>
 void launch_keygen(const VS& vs, const unsigned long long* offsets, const uint32_t* touched,
                    const unsigned long long* K_dev, int64_t n, const uint32_t* sorted_vals, const ushort4* rect,
-                   const float4* ext, const Rec* rec, float margin_abs, int64_t cap,
+                   const float4* ext, const Rec* rec, const Params& P, int64_t cap,
                    uint32_t* tile_keys, uint32_t* tile_vals, uint32_t* flags, cudaStream_t s,
                    const unsigned long long* n_dev) {
   if (n <= 0 || cap <= 0) return;
   k_keygen<VS><<<grid_cap(cdiv(n, kKeygenThreads), 8), kKeygenThreads, 0, s>>>(
-      vs, offsets, K_dev, n, n_dev, sorted_vals, touched, rect, ext, rec, margin_abs, cap, tile_keys, tile_vals, flags);
+      vs, offsets, K_dev, n, n_dev, sorted_vals, touched, rect, ext, rec, P, cap, tile_keys, tile_vals, flags);
   count_launches(1);
 }
 
-void launch_ranges(const uint32_t* tile_keys, const unsigned long long* K_dev, int64_t cap, uint2* ranges, int num_sms,
-                   cudaStream_t s) {
+void launch_ranges(const uint32_t* tile_keys, const unsigned long long* K_dev, int64_t cap, uint32_t seg_mask,
+                   uint2* ranges, int num_sms, cudaStream_t s) {
   if (cap <= 0) return;
   int64_t blocks = cdiv(cdiv(cap, 4), 256);
   if (blocks > (int64_t)num_sms * 8) blocks = (int64_t)num_sms * 8;
-  k_ranges<<<(unsigned)blocks, 256, 0, s>>>(tile_keys, K_dev, cap, ranges);
-  count_launches(1);
-}
-
-void launch_make_keys(const uint32_t* tile_keys, const uint32_t* tile_vals, const uint32_t* depth_key,
-                      const unsigned long long* K_dev, int64_t cap, unsigned long long* keys64, cudaStream_t s) {
-  if (cap <= 0) return;
-  int64_t blocks = cdiv(cap, 256);
-  if (blocks > 4096) blocks = 4096;
-  k_make_keys<<<(unsigned)blocks, 256, 0, s>>>(tile_keys, tile_vals, depth_key, K_dev, cap, keys64);
+  k_ranges<<<(unsigned)blocks, 256, 0, s>>>(tile_keys, K_dev, cap, seg_mask, ranges);
   count_launches(1);
 }
 
 template void launch_keygen<FrameViews>(const FrameViews&, const unsigned long long*, const uint32_t*,
                                         const unsigned long long*, int64_t, const uint32_t*, const ushort4*,
-                                        const float4*, const Rec*, float, int64_t, uint32_t*, uint32_t*, uint32_t*,
-                                        cudaStream_t, const unsigned long long*);
+                                        const float4*, const Rec*, const Params&, int64_t, uint32_t*, uint32_t*,
+                                        uint32_t*, cudaStream_t, const unsigned long long*);
 template void launch_keygen<BatchViews>(const BatchViews&, const unsigned long long*, const uint32_t*,
                                         const unsigned long long*, int64_t, const uint32_t*, const ushort4*,
-                                        const float4*, const Rec*, float, int64_t, uint32_t*, uint32_t*, uint32_t*,
-                                        cudaStream_t, const unsigned long long*);
+                                        const float4*, const Rec*, const Params&, int64_t, uint32_t*, uint32_t*,
+                                        uint32_t*, cudaStream_t, const unsigned long long*);
 
 }  // namespace ges

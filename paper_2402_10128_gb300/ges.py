@@ -59,7 +59,7 @@ class ges_params(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_float), ("falloff", ctypes.c_int32), ("dilation", ctypes.c_float),
                 ("alpha_max", ctypes.c_float), ("alpha_min", ctypes.c_float), ("t_min", ctypes.c_float),
                 ("extent_margin_rel", ctypes.c_float), ("extent_margin_abs", ctypes.c_float),
-                ("clamp_fov", ctypes.c_float)]
+                ("clamp_fov", ctypes.c_float), ("segment_tiles", ctypes.c_int32)]
 
 
 class ges_scene(ctypes.Structure):
@@ -242,15 +242,22 @@ def ges_frame_status(frame: int, stream=None):
 
 
 def ges_frame_keys(frame: int, stream=None):
-    """Sorted 64-bit keys and values of the last ges_bin_sort (host numpy arrays)."""
-    st, K = ges_frame_status(frame, stream)
-    _check(st)
-    keys = np.empty(K, np.uint64)
-    vals = np.empty(K, np.uint32)
+    """Per-tile sorted 64-bit keys (tile << 32 | depth bits) and values (primitive index) of the
+    last ges_bin_sort, expanded from its segment lists (host numpy arrays)."""
+    n = ges_frame_tile_entries(frame, stream)
+    keys = np.empty(n, np.uint64)
+    vals = np.empty(n, np.uint32)
     k = ctypes.c_int64(0)
-    _check(_lib.ges_frame_keys(frame, _stream(stream), _addr(keys) if K else None, _addr(vals) if K else None,
-                               K, ctypes.byref(k)))
+    _check(_lib.ges_frame_keys(frame, _stream(stream), _addr(keys) if n else None, _addr(vals) if n else None,
+                               n, ctypes.byref(k)))
     return keys, vals
+
+
+def ges_frame_tile_entries(frame: int, stream=None) -> int:
+    """Number of (tile, primitive) entries of the last ges_bin_sort (its segment lists expanded)."""
+    k = ctypes.c_int64(0)
+    _check(_lib.ges_frame_keys(frame, _stream(stream), None, None, 0, ctypes.byref(k)))
+    return int(k.value)
 
 
 def ges_frame_inspect(frame: int, n: int, n_tiles: int, stream=None):

@@ -21,6 +21,7 @@ def gpu_run(scene, cam, params=None, backward_grad=None, key_capacity=0, keys=Tr
     out.update(img=img.cpu().numpy(), T=T.cpu().numpy(), nc=nc.cpu().numpy())
     if keys:
         out["keys"], out["vals"] = fr.keys()
+        out["K_tiles"] = int(out["keys"].size)
     out["inspect"] = fr.inspect()
     if backward_grad is not None:
         g = torch.as_tensor(np.ascontiguousarray(backward_grad, np.float32), device="cuda")

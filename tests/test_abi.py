@@ -50,7 +50,7 @@ def test_params_default_matches_paper_constants(lib):
 def test_struct_layouts_match_header(lib):
     from paper_2402_10128_gb300 import ges
     assert ctypes.sizeof(ges.ges_camera) == 4 * (2 + 4 + 16 + 3 + 1 + 3)
-    assert ctypes.sizeof(ges.ges_params) == 4 * 9
+    assert ctypes.sizeof(ges.ges_params) == 4 * 10
     assert ctypes.sizeof(ges.ges_scene) == 8 + 8 + 6 * 8
     assert ctypes.sizeof(ges.ges_grads) == 6 * 8
 

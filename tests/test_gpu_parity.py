@@ -76,7 +76,7 @@ def test_sorted_keys_and_ranges_bitexact(lib, case):
     sc, cam, p = CASES[case]
     got = gpu_run(sc, cam, p)
     kk, vv = oracle.sorted_keys(sc, cam, p)
-    assert got["K"] == kk.size
+    assert got["K_tiles"] == kk.size
     assert np.array_equal(got["keys"], kk)
     assert np.array_equal(got["vals"], vv)
     n_tiles = ((cam.width + 15) // 16) * ((cam.height + 15) // 16)
@@ -85,6 +85,25 @@ def test_sorted_keys_and_ranges_bitexact(lib, case):
     gr = got["inspect"]["ranges"]
     assert np.array_equal(gr[~empty], ref_ranges[~empty])
     assert np.all(gr[empty, 0] == gr[empty, 1])
+
+
+@pytest.mark.parametrize("segment_tiles", [1, 2, 16, 1024])
+@pytest.mark.parametrize("case", ["tiny", "ragged_lowbeta", "dense_batches"])
+def test_segment_width_changes_neither_lists_nor_images(lib, case, segment_tiles):
+    """The per-tile lists (expanded from the segment lists) are bit-exact against the oracle for
+    every segment width, and the images are identical to those of the default width."""
+    from gpu_helpers import gpu_run
+    sc, cam, p = CASES[case]
+    q = dict(p or {}, segment_tiles=segment_tiles)
+    got = gpu_run(sc, cam, q)
+    base = gpu_run(sc, cam, p, keys=False)
+    kk, vv = oracle.sorted_keys(sc, cam, p)
+    assert np.array_equal(got["keys"], kk) and np.array_equal(got["vals"], vv)
+    assert np.array_equal(got["img"], base["img"]) and np.array_equal(got["T"], base["T"])
+    if segment_tiles == 1:
+        assert got["K"] == kk.size  # one entry per (tile, primitive)
+    else:
+        assert got["K"] <= kk.size
 
 
 @pytest.mark.parametrize("case", list(CASES))

@@ -1,13 +1,19 @@
-"""The stress configuration's beta = 2 run at full size (6M cube primitives, SH3, 3840x2160).
+"""The stress configuration at full size (6M cube primitives, SH3, 3840x2160), in both forms.
 
-* beta = 2 is the Gaussian degenerate case: the GEF falloff and the paper's Gaussian-form
-  rasterizer must give bit-identical images and final T on the GPU (their extents may differ in
-  the last ulp, q* = exp2(log2(.)) against q* = (.), so a few tile lists may differ by an entry
-  that no pixel takes; list positions, and hence contributor counts, may shift there);
-* a random sample of pixels against the oracle's brute force over all 6M primitives;
-* the backward with an upstream gradient on a random sample of pixels only, against the oracle's
-  exact FP64 gradient over those pixels;
-* the tile ranges partition the duplicate list.
+beta = 2 (the Gaussian degenerate case, default segment width):
+* the GEF falloff and the paper's Gaussian-form rasterizer give bit-identical images and final T
+  (their extents may differ in the last ulp, q* = exp2(log2(.)) against q* = (.), so a few tile
+  lists may differ by an entry that no pixel takes);
+* the per-tile lists expanded from the segment lists hold exactly as many entries as the oracle's
+  key module lists (the sum of its per-primitive tile counts, 776M at this size).
+
+beta log-U[0.3,16] (kernels from very sharp to very wide; about 3.3e10 (tile, primitive) pairs,
+listed once per tile row: segment_tiles = 256):
+* the list holds at most one entry per (primitive, tile row), far fewer than the tile pairs.
+
+Both forms: a random sample of pixels against the oracle's brute force over all 6M primitives,
+and the backward with an upstream gradient on a random sample of pixels only, against the
+oracle's exact FP64 gradient over those pixels.
 """
 import numpy as np
 import pytest
@@ -23,32 +29,28 @@ GRAD_TOL = 1e-3
 NAMES = ["means", "scales", "quats", "betas", "opacities", "shs"]
 
 
-@pytest.fixture(scope="module")
-def run():
-    import __graft_entry__
-    __graft_entry__.build()
-    assert torch.cuda.is_available()
-    from paper_2402_10128_gb300 import render
-    sc, cam = scenes.stress_beta2_workload()
+def _render(sc, cam, modes, segment_tiles, grad_seed):
+    from paper_2402_10128_gb300 import ges, render
     t = render.scene_tensors(sc, "cuda")
     fr = render.Frame(sc.n, cam.width, cam.height, key_capacity=0)
     out = {"scene": sc, "cam": cam}
-    for mode in (0, 1):
-        img, T, nc = fr.forward(t, sc.sh_degree, cam, {"mode": mode})
+    for mode in modes:
+        img, T, nc = fr.forward(t, sc.sh_degree, cam, {"mode": mode, "segment_tiles": segment_tiles})
         st, K = fr.status()
         assert st == 0
         torch.cuda.synchronize()
-        out[mode] = dict(img=img.cpu().numpy(), T=T.cpu().numpy(), nc=nc.cpu().numpy(), K=K)
-        out[mode]["ranges"] = fr.inspect()["ranges"]
+        out[mode] = dict(img=img.cpu().numpy(), T=T.cpu().numpy(), K=K)
+        if segment_tiles < 256:
+            out[mode]["K_tiles"] = ges.ges_frame_tile_entries(fr.handle)
     # backward with an upstream gradient on a pixel sample (GEF mode)
-    rng = np.random.default_rng(21)
+    rng = np.random.default_rng(grad_seed)
     pix = rng.choice(cam.width * cam.height, 24, replace=False)
     flags = oracle.render(sc, cam, pixels=pix)["flags"]
     pix = pix[flags == 0]
     gs = rng.standard_normal((3, pix.size))
     g = np.zeros((3, cam.height * cam.width), np.float32)
     g[:, pix] = gs
-    img, T, nc = fr.forward(t, sc.sh_degree, cam)
+    img, T, nc = fr.forward(t, sc.sh_degree, cam, {"segment_tiles": segment_tiles})
     grads = fr.render_bwd(T, nc, torch.as_tensor(g.reshape(3, cam.height, cam.width), device="cuda"))
     torch.cuda.synchronize()
     out["grads"] = {k: v.cpu().double().numpy() for k, v in zip(NAMES, grads)}
@@ -57,16 +59,52 @@ def run():
     return out
 
 
-def test_gef_equals_gaussian_form_bitwise(run):
-    a, b = run[0], run[1]
-    assert a["K"] > 100_000_000 and abs(a["K"] - b["K"]) <= a["K"] * 1e-6
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+
+
+@pytest.fixture(scope="module")
+def beta2(lib):
+    sc, cam = scenes.stress_beta2_workload()
+    return _render(sc, cam, (0, 1), 16, 21)
+
+
+@pytest.fixture(scope="module")
+def full(lib):
+    sc, cam = scenes.stress_workload()
+    return _render(sc, cam, (0,), 256, 22)
+
+
+def test_beta2_gef_equals_gaussian_form_bitwise(beta2):
+    a, b = beta2[0], beta2[1]
+    assert a["K_tiles"] > 100_000_000 and abs(a["K_tiles"] - b["K_tiles"]) <= a["K_tiles"] * 1e-6
     assert np.array_equal(a["img"], b["img"])
     assert np.array_equal(a["T"], b["T"])
 
 
-def test_sampled_pixels_match_the_oracle(run):
+def test_beta2_tile_entry_count_matches_the_oracle(beta2):
+    sc, cam = beta2["scene"], beta2["cam"]
+    for mode in (0, 1):
+        k = oracle.keys(sc, cam, {"mode": mode})
+        assert beta2[mode]["K_tiles"] == int(k["touched"].astype(np.int64).sum())
+        assert beta2[mode]["K"] < beta2[mode]["K_tiles"]
+
+
+def test_full_lists_at_most_one_entry_per_primitive_row(full):
+    sc, cam = full["scene"], full["cam"]
+    k = oracle.keys(sc, cam)
+    K_tiles = int(k["touched"].astype(np.int64).sum())
+    rows = (k["rect"][:, 3] - k["rect"][:, 1]).astype(np.int64)
+    assert K_tiles > 10_000_000_000          # the per-tile form would not fit on the device
+    assert int((k["touched"] > 0).sum()) <= full[0]["K"] <= int(rows.sum())
+
+
+def _sampled_pixels(run, seed):
     sc, cam = run["scene"], run["cam"]
-    rng = np.random.default_rng(20)
+    rng = np.random.default_rng(seed)
     pix = rng.choice(cam.width * cam.height, 32, replace=False)
     ref = oracle.render(sc, cam, pixels=pix)
     ok = ref["flags"] == 0
@@ -76,15 +114,7 @@ def test_sampled_pixels_match_the_oracle(run):
     assert np.abs(run[0]["T"].reshape(-1)[pix] - ref["T"])[ok].max() <= 1e-5
 
 
-def test_ranges_partition_the_list(run):
-    r = run[1]["ranges"].astype(np.int64)
-    nonempty = r[:, 1] > r[:, 0]
-    s = r[nonempty]
-    assert s[0, 0] == 0 and s[-1, 1] == run[1]["K"]
-    assert np.all(s[1:, 0] == s[:-1, 1])
-
-
-def test_sparse_gradient_matches_the_oracle(run):
+def _sparse_gradient(run):
     sc, cam = run["scene"], run["cam"]
     ref = oracle.backward(sc, cam, run["grad_up"], pixels=run["grad_pix"])
     for k in NAMES:
@@ -92,3 +122,19 @@ def test_sparse_gradient_matches_the_oracle(run):
         b = ref[k].reshape(-1)
         err = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
         assert err <= GRAD_TOL, (k, err)
+
+
+def test_beta2_sampled_pixels_match_the_oracle(beta2):
+    _sampled_pixels(beta2, 20)
+
+
+def test_beta2_sparse_gradient_matches_the_oracle(beta2):
+    _sparse_gradient(beta2)
+
+
+def test_full_sampled_pixels_match_the_oracle(full):
+    _sampled_pixels(full, 23)
+
+
+def test_full_sparse_gradient_matches_the_oracle(full):
+    _sparse_gradient(full)
