@@ -544,7 +544,7 @@ ges_status ges_bin_sort(ges_frame* f, void* stream) {
   }
   int tcur = 0;
   {
-    TraceScope tr(f->ctx, "tile_sort", s);
+    TraceScope tr(f->ctx, "list_sort", s);
     if (!radix_sort_pairs(f->tk, f->tv, tcur, 0, f->d_K, f->key_cap, f->P.seg_bits, f->hist, f->hist_cap, f->scan, s))
       return fail(GES_ERR_CUDA, "internal: list-sort histogram exceeds its buffer");
   }
