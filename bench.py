@@ -119,6 +119,28 @@ def _traffic(kernel):
         return None
 
 
+def replica_cameras(cams, rank):
+    """Replicas only: rank r renders the camera sequence rotated by r, so that ranks start on
+    different views and together cover the orbit."""
+    k = rank % len(cams)
+    return cams[k:] + cams[:k]
+
+
+def max_over_ranks(ms, dist, dev):
+    """The slowest rank's time (every rank gets it); ms unchanged without a process group."""
+    if dist is None:
+        return ms
+    import torch
+    x = torch.tensor([float(ms)], device=dev)
+    dist.all_reduce(x, op=dist.ReduceOp.MAX)
+    return float(x.item())
+
+
+def aggregate_mpix_s(ws, pixels_per_step, steps, ms):
+    """Whole-job throughput: every rank renders `steps` views of `pixels_per_step` pixels."""
+    return ws * pixels_per_step * steps / (ms / 1e3) / 1e6
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -328,7 +350,7 @@ def main():
 
     sc, cams = scenes.scene_scale_workload(args.n)
     # each rank renders its own views (replicas): rotate the camera sequence by rank
-    cams = cams[rank % len(cams):] + cams[:rank % len(cams)]
+    cams = replica_cameras(cams, rank)
     dev = torch.device("cuda", local)
     t = render.scene_tensors(sc, dev)
     stream = torch.cuda.current_stream()
@@ -401,11 +423,7 @@ def main():
         s1.record(stream)
         torch.cuda.synchronize()
         launches = ges.ges_kernel_launches() - l0
-        ms = s0.elapsed_time(s1)
-        if dist:
-            x = torch.tensor([ms], device=dev)
-            dist.all_reduce(x, op=dist.ReduceOp.MAX)
-            ms = float(x.item())
+        ms = max_over_ranks(s0.elapsed_time(s1), dist, dev)
         return ms, launches
 
     if args.profile:
@@ -424,8 +442,8 @@ def main():
     assert err == ges.GES_OK, "key capacity overflowed during the timed region"
 
     pix = WIDTH * HEIGHT
-    value = ws * pix * args.steps / (ms_fb / 1e3) / 1e6
-    fwd_rate = ws * pix * args.steps / (ms_f / 1e3) / 1e6
+    value = aggregate_mpix_s(ws, pix, args.steps, ms_fb)
+    fwd_rate = aggregate_mpix_s(ws, pix, args.steps, ms_f)
     st_mean = stage.mean(0)
 
     # roofline of the dominant kernel: the composites are bound by the special-function unit
@@ -694,12 +712,8 @@ def e2e(args, sc, gcam, frame, params, dev, stream, ws, dist):
     stream.wait_stream(s_out)  # the last results are in host memory
     s1.record(stream)
     torch.cuda.synchronize()
-    ms = s0.elapsed_time(s1)
-    if dist:
-        x = torch.tensor([ms], device=dev)
-        dist.all_reduce(x, op=dist.ReduceOp.MAX)
-        ms = float(x.item())
-    return {"value": ws * WIDTH * HEIGHT * args.steps / (ms / 1e3) / 1e6, "unit": "Mpix/s",
+    ms = max_over_ranks(s0.elapsed_time(s1), dist, dev)
+    return {"value": aggregate_mpix_s(ws, WIDTH * HEIGHT, args.steps, ms), "unit": "Mpix/s",
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": ms / args.steps,
             "overlap": "copies pipelined against the kernels (two buffer slots, one copy stream per direction)"}
 
