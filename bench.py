@@ -512,6 +512,7 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sc, cams, args.cpu_pixels, os.cpu_count() or 1)
     if not args.no_extra:
+        out["image_loss"] = loss_bench(50, 3, dev, img)
         out["differentiation"] = differentiation_bench(20, 3, dev)
         torch.cuda.empty_cache()
         out["stress"] = stress_bench(5, 3, dev, beta2=False, segment_tiles=256)
@@ -590,6 +591,51 @@ def differentiation_bench(steps, warmup, dev):
                         "0.8 L1 + 0.2 (1 - SSIM) vs a seeded uniform target; step = rasterize + autograd.grad",
             "fwd_bwd_mpix_s": cam.width * cam.height / (ms / 1e3) / 1e6, "ms_per_step": ms, "steps": steps,
             "K": int(K), "loss": float(loss.detach())}
+
+
+def loss_bench(steps, warmup, dev, img):
+    """The training image loss on the rendered 1245x825 view: ges_freq_mask (omega 0.7, scale 0.2)
+    and ges_image_loss (lambda_ssim 0.2, lambda_omega 0.5) against a perturbed copy as the
+    ground truth.  Roofline: HBM, on the algorithmic bytes (mask: read I_gt, write the mask; loss:
+    read I, I_gt and the mask, write dL/dI)."""
+    import torch
+    from paper_2402_10128_gb300 import ges, render
+    ctx = render.default_context(dev.index or 0)
+    C, H, W = img.shape
+    gen = torch.Generator(device=dev).manual_seed(9)
+    gt = (img + 0.05 * torch.randn(img.shape, device=dev, generator=gen)).contiguous()
+    mask = torch.empty((H, W), dtype=torch.uint8, device=dev)
+    loss = torch.empty(4, device=dev)
+    grad = torch.empty_like(img)
+
+    def step():
+        ges.ges_freq_mask(ctx.handle, gt, W, H, 0.7, mask)
+        ges.ges_image_loss(ctx.handle, img, gt, mask, W, H, loss, grad)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record()
+    for _ in range(steps):
+        ges.ges_freq_mask(ctx.handle, gt, W, H, 0.7, mask)
+    e[1].record()
+    for _ in range(steps):
+        ges.ges_image_loss(ctx.handle, img, gt, mask, W, H, loss, grad)
+    e[2].record()
+    torch.cuda.synchronize()
+    ms_mask, ms_loss = e[0].elapsed_time(e[1]) / steps, e[1].elapsed_time(e[2]) / steps
+    peaks, _ = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    px = W * H
+    b_mask, b_loss = px * (12 + 1), px * (12 + 12 + 1 + 12)
+    return {"workload": "training image loss of the rendered 1245x825 view: frequency mask (omega 0.7, scale 0.2) "
+                        "and L = 0.3 L1 + 0.2 (1 - SSIM) + 0.5 L_omega with dL/dI",
+            "mask_ms": ms_mask, "loss_ms": ms_loss, "loss": [float(v) for v in loss.cpu()],
+            "roofline": {"bound": "hbm", "unit": "GB/s", "peak": hbm,
+                         "mask_achieved": b_mask / (ms_mask / 1e3) / 1e9, "mask_frac": b_mask / (ms_mask / 1e3) / 1e9 / hbm,
+                         "loss_achieved": b_loss / (ms_loss / 1e3) / 1e9, "loss_frac": b_loss / (ms_loss / 1e3) / 1e9 / hbm,
+                         "bytes_per_pixel": {"mask": 13, "loss": 37}}}
 
 
 def stress_bench(steps, warmup, dev, beta2, segment_tiles):

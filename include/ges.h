@@ -216,6 +216,33 @@ ges_status ges_trace_enable(ges_ctx* ctx, int on);
 ges_status ges_trace_read(ges_ctx* ctx, int32_t capacity, char* names, int64_t* launches, double* total_ms,
                           int32_t* n_out);
 
+/* Training image loss (Sec. 3.3, Eq. mask, Eq. laplace, Eq. final; no rasterizer state).
+
+   ges_freq_mask: the frequency-modulated mask M_omega of a ground-truth image gt [3,H,W] (fp32,
+   device): the channel mean of gt, box-downsampled by f = round(1/scale) (the image-frequency
+   scale, 0.2), filtered by DoG_omega = G(., 0.2 + 20 omega) - G(., 0.1 + 10 omega) (separable
+   Gaussian blurs truncated at ceil(3 sigma), zero outside the image); |DoG| divided by its maximum
+   and compared with `threshold` (0.5); upsampled by nearest neighbour into mask [H,W] (uint8 0/1,
+   device, caller-owned).  For omega <= 1/2 the mask is 1 - M_(1 - omega).  omega in [0,1] (the
+   training schedule uses iteration / total iterations), scale in (0,1].
+
+   ges_image_loss: L = (1 - lambda_ssim - lambda_omega) L1 + lambda_ssim (1 - SSIM)
+   + lambda_omega L_omega (paper: 0.2 and 0.5), L1 = mean |I - I_gt|,
+   L_omega = mean |(I - I_gt) M| (means over the 3 H W values; M from ges_freq_mask), SSIM with
+   an 11 x 11 Gaussian window (sigma 1.5), zero padding, C1 = 0.01^2, C2 = 0.03^2.  Writes
+   loss[4] = (L, L1, SSIM, L_omega) and dL_dimg [3,H,W] = dL/dI (the upstream gradient of
+   ges_render_bwd); all device pointers, caller-owned; I and I_gt [3,H,W] fp32.
+
+   Both are stream-ordered and asynchronous.  Each keeps grow-only scratch in the context (one
+   buffer per call kind), so calls of one kind on one context must be ordered on one stream.
+   Errors: GES_ERR_INVALID_ARG for NULL pointers, sizes or parameters out of range (nothing
+   enqueued); GES_ERR_OOM if the scratch cannot be allocated. */
+ges_status ges_freq_mask(ges_ctx* ctx, const float* gt, int32_t width, int32_t height, float omega, float scale,
+                         float threshold, uint8_t* mask, void* stream);
+ges_status ges_image_loss(ges_ctx* ctx, const float* img, const float* gt, const uint8_t* mask, int32_t width,
+                          int32_t height, float lambda_ssim, float lambda_omega, float* loss, float* dL_dimg,
+                          void* stream);
+
 /* Forward render that allocates no device memory (no counterpart in the paper; it exists for
    callers that cannot allocate).  Some callers cannot call cudaMalloc: code running under another
    runtime's memory manager that has already reserved the device's memory for its own pool, or

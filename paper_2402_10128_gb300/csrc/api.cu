@@ -278,6 +278,8 @@ ges_status ges_ctx_create(int device, size_t hbm_budget_bytes, ges_ctx** out) {
 
 void ges_ctx_destroy(ges_ctx* ctx) {
   if (!ctx) return;
+  if (ctx->scratch[0] || ctx->scratch[1]) cudaDeviceSynchronize();
+  for (int i = 0; i < 2; ++i) ctx_free(ctx, ctx->scratch[i], ctx->scratch_bytes[i]);
   for (auto& r : ctx->trace) {
     ctx->event_pool.push_back(r.a);
     ctx->event_pool.push_back(r.b);

@@ -21,6 +21,10 @@ struct ges_ctx {
   size_t used = 0;
   int num_sms = 0;
   std::mutex mu;
+  // scratch of the image-loss calls (grow-only): 0 mask, 1 loss
+  std::mutex scratch_mu;
+  void* scratch[2] = {nullptr, nullptr};
+  size_t scratch_bytes[2] = {0, 0};
   // kernel tracing (ges_trace_enable / ges_trace_read)
   bool trace_on = false;
   std::vector<ges_trace_rec> trace;

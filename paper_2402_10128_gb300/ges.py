@@ -37,7 +37,8 @@ GES_FALLOFF_PAPER_APPROX = 1
 EXPORTED = ["ges_last_error", "ges_params_default", "ges_ctx_create", "ges_ctx_destroy", "ges_frame_create",
             "ges_frame_destroy", "ges_preprocess", "ges_bin_sort", "ges_render_fwd", "ges_render_bwd",
             "ges_frame_status", "ges_frame_keys", "ges_frame_inspect", "ges_frame_count_work",
-            "ges_kernel_launches", "ges_trace_enable", "ges_trace_read", "ges_render_fwd_noalloc",
+            "ges_kernel_launches", "ges_trace_enable", "ges_trace_read", "ges_freq_mask", "ges_image_loss",
+            "ges_render_fwd_noalloc",
             "ges_serve_create", "ges_serve_add_scene",
             "ges_serve_submit", "ges_serve_poll", "ges_serve_destroy"]
 
@@ -96,6 +97,8 @@ def _load():
         "ges_kernel_launches": ([], u64),
         "ges_trace_enable": ([P, ctypes.c_int], i32),
         "ges_trace_read": ([P, i32, P, P, P, P], i32),
+        "ges_freq_mask": ([P, P, i32, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float, P, P], i32),
+        "ges_image_loss": ([P, P, P, P, i32, i32, ctypes.c_float, ctypes.c_float, P, P, P], i32),
         "ges_render_fwd_noalloc": ([P, P, P, P, P, P, P], i32),
         "ges_serve_create": ([P, P, i32, P], i32),
         "ges_serve_add_scene": ([P, P, P], i32),
@@ -279,6 +282,19 @@ def ges_frame_count_work(frame: int, stream=None):
 
 def ges_kernel_launches() -> int:
     return int(_lib.ges_kernel_launches())
+
+
+def ges_freq_mask(ctx: int, gt, width: int, height: int, omega: float, mask, scale: float = 0.2,
+                  threshold: float = 0.5, stream=None) -> None:
+    """Frequency-modulated mask M_omega of gt [3,H,W] into mask [H,W] uint8 (device tensors)."""
+    _check(_lib.ges_freq_mask(ctx, _addr(gt), width, height, omega, scale, threshold, _addr(mask), _stream(stream)))
+
+
+def ges_image_loss(ctx: int, img, gt, mask, width: int, height: int, loss, dL_dimg, lambda_ssim: float = 0.2,
+                   lambda_omega: float = 0.5, stream=None) -> None:
+    """loss[4] = (L, L1, SSIM, L_omega) and dL_dimg [3,H,W] (device tensors)."""
+    _check(_lib.ges_image_loss(ctx, _addr(img), _addr(gt), _addr(mask), width, height, lambda_ssim, lambda_omega,
+                               _addr(loss), _addr(dL_dimg), _stream(stream)))
 
 
 def ges_trace_enable(ctx: int, on: bool) -> None:
