@@ -13,6 +13,8 @@
 
 #include "api_internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace ges {
 
 static thread_local std::string g_last_error;
@@ -302,13 +304,15 @@ cudaEvent_t trace_event(ges_ctx* c) {
   return e;
 }
 
-// brackets the launches made in its lifetime with two events on stream s, when tracing is on
+// brackets the launches made in its lifetime with an NVTX range (for profilers) and, when tracing
+// is on, with two events on stream s
 struct TraceScope {
   ges_ctx* c;
   const char* name;
   cudaStream_t s;
   cudaEvent_t a = nullptr;
   TraceScope(ges_ctx* c_, const char* name_, cudaStream_t s_) : c(c_), name(name_), s(s_) {
+    nvtxRangePushA(name);
     if (!c->trace_on) return;
     std::lock_guard<std::mutex> lk(c->mu);
     a = trace_event(c);
@@ -318,6 +322,7 @@ struct TraceScope {
     }
   }
   ~TraceScope() {
+    nvtxRangePop();
     if (!a) return;
     std::lock_guard<std::mutex> lk(c->mu);
     cudaEvent_t b = trace_event(c);

@@ -105,6 +105,22 @@ def test_poll_semantics_and_errors(ges):
         ges.ges_serve_destroy(srv)
 
 
+def test_poll_times_out_then_completes(ges):
+    # the first request of a server also sets up its workspaces (allocation, graph capture), so a
+    # 1 us wait cannot see it finished; a long wait then does
+    srv, scs, ids, keep = _setup(ges, slots=2)
+    try:
+        cam = _cams(1, seed=6)[0]
+        out = np.empty((3, cam.height, cam.width), np.float32)
+        t = ges.ges_serve_submit(srv, ids[1], ges.make_camera(cam), out)
+        st, _ = ges.ges_serve_poll(srv, t, 1)
+        assert st == ges.GES_ERR_TIMEOUT
+        st, lat = ges.ges_serve_poll(srv, t, 30_000_000)
+        assert st == ges.GES_OK and lat > 0
+    finally:
+        ges.ges_serve_destroy(srv)
+
+
 def test_scenes_cannot_be_added_once_serving(ges):
     srv, scs, ids, keep = _setup(ges, slots=1)
     try:
