@@ -36,10 +36,16 @@ _lib = None
 # clamp 1.3).  flag_tol_* mark pixels whose result sits on a threshold.
 DEFAULT_PARAMS = dict(rho=0.1, mode=0, dilation=0.3, alpha_max=0.99, alpha_min=1.0 / 255.0,
                       t_min=1e-4, margin_rel=1e-3, margin_abs=1e-2, clamp_fov=1.3,
-                      flag_tol_alpha=1e-4, flag_tol_t=1e-4)
+                      flag_tol_alpha=1e-4, flag_tol_t=1e-4, phi_mode=0)
 
 MODE_GEF = 0
 MODE_PAPER_APPROX = 1
+
+# scale modification (Sec. 3.2): phi_bar_rho (Eq. approx); the exact Gamma ratio (Eq. probablity)
+# normalised to phi_n = 2 Gamma(3/beta)/Gamma(1/beta) on the scale vector; phi_n on the variance
+PHI_APPROX = 0
+PHI_EXACT = 1
+PHI_EXACT_VARIANCE = 2
 
 
 def build(force: bool = False) -> str:
@@ -71,6 +77,13 @@ def _load():
     lib.ora_key_log2.argtypes = [f32]
     lib.ora_phi_bar.argtypes = [i64, P, f64, P]
     lib.ora_phi_exact.argtypes = [i64, P, P]
+    lib.ora_phi_mod.argtypes = [i64, P, P, P, P]
+    lib.ora_digamma.restype = f64
+    lib.ora_digamma.argtypes = [f64]
+    lib.ora_key_lgamma.restype = f32
+    lib.ora_key_lgamma.argtypes = [f32]
+    lib.ora_key_phi.restype = f32
+    lib.ora_key_phi.argtypes = [f32, f32, i32]
     lib.ora_sh_basis.argtypes = [i32, i64, P, P]
     lib.ora_keys.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, P, P, P]
     lib.ora_sorted_keys.argtypes = [i64, P, P, P, P, P, P, P, P, P]
@@ -112,12 +125,12 @@ def par_array(params=None) -> np.ndarray:
     if params:
         p.update(params)
     keys = ["rho", "mode", "dilation", "alpha_max", "alpha_min", "t_min", "margin_rel",
-            "margin_abs", "clamp_fov", "flag_tol_alpha", "flag_tol_t"]
+            "margin_abs", "clamp_fov", "flag_tol_alpha", "flag_tol_t", "phi_mode"]
     out = np.zeros(16, np.float64)
     for i, k in enumerate(keys):
         v = p[k]
         # the kernels receive these as float32; the oracle uses the same values
-        out[i] = v if k in ("mode", "flag_tol_alpha", "flag_tol_t") else float(np.float32(v))
+        out[i] = v if k in ("mode", "flag_tol_alpha", "flag_tol_t", "phi_mode") else float(np.float32(v))
     return out
 
 
@@ -148,6 +161,28 @@ def phi_exact(beta):
     out = np.empty_like(b)
     _load().ora_phi_exact(b.size, _p(b), _p(out))
     return out
+
+
+def phi_mod(beta, params=None):
+    """(phi, dphi/dbeta) of the projection's scale modification in FP64 (params' phi_mode, rho)."""
+    b = _d(np.atleast_1d(beta))
+    phi, dphi = np.empty_like(b), np.empty_like(b)
+    _load().ora_phi_mod(b.size, _p(b), _p(par_array(params)), _p(phi), _p(dphi))
+    return phi, dphi
+
+
+def digamma(x: float) -> float:
+    return float(_load().ora_digamma(float(x)))
+
+
+def key_lgamma(x: float) -> float:
+    """The key path's FP32 ln Gamma."""
+    return float(_load().ora_key_lgamma(float(x)))
+
+
+def key_phi(beta: float, rho: float = 0.1, phi_mode: int = 0) -> float:
+    """The key path's FP32 scale modification."""
+    return float(_load().ora_key_phi(float(beta), float(rho), int(phi_mode)))
 
 
 def sh_basis(degree: int, dirs):

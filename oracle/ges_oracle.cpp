@@ -10,6 +10,7 @@
 //   * GES kernel  L(x) = exp(-1/2 ((x-mu)^T Sigma^-1 (x-mu))^(beta/2))      Sec. 3.1, Eq. (ges)
 //   * Sigma = R S S^T R^T with S scaled by the shape modification phi(beta)  Sec. 3.1
 //   * phi_bar_rho(beta) = 2 / (1 + exp(-(rho*beta - 2*rho))), rho = 0.1     Sec. 3.2, Eq. (approx); App. B.2
+//     or, as an option, the exact phi_n(beta) = 2 Gamma(3/beta)/Gamma(1/beta) Sec. 3.2, Eq. (probablity)
 //   * EWA projection Sigma' = J W Sigma W^T J^T (Zwicker et al.)             Sec. 3.1
 //   * discrete front-to-back compositing of the volume-rendering integral   Sec. 3.2, Eq. (transmittance)
 //   * view-dependent colour from real spherical harmonics                   Sec. 3.1
@@ -35,8 +36,10 @@
 //      primitive by the dual-number Jacobian of part 2.
 //
 // Parity pins live in tests/test_oracle_pins.py (closed forms, invariants,
-// finite differences).  The exact-Gamma modification phi(beta) (Eq. probablity)
-// is exported for completeness and is "parity unpinned" beyond phi(2)=1/2.
+// finite differences).  The exact-Gamma modification (Eq. probablity) is an option
+// of the projection, normalised to 2 Gamma(3/beta) / Gamma(1/beta) so that it is 1
+// at beta = 2 like phi_bar; it is applied to the scale vector (phi_mode 1) or, read
+// as a variance ratio, to the variance (phi_mode 2).
 
 #include <algorithm>
 #include <atomic>
@@ -62,6 +65,8 @@ struct Cam {
 struct Par {
   double rho;
   int mode;  // 0 = GEF falloff exp(-1/2 q^(beta/2)); 1 = paper's Gaussian-form rasterizer exp(-1/2 q)
+  int phi_mode;  // scale modification: 0 = phi_bar_rho (Eq. approx); 1 = normalised exact phi_n on the
+                 // scale vector; 2 = phi_n on the variance (sqrt(phi_n) on the scale vector)
   double dilation, alpha_max, alpha_min, t_min, margin_rel, margin_abs, clamp_fov;
   double flag_tol_alpha, flag_tol_t;
 };
@@ -82,6 +87,7 @@ Par read_par(const double* p) {
   r.rho = p[0]; r.mode = (int)p[1]; r.dilation = p[2]; r.alpha_max = p[3]; r.alpha_min = p[4];
   r.t_min = p[5]; r.margin_rel = p[6]; r.margin_abs = p[7]; r.clamp_fov = p[8];
   r.flag_tol_alpha = p[9]; r.flag_tol_t = p[10];
+  r.phi_mode = (int)p[11];
   return r;
 }
 
@@ -145,6 +151,53 @@ float key_log2(float x) {
   float ln_m = (2.0f * s) * p;
   const float log2e = (float)(1.0 / std::log(2.0));
   return (float)e + ln_m * log2e;
+}
+
+// ln Gamma(x) for x > 0, FP32.  Gamma(x) = Gamma(z) / (x (x+1) ... (z-1)) with z = x + k the first
+// shift at or above 4 (k <= 4), then Stirling's series for ln Gamma(z):
+//   (z - 1/2) ln z - z + ln(2 pi)/2 + 1/(12 z) - 1/(360 z^3) + 1/(1260 z^5) - 1/(1680 z^7)
+// (its first omitted term, 1/(1188 z^9), is below 4e-9 at z >= 4).  ln via key_log2 * ln 2.
+float key_lgamma(float x) {
+  const float ln2 = (float)std::log(2.0);
+  float z = x, acc = 1.0f;
+  for (int k = 0; k < 4 && z < 4.0f; ++k) {
+    acc = acc * z;
+    z = z + 1.0f;
+  }
+  float r = 1.0f / z;
+  float r2 = r * r;
+  float ser = -(float)(1.0 / 1680.0);
+  ser = ser * r2; ser = ser + (float)(1.0 / 1260.0);
+  ser = ser * r2; ser = ser - (float)(1.0 / 360.0);
+  ser = ser * r2; ser = ser + (float)(1.0 / 12.0);
+  ser = ser * r;
+  float lz = key_log2(z) * ln2;
+  float lg = (z - 0.5f) * lz;
+  lg = lg - z;
+  lg = lg + (float)(0.5 * std::log(2.0 * std::acos(-1.0)));
+  lg = lg + ser;
+  return lg - key_log2(acc) * ln2;
+}
+
+// The scale modification in the key path's precision:
+//   mode 0: phi_bar_rho(beta) = 2 / (1 + 2^(-rho (beta - 2) log2 e))                 (Eq. approx)
+//   mode 1: phi_n(beta) = 2 Gamma(3/beta) / Gamma(1/beta)
+//                       = 2^((ln Gamma(3/beta) - ln Gamma(1/beta) + ln 2) log2 e)  (Eq. probablity,
+//           normalised to 1 at beta = 2)
+//   mode 2: sqrt(phi_n(beta)): the same exponent halved
+float key_phi(float beta, float rho, int phi_mode) {
+  const float log2e = (float)(1.0 / std::log(2.0));
+  if (phi_mode == 0) {
+    float dbeta = beta - 2.0f;
+    float rdb = rho * dbeta;
+    float ex = key_exp2((-rdb) * log2e);
+    return 2.0f / (1.0f + ex);
+  }
+  float g3 = key_lgamma(3.0f / beta);
+  float g1 = key_lgamma(1.0f / beta);
+  float e = ((g3 - g1) + (float)std::log(2.0)) * log2e;
+  if (phi_mode == 2) e = e * 0.5f;
+  return key_exp2(e);
 }
 
 struct KeyOut {
@@ -238,11 +291,7 @@ void key_prim(const double* mu_d, const double* s_d, const double* q_d, double b
 
   // shape modification on the scale vector
   valid = valid && (beta > 0.0f);
-  const float log2e = (float)(1.0 / std::log(2.0));
-  float dbeta = beta - 2.0f;
-  float rdb = rho * dbeta;
-  float ex = key_exp2((-rdb) * log2e);
-  float phi = 2.0f / (1.0f + ex);
+  float phi = key_phi(beta, rho, par.phi_mode);
   float sp[3] = {phi * s[0], phi * s[1], phi * s[2]};
   float M[9];
   for (int i = 0; i < 3; ++i)
@@ -363,6 +412,40 @@ inline double dsqrt(double a) { return std::sqrt(a); }
 inline double dexp(double a) { return std::exp(a); }
 inline double val(double a) { return a; }
 
+// psi(x) = d ln Gamma(x) / dx for x > 0: psi(x) = psi(x + 1) - 1/x until x >= 10, then the
+// asymptotic series ln x - 1/(2x) - sum_k B_2k / (2k x^2k) with Bernoulli numbers B_2 .. B_12
+// (1/6, -1/30, 1/42, -1/30, 5/66, -691/2730); the first omitted term is below 1e-16 at x >= 10.
+double digamma(double x) {
+  double acc = 0.0;
+  for (int k = 0; k < 16 && x < 10.0; ++k) {
+    acc -= 1.0 / x;
+    x += 1.0;
+  }
+  double r2 = 1.0 / (x * x);
+  double s = r2 * (1.0 / 12 - r2 * (1.0 / 120 - r2 * (1.0 / 252 - r2 * (1.0 / 240 - r2 * (1.0 / 132 - r2 * 691.0 / 32760)))));
+  return acc + std::log(x) - 0.5 / x - s;
+}
+
+// The scale modification phi(beta) (its value and, for dual numbers, its derivative):
+//   phi_mode 0: phi_bar_rho(beta) = 2 / (1 + exp(-(rho beta - 2 rho)))                 Eq. approx
+//   phi_mode 1: phi_n(beta) = 2 Gamma(3/beta) / Gamma(1/beta)   (Eq. probablity, normalised so that
+//               phi_n(2) = 1 like phi_bar); d ln phi_n / d beta = (psi(1/beta) - 3 psi(3/beta)) / beta^2
+//   phi_mode 2: sqrt(phi_n(beta)) (phi_n read as a variance ratio, Eq. effective)
+inline double phi_n_log(double b) { return std::lgamma(3.0 / b) - std::lgamma(1.0 / b) + std::log(2.0); }
+inline double phi_mod(double beta, const Par& par) {
+  if (par.phi_mode == 0) return 2.0 / (1.0 + std::exp(-(par.rho * beta - 2.0 * par.rho)));
+  return std::exp((par.phi_mode == 2 ? 0.5 : 1.0) * phi_n_log(beta));
+}
+template <int K> Dual<K> phi_mod(const Dual<K>& beta, const Par& par) {
+  if (par.phi_mode == 0) return 2.0 / (1.0 + dexp(-(par.rho * beta - 2.0 * par.rho)));
+  const double c = par.phi_mode == 2 ? 0.5 : 1.0, b = beta.v;
+  Dual<K> r;
+  r.v = std::exp(c * phi_n_log(b));
+  const double slope = c * r.v * (digamma(1.0 / b) - 3.0 * digamma(3.0 / b)) / (b * b);
+  for (int i = 0; i < K; ++i) r.d[i] = slope * beta.d[i];
+  return r;
+}
+
 // clamp(x, lo, hi) as a function of x: constant (zero derivative) when clamped
 template <class S> S clampv(const S& x, double lo, double hi) {
   if (val(x) < lo) return S(lo);
@@ -434,8 +517,8 @@ void project(const S mu[3], const S s[3], const S q[4], const S& beta, const S& 
   R[3] = 2.0 * (x * y + w * z); R[4] = 1.0 - 2.0 * (x * x + z * z); R[5] = 2.0 * (y * z - w * x);
   R[6] = 2.0 * (x * z - w * y); R[7] = 2.0 * (y * z + w * x); R[8] = 1.0 - 2.0 * (x * x + y * y);
 
-  // phi_bar_rho(beta) = 2 / (1 + exp(-(rho beta - 2 rho)))  (Eq. approx), applied to the scale vector
-  S phi = 2.0 / (1.0 + dexp(-(par.rho * beta - 2.0 * par.rho)));
+  // the scale modification (phi_bar_rho by default, Eq. approx), applied to the scale vector
+  S phi = phi_mod(beta, par);
   S sp[3] = {phi * s[0], phi * s[1], phi * s[2]};
   S Sig[9];
   for (int i = 0; i < 3; ++i)
@@ -638,10 +721,24 @@ float ora_key_log2(float x) { return key_log2(x); }
 void ora_phi_bar(int64_t n, const double* beta, double rho, double* out) {
   for (int64_t i = 0; i < n; ++i) out[i] = 2.0 / (1.0 + std::exp(-(rho * beta[i] - 2.0 * rho)));
 }
-// exact modification Gamma(3/beta)/Gamma(1/beta) (Eq. probablity); parity unpinned beyond beta=2
+// exact modification Gamma(3/beta)/Gamma(1/beta) (Eq. probablity), not normalised
 void ora_phi_exact(int64_t n, const double* beta, double* out) {
   for (int64_t i = 0; i < n; ++i) out[i] = std::tgamma(3.0 / beta[i]) / std::tgamma(1.0 / beta[i]);
 }
+// the modification the projection applies, and its derivative in beta (dual numbers)
+void ora_phi_mod(int64_t n, const double* beta, const double* par_d, double* phi, double* dphi) {
+  Par par = read_par(par_d);
+  for (int64_t i = 0; i < n; ++i) {
+    Dual<1> b(beta[i]);
+    b.d[0] = 1.0;
+    Dual<1> r = phi_mod(b, par);
+    phi[i] = r.v;
+    dphi[i] = r.d[0];
+  }
+}
+double ora_digamma(double x) { return digamma(x); }
+float ora_key_lgamma(float x) { return key_lgamma(x); }
+float ora_key_phi(float beta, float rho, int phi_mode) { return key_phi(beta, rho, phi_mode); }
 
 void ora_sh_basis(int deg, int64_t n, const double* dirs, double* out) {
   int nb = (deg + 1) * (deg + 1);

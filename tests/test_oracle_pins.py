@@ -64,6 +64,82 @@ def test_phi_exact_closed_forms():
     assert abs(oracle.phi_exact(4.0)[0] - math.gamma(0.75) / math.gamma(0.25)) < 1e-14
 
 
+def _phi_ref(beta, phi_mode, rho=RHO32):
+    """The scale modification written from Sec. 3.2 with the standard library's Gamma function:
+    phi_bar_rho (Eq. approx); 2 Gamma(3/b)/Gamma(1/b) (Eq. probablity, normalised to 1 at b = 2);
+    its square root (the ratio read as one of variances, Eq. effective)."""
+    if phi_mode == oracle.PHI_APPROX:
+        return 2.0 / (1.0 + math.exp(-rho * (beta - 2.0)))
+    r = 2.0 * math.gamma(3.0 / beta) / math.gamma(1.0 / beta)
+    return r if phi_mode == oracle.PHI_EXACT else math.sqrt(r)
+
+
+def test_digamma_special_values_and_recurrence():
+    gamma_e = 0.57721566490153286  # Euler-Mascheroni constant: psi(1) = -gamma
+    assert abs(oracle.digamma(1.0) + gamma_e) < 1e-14
+    assert abs(oracle.digamma(0.5) + gamma_e + 2 * math.log(2.0)) < 1e-14   # psi(1/2) = -gamma - 2 ln 2
+    for n in range(1, 25):                                                     # psi(n+1) = H_n - gamma
+        h = sum(1.0 / k for k in range(1, n + 1))
+        assert abs(oracle.digamma(n + 1.0) - (h - gamma_e)) < 1e-14 * max(1.0, h)
+    rng = np.random.default_rng(30)
+    for x in np.exp(rng.uniform(math.log(0.02), math.log(200.0), 200)):
+        # psi(x + 1) - psi(x) = 1/x, and psi is the slope of ln Gamma (central differences of libm)
+        assert abs(oracle.digamma(x + 1) - oracle.digamma(x) - 1 / x) < 1e-12 * max(1.0, 1 / x)
+        h = 1e-5 * x
+        fd = (math.lgamma(x + h) - math.lgamma(x - h)) / (2 * h)
+        assert abs(oracle.digamma(x) - fd) < 1e-7 * max(1.0, abs(fd))
+
+
+def test_key_lgamma_matches_the_library():
+    """The key path's FP32 ln Gamma (shift to z >= 4, Stirling's series) against libm's."""
+    xs = np.concatenate([np.exp(np.linspace(math.log(1 / 64), math.log(64.0), 400)), [0.5, 1.0, 2.0, 3.0, 8.0]])
+    for x in xs.astype(np.float32):
+        got, ref = oracle.key_lgamma(float(x)), math.lgamma(float(x))
+        assert abs(got - ref) <= 2.5e-6 * max(1.0, abs(ref)), (x, got, ref)
+
+
+@pytest.mark.parametrize("phi_mode", [0, 1, 2])
+def test_key_phi_matches_the_gamma_ratio(phi_mode):
+    """The key path's FP32 scale modification against Sec. 3.2 written with math.gamma."""
+    for b in np.exp(np.linspace(math.log(0.4), math.log(32.0), 300)).astype(np.float32):
+        got, ref = oracle.key_phi(float(b), RHO32, phi_mode), _phi_ref(float(b), phi_mode)
+        assert abs(got - ref) <= 4e-6 * ref, (b, got, ref)
+
+
+def test_phi_exact_normalised_closed_forms():
+    g = _golden()
+    P1 = dict(phi_mode=oracle.PHI_EXACT)
+    P2 = dict(phi_mode=oracle.PHI_EXACT_VARIANCE)
+    phi = lambda b, p: oracle.phi_mod(b, p)[0][0]
+    # 1 at beta = 2 (Sec. 3.2, after Eq. approx; Fig. approximation caption), in both readings
+    assert abs(phi(2.0, P1) - g["phi_bar_at_beta_2"]) < 1e-15 and abs(phi(2.0, P2) - 1.0) < 1e-15
+    assert abs(phi(1.0, P1) - 4.0) < 1e-14            # 2 Gamma(3) / Gamma(1)
+    assert abs(phi(0.5, P1) - 240.0) < 1e-11          # 2 Gamma(6) / Gamma(2) = 2 * 5!
+    assert abs(phi(3.0, P1) - 2.0 / math.gamma(1 / 3)) < 1e-14
+    assert abs(phi(1.0, P2) - 2.0) < 1e-14
+    # beta -> infinity: Gamma(3/b)/Gamma(1/b) -> 1/3 (the box), so phi_n -> 2/3
+    assert abs(phi(1e7, P1) - 2.0 / 3.0) < 1e-6
+    # the normalisation of the unnormalised ratio printed in Eq. probablity
+    for b in (0.7, 1.3, 2.9, 6.0):
+        assert abs(phi(b, P1) - 2.0 * oracle.phi_exact(b)[0]) < 1e-13 * phi(b, P1)
+
+
+@pytest.mark.parametrize("phi_mode", [0, 1, 2])
+def test_phi_derivative_by_finite_differences(phi_mode):
+    """d phi / d beta carried by the oracle's dual numbers (digamma for the exact forms) against
+    central differences of its value (libm's lgamma)."""
+    params = dict(phi_mode=phi_mode)
+    b = np.exp(np.linspace(math.log(0.4), math.log(24.0), 60))
+    _, d = oracle.phi_mod(b, params)
+    h = 1e-6 * b
+    fd = (oracle.phi_mod(b + h, params)[0] - oracle.phi_mod(b - h, params)[0]) / (2 * h)
+    assert np.all(np.abs(d - fd) <= 1e-6 * np.maximum(np.abs(fd), 1e-3))
+    if phi_mode == oracle.PHI_EXACT:
+        # at beta = 1: 4 (psi(1) - 3 psi(3)) with psi(1) = -gamma, psi(3) = 3/2 - gamma: 4 (2 gamma - 9/2)
+        gamma_e = 0.57721566490153286
+        assert abs(oracle.phi_mod(1.0, params)[1][0] - 4 * (2 * gamma_e - 4.5)) < 1e-12
+
+
 def test_eta_bounds_arithmetic():
     g = _golden()
     assert abs((4 - math.pi) / math.pi - g["eta_square_larger"]) < 5e-5
@@ -106,21 +182,24 @@ def test_sh_addition_theorem_and_parity():
 
 
 # ---------------------------------------------------------------- projection
-def test_isotropic_on_axis_projection_closed_form():
+@pytest.mark.parametrize("phi_mode", [0, 1, 2])
+def test_isotropic_on_axis_projection_closed_form(phi_mode):
     cam = axis_camera(64, 64)
+    params = dict(phi_mode=phi_mode)
     for beta in (2.0, 0.7, 5.0):
-        s, z = 0.125, 4.0
+        s, z = 0.125 if phi_mode == 0 else 0.0625, 4.0
         sc = make_scene([[0, 0, z]], [[s, s, s]], [[1, 0, 0, 0]], [beta], [0.8], rgb=[[0.3, 0.6, 0.9]])
-        pr = oracle.project(sc, cam)[0]
-        b32, rho32, dil32 = (float(np.float32(v)) for v in (beta, 0.1, 0.3))
-        phi = 2.0 / (1.0 + math.exp(-rho32 * (b32 - 2.0)))
+        pr = oracle.project(sc, cam, params)[0]
+        b32, dil32 = (float(np.float32(v)) for v in (beta, 0.3))
+        phi = _phi_ref(b32, phi_mode)
         var = (cam.fx * phi * s / z) ** 2 + dil32
         assert abs(pr[0] - cam.cx) < 1e-12 and abs(pr[1] - cam.cy) < 1e-12
         assert abs(pr[5] - var) < 1e-12 * var and abs(pr[6]) < 1e-15 and abs(pr[7] - var) < 1e-12 * var
         assert abs(pr[2] - 1 / var) < 1e-12 / var and abs(pr[4] - 1 / var) < 1e-12 / var
         np.testing.assert_allclose(pr[8:11], [0.3, 0.6, 0.9], atol=1e-6)
-        k = oracle.keys(sc, cam)
-        np.testing.assert_allclose(k["cov2d"][0], [var, 0, var], rtol=1e-6, atol=1e-6)
+        k = oracle.keys(sc, cam, params)
+        # FP32 key path: phi_n carries up to 2e-6 relative error (its Gamma ratio in FP32), twice that in var
+        np.testing.assert_allclose(k["cov2d"][0], [var, 0, var], rtol=1e-6 if phi_mode == 0 else 5e-6, atol=1e-6)
         np.testing.assert_allclose(k["mean2d"][0], [cam.cx, cam.cy], rtol=0, atol=1e-4)
 
 
@@ -173,8 +252,8 @@ def test_anisotropic_ewa_matches_textbook():
 
 
 # ---------------------------------------------------------------- falloff
-@pytest.mark.parametrize("beta", [1.0, 2.0, 0.6, 3.5])
-def test_lone_splat_is_the_1d_gef(beta):
+@pytest.mark.parametrize("beta,phi_mode", [(1.0, 0), (2.0, 0), (0.6, 0), (3.5, 0), (1.0, 1), (3.5, 1), (0.8, 2)])
+def test_lone_splat_is_the_1d_gef(beta, phi_mode):
     """A lone isotropic splat on the optical axis, bg = 0: along the centre row the
     pixel value is rgb * min(0.99, A exp(-(|x-mu|/alpha)^beta)) with A = kappa and
     alpha = sigma' 2^(1/beta) (Eq. gef); beta=1 is Laplace-shaped, beta=2 Gaussian."""
@@ -183,10 +262,10 @@ def test_lone_splat_is_the_1d_gef(beta):
     s, z, kappa = 0.0625, 3.0, 0.875
     rgb = np.array([0.25, 0.5, 1.0])
     sc = make_scene([[0, 0, z]], [[s, s, s]], [[1, 0, 0, 0]], [beta], [kappa], rgb=[rgb])
-    out = oracle.render(sc, cam)
-    b32, rho32, dil32 = (float(np.float32(v)) for v in (beta, 0.1, 0.3))
+    out = oracle.render(sc, cam, params=dict(phi_mode=phi_mode))
+    b32, dil32 = (float(np.float32(v)) for v in (beta, 0.3))
     rgb = Y00 * sc.shs[0, 0].astype(np.float64) + 0.5
-    phi = 2.0 / (1.0 + math.exp(-rho32 * (b32 - 2.0)))
+    phi = _phi_ref(b32, phi_mode)
     sigma = math.sqrt((cam.fx * phi * s / z) ** 2 + dil32)
     alpha_scale = sigma * 2.0 ** (1.0 / b32)
     row = W // 2  # pixel centre y = 32.5, mean y = 32 -> offset 0.5
@@ -270,6 +349,26 @@ def test_beta2_equals_independent_gaussian_renderer():
         out = oracle.render(sc, cam, params=dict(mode=mode))
         assert np.max(np.abs(out["img"] - ref)) < 1e-10
         assert np.max(np.abs(out["T"] - Tref)) < 1e-10
+
+
+def test_beta2_scale_modifications_agree():
+    """At beta = 2 every form of the modification is 1 (Sec. 3.2), so the images agree."""
+    sc = random_small_scene(25, seed=4, beta_range=(2.0, 2.0))
+    cam = axis_camera(48, 40)
+    ref = oracle.render(sc, cam)["img"]
+    for pm in (oracle.PHI_EXACT, oracle.PHI_EXACT_VARIANCE):
+        assert np.max(np.abs(oracle.render(sc, cam, params=dict(phi_mode=pm))["img"] - ref)) < 1e-12
+
+
+def test_exact_phi_paper_form_is_the_scaled_gaussian():
+    """With the exact modification, the paper's Gaussian-form rasterizer is the Gaussian with its
+    scales times 2 Gamma(3/b)/Gamma(1/b) (Eq. probablity), written here with math.gamma."""
+    sc = random_small_scene(25, seed=5, beta_range=(1.0, 9.0))
+    cam = axis_camera(48, 40)
+    mult = np.array([_phi_ref(float(b), oracle.PHI_EXACT) for b in sc.betas.astype(np.float64)])
+    ref, _ = _gaussian_reference(sc, cam, scale_mult=mult)
+    out = oracle.render(sc, cam, params=dict(mode=oracle.MODE_PAPER_APPROX, phi_mode=oracle.PHI_EXACT))
+    assert np.max(np.abs(out["img"] - ref)) < 1e-10
 
 
 def test_rho0_paper_form_is_gaussian_for_any_beta():
@@ -435,11 +534,12 @@ def _f64(sc):
     return scenes.Scene(*(np.asarray(a, np.float64) for a in sc.arrays()), sc.sh_degree)
 
 
-@pytest.mark.parametrize("mode", [oracle.MODE_GEF, oracle.MODE_PAPER_APPROX])
-def test_backward_matches_finite_differences(mode):
-    sc = _f64(random_small_scene(10, seed=21, beta_range=(0.6, 4.5)))
+@pytest.mark.parametrize("mode,phi_mode", [(oracle.MODE_GEF, 0), (oracle.MODE_PAPER_APPROX, 0),
+                                           (oracle.MODE_GEF, 1), (oracle.MODE_GEF, 2)])
+def test_backward_matches_finite_differences(mode, phi_mode):
+    sc = _f64(random_small_scene(10, seed=21, beta_range=(0.6, 4.5) if phi_mode == 0 else (1.2, 4.5)))
     cam = axis_camera(32, 32, bg=(0.2, 0.1, 0.3))
-    _fd_check(sc, cam, dict(mode=mode), seed=1)
+    _fd_check(sc, cam, dict(mode=mode, phi_mode=phi_mode), seed=1)
 
 
 def test_backward_matches_finite_differences_sh3_offaxis():
