@@ -514,6 +514,7 @@ def main():
     if not args.no_extra:
         out["image_loss"] = loss_bench(50, 3, dev, img)
         out["differentiation"] = differentiation_bench(20, 3, dev)
+        out["scale_modification"] = scale_modification_bench(10, 3, dev, sc, t, cams[0], args.segment_tiles)
         torch.cuda.empty_cache()
         out["stress"] = stress_bench(5, 3, dev, beta2=False, segment_tiles=256)
         torch.cuda.empty_cache()
@@ -638,21 +639,18 @@ def loss_bench(steps, warmup, dev, img):
                          "bytes_per_pixel": {"mask": 13, "loss": 37}}}
 
 
-def stress_bench(steps, warmup, dev, beta2, segment_tiles):
-    """The stress configuration (6M cube primitives, SH3, 3840x2160): fwd and fwd+bwd, either with
-    beta log-U[0.3,16] (very sharp and very wide kernels; listed per tile row, segment_tiles =
-    256) or with beta = 2 everywhere (the Gaussian degenerate case)."""
+def _time_c_abi_steps(sc, t, cam, params, steps, warmup, dev):
+    """fwd (K1-K4) and fwd+bwd (K1-K8) through the C-ABI on device-resident scene tensors `t`,
+    timed with CUDA events; returns (K entries, {"fwd": ..., "fwd_bwd": ...})."""
     import torch
-    from paper_2402_10128_gb300 import ges, render, scenes
-    sc, cam = scenes.stress_beta2_workload() if beta2 else scenes.stress_workload()
-    t = render.scene_tensors(sc, dev)
+    from paper_2402_10128_gb300 import ges, render
     probe = render.Frame(sc.n, cam.width, cam.height, key_capacity=0)
-    probe.forward(t, sc.sh_degree, cam, {"segment_tiles": segment_tiles})
+    probe.forward(t, sc.sh_degree, cam, {"segment_tiles": params.segment_tiles, "mode": params.falloff,
+                                         "rho": params.rho, "phi_mode": params.phi_mode})
     K = probe.status()[1]
     probe.close()
     frame = render.Frame(sc.n, cam.width, cam.height, key_capacity=int(K * 1.02) + 4096)
-    gcam, params = ges.make_camera(cam), ges.params_default()
-    params.segment_tiles = segment_tiles
+    gcam = ges.make_camera(cam)
     H, W = cam.height, cam.width
     img = torch.empty((3, H, W), device=dev)
     T = torch.empty((H, W), device=dev)
@@ -682,10 +680,47 @@ def stress_bench(steps, warmup, dev, beta2, segment_tiles):
         ms = e0.elapsed_time(e1) / steps
         out["fwd_bwd" if bwd else "fwd"] = {"mpix_s": W * H / (ms / 1e3) / 1e6, "ms_per_frame": ms}
     assert frame.status()[0] == 0
+    assert all(torch.isfinite(g).all() for g in grads)
     frame.close()
+    return int(K), out
+
+
+def stress_bench(steps, warmup, dev, beta2, segment_tiles):
+    """The stress configuration (6M cube primitives, SH3, 3840x2160): fwd and fwd+bwd, either with
+    beta log-U[0.3,16] (very sharp and very wide kernels; listed per tile row, segment_tiles =
+    256) or with beta = 2 everywhere (the Gaussian degenerate case)."""
+    from paper_2402_10128_gb300 import ges, render, scenes
+    sc, cam = scenes.stress_beta2_workload() if beta2 else scenes.stress_workload()
+    t = render.scene_tensors(sc, dev)
+    params = ges.params_default()
+    params.segment_tiles = segment_tiles
+    K, out = _time_c_abi_steps(sc, t, cam, params, steps, warmup, dev)
     form = "beta = 2" if beta2 else "beta log-U[0.3,16]"
     return {"workload": f"stress, {form}: 6M cube primitives, SH3, 3840x2160", "segment_tiles": segment_tiles,
-            "K_entries": int(K), "steps": steps, **out}
+            "K_entries": K, "steps": steps, **out}
+
+
+def scale_modification_bench(steps, warmup, dev, sc, t, cam, segment_tiles):
+    """The scale-modification variants (Sec. 3.2 and the ablation's shape strengths) on one view of
+    the scene-scale workload: phi_bar_rho at rho = 0.1 (default), 0 and 10, the exact normalised
+    Gamma ratio on the scale vector and on the variance, and the Gaussian-form rasterizer.  The
+    exact ratio makes small-beta primitives far larger (240x at beta = 1/2), hence more list entries
+    and more pairs to composite."""
+    from paper_2402_10128_gb300 import ges
+    variants = {"phi_bar_rho0.1": {}, "phi_bar_rho0": {"rho": 0.0}, "phi_bar_rho10": {"rho": 10.0},
+                "phi_exact": {"phi_mode": ges.GES_PHI_EXACT},
+                "phi_exact_variance": {"phi_mode": ges.GES_PHI_EXACT_VARIANCE},
+                "gaussian_form_phi_bar": {"falloff": ges.GES_FALLOFF_PAPER_APPROX}}
+    res = {}
+    for name, kw in variants.items():
+        params = ges.params_default()
+        params.segment_tiles = segment_tiles
+        for k, v in kw.items():
+            setattr(params, k, v)
+        K, out = _time_c_abi_steps(sc, t, cam, params, steps, warmup, dev)
+        res[name] = {"K_entries": K, **out}
+    return {"workload": "scene-scale view 0: 1.5M clustered primitives, SH3, beta log-U[0.5,8], 1245x825",
+            "steps": steps, "segment_tiles": segment_tiles, "variants": res}
 
 
 def e2e(args, sc, gcam, frame, params, dev, stream, ws, dist):

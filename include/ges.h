@@ -62,6 +62,18 @@ typedef enum ges_falloff {
   GES_FALLOFF_PAPER_APPROX = 1
 } ges_falloff;
 
+typedef enum ges_phi_mode {
+  /* phi_bar_rho(beta) = 2 / (1 + exp(-(rho beta - 2 rho))) on the scale vector (Eq. approx); default */
+  GES_PHI_APPROX = 0,
+  /* the exact Gamma ratio of Eq. probablity normalised to 1 at beta = 2,
+     phi_n(beta) = 2 Gamma(3/beta) / Gamma(1/beta), on the scale vector (the slot phi_bar approximates).
+     phi_n is 4 at beta = 1, 240 at beta = 1/2 and over 1e5 below beta = 0.33: primitives of small beta
+     grow accordingly (the instability Sec. 3.2 gives as the reason for phi_bar) */
+  GES_PHI_EXACT = 1,
+  /* phi_n read as a ratio of variances (Eq. effective): sqrt(phi_n(beta)) on the scale vector */
+  GES_PHI_EXACT_VARIANCE = 2
+} ges_phi_mode;
+
 typedef struct ges_camera {
   int32_t width, height;  /* pixels, 1..16384 each */
   float fx, fy, cx, cy;   /* pinhole intrinsics in pixels */
@@ -87,6 +99,10 @@ typedef struct ges_params {
                              (1 lists every tile separately).  Larger segments mean fewer entries
                              to sort and more entries for the composite to skip; the images do
                              not depend on it. */
+  int32_t phi_mode;       /* ges_phi_mode: the scale modification (GES_PHI_APPROX).  rho is used by
+                             GES_PHI_APPROX only.  The exact forms take ln Gamma on the key path's
+                             fixed-order FP32 arithmetic (Stirling's series after a shift to >= 4),
+                             so their phi is within 2e-6 of the exact ratio for beta in [0.4, 32] */
 } ges_params;
 
 typedef struct ges_scene {

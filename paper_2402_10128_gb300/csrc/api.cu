@@ -88,6 +88,7 @@ Params to_params(const ges_params& p) {
   while ((1 << l) < p.segment_tiles) ++l;
   P.seg_log2 = l;
   P.seg_bits = 0;  // set once the segment count is known
+  P.phi_mode = p.phi_mode;
   return P;
 }
 
@@ -103,6 +104,8 @@ ges_status check_params(const ges_params* p) {
     return fail(GES_ERR_INVALID_ARG, "dilation, rho and margins must be >= 0, clamp_fov > 0");
   if (p->segment_tiles < 1 || p->segment_tiles > 1024 || (p->segment_tiles & (p->segment_tiles - 1)))
     return fail(GES_ERR_INVALID_ARG, "segment_tiles %d is not a power of two in [1, 1024]", p->segment_tiles);
+  if (p->phi_mode != GES_PHI_APPROX && p->phi_mode != GES_PHI_EXACT && p->phi_mode != GES_PHI_EXACT_VARIANCE)
+    return fail(GES_ERR_INVALID_ARG, "unknown phi_mode %d", p->phi_mode);
   return GES_OK;
 }
 
@@ -252,6 +255,7 @@ ges_status ges_params_default(ges_params* out) {
   out->extent_margin_abs = 1e-2f;
   out->clamp_fov = 1.3f;
   out->segment_tiles = 16;
+  out->phi_mode = GES_PHI_APPROX;
   return GES_OK;
 }
 

@@ -48,4 +48,49 @@ __device__ __forceinline__ float key_log2(float x) {
   return kadd((float)e, kmul(ln_m, log2e));
 }
 
+// ln Gamma(x) for x > 0: Gamma(x) = Gamma(z) / (x (x+1) ... (z-1)) with z = x + k the first shift at
+// or above 4 (k <= 4), then Stirling's series for ln Gamma(z),
+//   (z - 1/2) ln z - z + ln(2 pi)/2 + 1/(12 z) - 1/(360 z^3) + 1/(1260 z^5) - 1/(1680 z^7),
+// whose first omitted term, 1/(1188 z^9), is below 4e-9 at z >= 4.  ln via key_log2 * ln 2.
+__device__ __forceinline__ float key_lgamma(float x) {
+  const float ln2 = (float)0.6931471805599453;
+  float z = x, acc = 1.0f;
+  for (int k = 0; k < 4 && z < 4.0f; ++k) {
+    acc = kmul(acc, z);
+    z = kadd(z, 1.0f);
+  }
+  const float r = kdiv(1.0f, z);
+  const float r2 = kmul(r, r);
+  float ser = -(float)(1.0 / 1680.0);
+  ser = kmul(ser, r2); ser = kadd(ser, (float)(1.0 / 1260.0));
+  ser = kmul(ser, r2); ser = ksub(ser, (float)(1.0 / 360.0));
+  ser = kmul(ser, r2); ser = kadd(ser, (float)(1.0 / 12.0));
+  ser = kmul(ser, r);
+  const float lz = kmul(key_log2(z), ln2);
+  float lg = kmul(ksub(z, 0.5f), lz);
+  lg = ksub(lg, z);
+  lg = kadd(lg, (float)0.91893853320467274);  // ln(2 pi) / 2
+  lg = kadd(lg, ser);
+  return ksub(lg, kmul(key_log2(acc), ln2));
+}
+
+// The scale modification phi(beta) (Sec. 3.2) applied to the scale vector:
+//   phi_mode 0: phi_bar_rho(beta) = 2 / (1 + 2^(-rho (beta - 2) log2 e))                   Eq. approx
+//   phi_mode 1: phi_n(beta) = 2 Gamma(3/beta) / Gamma(1/beta)                            Eq. probablity
+//               = 2^((ln Gamma(3/beta) - ln Gamma(1/beta) + ln 2) log2 e), 1 at beta = 2
+//   phi_mode 2: sqrt(phi_n(beta)), phi_n read as a ratio of variances (Eq. effective)
+__device__ __forceinline__ float key_phi(float beta, const Params& P) {
+  const float log2e = (float)1.4426950408889634;
+  if (P.phi_mode == 0) {
+    const float rdb = kmul(P.rho, ksub(beta, 2.0f));
+    const float ex = key_exp2(kmul(-rdb, log2e));
+    return kdiv(2.0f, kadd(1.0f, ex));
+  }
+  const float g3 = key_lgamma(kdiv(3.0f, beta));
+  const float g1 = key_lgamma(kdiv(1.0f, beta));
+  float e = kmul(kadd(ksub(g3, g1), (float)0.6931471805599453), log2e);
+  if (P.phi_mode == 2) e = kmul(e, 0.5f);
+  return key_exp2(e);
+}
+
 }  // namespace ges

@@ -2,6 +2,7 @@
 //
 // Forward, per primitive (Sec. 3.1, Sec. 3.2):
 //   phi_bar_rho(beta) = 2 / (1 + exp(-rho (beta - 2)))            Eq. approx (App. B.2: rho = 0.1)
+//   or phi_n(beta) = 2 Gamma(3/beta) / Gamma(1/beta) (or its root)   Eq. probablity, normalised
 //   Sigma = R diag(phi_bar s)^2 R^T                                  Sec. 3.1 (scale vector modified by phi)
 //   Sigma' = J W Sigma W^T J^T + dilation I, conic = Sigma'^-1       Sec. 3.1 (EWA, Zwicker et al.)
 //   extent: alpha = kappa exp(-1/2 q^(beta/2)) >= alpha_min  <=>  q <= q* = (2 ln(kappa/alpha_min))^(2/beta)
@@ -159,6 +160,19 @@ __device__ __forceinline__ float3 sh_colour_bwd(float dx, float dy, float dz, co
   return gd;
 }
 
+// psi(x) = d ln Gamma(x) / dx for x > 0 (the backward's slope of the exact modification, ordinary
+// FP32): psi(x) = psi(x + 1) - 1/x until x >= 6, then ln x - 1/(2x) - 1/(12 x^2) + 1/(120 x^4) -
+// 1/(252 x^6) (the first omitted term, 1/(240 x^8), is below 3e-9 at x >= 6).
+__device__ __forceinline__ float digammaf(float x) {
+  float acc = 0.0f;
+  for (int k = 0; k < 6 && x < 6.0f; ++k) {
+    acc -= 1.0f / x;
+    x += 1.0f;
+  }
+  const float r = 1.0f / x, r2 = r * r;
+  return acc + logf(x) - 0.5f * r - r2 * ((1.0f / 12.0f) - r2 * ((1.0f / 120.0f) - r2 * (1.0f / 252.0f)));
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
@@ -214,12 +228,9 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ VS v
     R[7] = kmul(2.0f, kadd(yz, wx));
     R[8] = ksub(1.0f, kmul(2.0f, kadd(xx, yy)));
 
-    // shape modification phi_bar on the scale vector
+    // shape modification on the scale vector
     valid = valid && (beta > 0.0f);
-    const float log2e = (float)1.4426950408889634;
-    float rdb = kmul(P.rho, ksub(beta, 2.0f));
-    float ex = key_exp2(kmul(-rdb, log2e));
-    float phi = kdiv(2.0f, kadd(1.0f, ex));
+    const float phi = key_phi(beta, P);
     float sp[3] = {kmul(phi, s0), kmul(phi, s1), kmul(phi, s2)};
     float M[9];
 #pragma unroll
@@ -399,7 +410,7 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(const __grid_constant__ 
     R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z); R[2] = 2.f * (x * z + w * y);
     R[3] = 2.f * (x * y + w * z); R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
     R[6] = 2.f * (x * z - w * y); R[7] = 2.f * (y * z + w * x); R[8] = 1.f - 2.f * (x * x + y * y);
-    const float phi = 2.0f / (1.0f + expf(-P.rho * (beta - 2.0f)));
+    const float phi = P.phi_mode == 0 ? 2.0f / (1.0f + expf(-P.rho * (beta - 2.0f))) : key_phi(beta, P);
     const float sp[3] = {phi * s[0], phi * s[1], phi * s[2]};
     float M[9];
 #pragma unroll
@@ -486,7 +497,16 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(const __grid_constant__ 
         gsp[b] += gM * R[3 * a + b];
       }
     const float gphi = s[0] * gsp[0] + s[1] * gsp[1] + s[2] * gsp[2];
-    float gbeta = gphi * P.rho * phi * (1.0f - 0.5f * phi);
+    // d phi / d beta: rho phi (1 - phi/2) for phi_bar; c phi (psi(1/beta) - 3 psi(3/beta)) / beta^2 for
+    // phi_n^c (c = 1, or 1/2 for the variance reading)
+    float gbeta;
+    if (P.phi_mode == 0) {
+      gbeta = gphi * P.rho * phi * (1.0f - 0.5f * phi);
+    } else {
+      const float ib = 1.0f / beta;
+      const float dl = (digammaf(ib) - 3.0f * digammaf(3.0f * ib)) * ib * ib;
+      gbeta = gphi * phi * (P.phi_mode == 2 ? 0.5f * dl : dl);
+    }
     if (P.mode == 0) gbeta += 0.5f * g_hb;
     // ---- rotation from the normalised quaternion
     float gw = 2.f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);

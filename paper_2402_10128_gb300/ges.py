@@ -32,6 +32,9 @@ STATUS_NAMES = {0: "GES_OK", 1: "GES_ERR_INVALID_ARG", 2: "GES_ERR_OOM", 3: "GES
 
 GES_FALLOFF_GEF = 0
 GES_FALLOFF_PAPER_APPROX = 1
+GES_PHI_APPROX = 0
+GES_PHI_EXACT = 1
+GES_PHI_EXACT_VARIANCE = 2
 
 # every symbol declared in include/ges.h
 EXPORTED = ["ges_last_error", "ges_params_default", "ges_ctx_create", "ges_ctx_destroy", "ges_frame_create",
@@ -60,7 +63,7 @@ class ges_params(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_float), ("falloff", ctypes.c_int32), ("dilation", ctypes.c_float),
                 ("alpha_max", ctypes.c_float), ("alpha_min", ctypes.c_float), ("t_min", ctypes.c_float),
                 ("extent_margin_rel", ctypes.c_float), ("extent_margin_abs", ctypes.c_float),
-                ("clamp_fov", ctypes.c_float), ("segment_tiles", ctypes.c_int32)]
+                ("clamp_fov", ctypes.c_float), ("segment_tiles", ctypes.c_int32), ("phi_mode", ctypes.c_int32)]
 
 
 class ges_scene(ctypes.Structure):

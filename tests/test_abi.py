@@ -45,12 +45,13 @@ def test_params_default_matches_paper_constants(lib):
     assert abs(p.rho - 0.1) < 1e-7 and p.falloff == ges.GES_FALLOFF_GEF
     assert abs(p.alpha_max - 0.99) < 1e-7 and abs(p.alpha_min - 1 / 255) < 1e-9 and abs(p.t_min - 1e-4) < 1e-10
     assert abs(p.dilation - 0.3) < 1e-7
+    assert p.segment_tiles == 16 and p.phi_mode == ges.GES_PHI_APPROX
 
 
 def test_struct_layouts_match_header(lib):
     from paper_2402_10128_gb300 import ges
     assert ctypes.sizeof(ges.ges_camera) == 4 * (2 + 4 + 16 + 3 + 1 + 3)
-    assert ctypes.sizeof(ges.ges_params) == 4 * 10
+    assert ctypes.sizeof(ges.ges_params) == 4 * 11
     assert ctypes.sizeof(ges.ges_scene) == 8 + 8 + 6 * 8
     assert ctypes.sizeof(ges.ges_grads) == 6 * 8
 

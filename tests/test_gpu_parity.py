@@ -30,6 +30,18 @@ def _cases():
         "paper_form": (*scenes.tiny_workload(), dict(mode=1)),
         "dense_batches": (scenes.cube_scene(5000, seed=13, scale_range=(0.01, 0.06)), scenes.tiny_camera(160, 120),
                           None),
+        # the exact Gamma-ratio modification (Eq. probablity, normalised) on the scale vector and, with
+        # the Gaussian-form rasterizer, on the variance; beta from 0.8 (phi_n = 11) to 12
+        "exact_phi": (scenes.cube_scene(400, seed=14, beta_range=(0.8, 12.0), beta_log=True,
+                                        scale_range=(0.01, 0.06)), scenes.tiny_camera(70, 50), dict(phi_mode=1)),
+        "exact_phi_variance_paper_form": (scenes.cube_scene(400, seed=15, sh_degree=2, beta_range=(0.5, 12.0),
+                                                            beta_log=True, scale_range=(0.01, 0.08)),
+                                          scenes.tiny_camera(70, 50), dict(phi_mode=2, mode=1)),
+        # the ablation's shape strengths: rho = 10 (phi_bar close to a step at beta = 2) and rho = 0
+        "rho10": (scenes.cube_scene(400, seed=16, beta_range=(0.5, 8.0), beta_log=True), scenes.tiny_camera(70, 50),
+                  dict(rho=10.0)),
+        "rho0": (scenes.cube_scene(400, seed=16, beta_range=(0.5, 8.0), beta_log=True), scenes.tiny_camera(70, 50),
+                 dict(rho=0.0)),
     }
 
 
@@ -204,6 +216,8 @@ def test_invalid_arguments_rejected(lib):
         fr.preprocess(t, 4, cam)
     with pytest.raises(lib.GesError):
         fr.preprocess(t, sc.sh_degree, cam, dict(alpha_min=0.995))
+    with pytest.raises(lib.GesError):
+        fr.preprocess(t, sc.sh_degree, cam, dict(phi_mode=3))
     with pytest.raises(lib.GesError):
         fr.bin_sort()  # nothing preprocessed yet
 
