@@ -516,6 +516,8 @@ def main():
         out["differentiation"] = differentiation_bench(20, 3, dev)
         out["scale_modification"] = scale_modification_bench(10, 3, dev, sc, t, cams[0], args.segment_tiles)
         torch.cuda.empty_cache()
+        out["training"] = training_bench(20, 3, dev, sc, cams, args.segment_tiles)
+        torch.cuda.empty_cache()
         out["stress"] = stress_bench(5, 3, dev, beta2=False, segment_tiles=256)
         torch.cuda.empty_cache()
         out["stress_beta2"] = stress_bench(5, 3, dev, beta2=True, segment_tiles=args.segment_tiles)
@@ -637,6 +639,115 @@ def loss_bench(steps, warmup, dev, img):
                          "mask_achieved": b_mask / (ms_mask / 1e3) / 1e9, "mask_frac": b_mask / (ms_mask / 1e3) / 1e9 / hbm,
                          "loss_achieved": b_loss / (ms_loss / 1e3) / 1e9, "loss_frac": b_loss / (ms_loss / 1e3) / 1e9 / hbm,
                          "bytes_per_pixel": {"mask": 13, "loss": 37}}}
+
+
+def training_bench(steps, warmup, dev, sc, cams, segment_tiles):
+    """One training iteration of the paper's loop per step on the scene-scale workload (1.5M
+    primitives, SH3, 1245x825, cycling through the 20 views): ges_preprocess, ges_bin_sort,
+    ges_render_fwd, ges_freq_mask of the view's target (omega 0.7), ges_image_loss (0.2 SSIM,
+    0.5 L_omega), ges_render_bwd, ges_densify_stats and ges_adam_step over all 1.5M primitives.  The
+    targets are the views rendered once from the scene; the optimizer starts from the scene's own
+    parameters (log-scales, logits, beta - 2).  Then one ges_density_control over the statistics
+    of the timed steps (App. B.2 thresholds, extent 1, split normals from a seeded generator).
+    Roofline of k_adam: HBM, 32 B per element (read variable, moments, gradient; write variable,
+    moments, physical value), 60 elements per primitive at SH3."""
+    import torch
+    from paper_2402_10128_gb300 import ges, render
+    ctx = render.default_context(dev.index or 0)
+    n, sh = sc.n, sc.sh_degree
+    W, H = cams[0].width, cams[0].height
+    t = render.scene_tensors(sc, dev)
+    probe = render.Frame(n, W, H, key_capacity=0)
+    targets, K = [], 0
+    for cam in cams:
+        img, _, _ = probe.forward(t, sh, cam, {"segment_tiles": segment_tiles})
+        targets.append(img.clone())
+        K = max(K, probe.status()[1])
+    probe.close()
+    raw = [t[0].clone(), torch.log(t[1]), t[2].clone(), t[3] - 2.0, torch.logit(t[4]), t[5].clone()]
+    mom = [torch.zeros_like(a) for a in raw]
+    vel = [torch.zeros_like(a) for a in raw]
+    phys = [torch.empty_like(a) for a in raw]
+    grads = tuple(torch.empty_like(a) for a in raw)
+    del t
+    tset = ges.make_train_set(n, sh, raw, mom, vel)
+    so = ges.make_scene_out(*phys)
+    ges.ges_activate(ctx.handle, tset, so)
+    hp = ges.adam_params_default()
+    frame = render.Frame(n, W, H, key_capacity=int(K * 1.05) + 4096)
+    gcams = [ges.make_camera(c) for c in cams]
+    params = ges.params_default()
+    params.segment_tiles = segment_tiles
+    scene_c, grads_c = ges.make_scene(*phys, sh), ges.make_grads(*grads)
+    img = torch.empty((3, H, W), device=dev)
+    T = torch.empty((H, W), device=dev)
+    nc = torch.empty((H, W), dtype=torch.int32, device=dev)
+    mask = torch.empty((H, W), dtype=torch.uint8, device=dev)
+    loss = torch.empty(4, device=dev)
+    dL = torch.empty((3, H, W), device=dev)
+    acc = torch.zeros(n, device=dev)
+    cnt = torch.zeros(n, dtype=torch.int32, device=dev)
+    it = [0]
+
+    def step():
+        i = it[0]
+        it[0] += 1
+        k = i % len(cams)
+        ges.ges_preprocess(frame.handle, scene_c, gcams[k], params)
+        ges.ges_bin_sort(frame.handle)
+        ges.ges_render_fwd(frame.handle, img, T, nc)
+        ges.ges_freq_mask(ctx.handle, targets[k], W, H, 0.7, mask)
+        ges.ges_image_loss(ctx.handle, img, targets[k], mask, W, H, loss, dL)
+        ges.ges_render_bwd(frame.handle, scene_c, T, nc, dL, grads_c)
+        ges.ges_densify_stats(frame.handle, acc, cnt)
+        ges.ges_adam_step(ctx.handle, tset, grads_c, so, hp, i + 1)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    ges.ges_trace_enable(ctx.handle, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    trace = ges.ges_trace_read(ctx.handle)
+    ges.ges_trace_enable(ctx.handle, False)
+    ms = e0.elapsed_time(e1) / steps
+    assert frame.status()[0] == 0 and bool(torch.isfinite(loss).all())
+    frame.close()
+    kernel_ms = {k: v[1] / steps for k, v in trace.items()}
+    adam_ms = trace["k_adam"][1] / trace["k_adam"][0]
+    elems = n * (12 + 3 * (sh + 1) ** 2)
+    peaks, _ = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    adam_gbs = elems * 32 / (adam_ms / 1e3) / 1e9
+
+    # one density control over the statistics gathered above
+    gen = torch.Generator(device=dev).manual_seed(11)
+    xi = torch.randn((n, 2, 3), device=dev, generator=gen)
+    dp = ges.density_params_default()
+    cap = 3 * n
+    out = [torch.empty((cap,) + tuple(a.shape[1:]), device=dev) for a in raw]
+    om = [torch.empty_like(a) for a in out]
+    ov = [torch.empty_like(a) for a in out]
+    tout = ges.make_train_set(cap, sh, out, om, ov)
+    torch.cuda.synchronize()
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d0.record()
+    n_out = ges.ges_density_control(ctx.handle, tset, acc, cnt, xi, dp, tout)
+    d1.record()
+    torch.cuda.synchronize()
+    return {"workload": "training iteration: scene-scale, 1.5M primitives, SH3, 1245x825, 20 views; fwd + frequency "
+                        "mask + image loss + bwd + densification statistics + Adam over all primitives",
+            "steps": steps, "ms_per_step": ms, "iterations_per_s": 1e3 / ms,
+            "kernel_ms_per_step": kernel_ms, "loss_last": [float(v) for v in loss.cpu()],
+            "adam": {"ms": adam_ms, "elements": elems,
+                     "roofline": {"bound": "hbm", "achieved": adam_gbs, "peak": hbm, "unit": "GB/s",
+                                  "frac": adam_gbs / hbm, "bytes_per_element": 32}},
+            "density_control": {"ms": d0.elapsed_time(d1), "rows_in": n, "rows_out": int(n_out),
+                                "views_accumulated": steps + warmup}}
 
 
 def _time_c_abi_steps(sc, t, cam, params, steps, warmup, dev):

@@ -259,6 +259,108 @@ ges_status ges_image_loss(ges_ctx* ctx, const float* img, const float* gt, const
                           int32_t height, float lambda_ssim, float lambda_omega, float* loss, float* dL_dimg,
                           void* stream);
 
+/* Training-side updates (Sec. 3.4; App. B.2): the optimizer and the density control that consume
+   ges_render_bwd's gradients, as in Gaussian splatting (whose optimisation the paper keeps) plus
+   the paper's shape resets and shape pruning.
+
+   The optimizer's variables of a primitive, in six groups (index: contents, activation):
+     0 means [n,3]                    mu = p
+     1 log-scales [n,3]               s = exp(p)
+     2 quaternions [n,4]              q = p (the rasterizer normalises; its gradient is w.r.t. p)
+     3 shifted shapes [n]             beta = p + 2 (App. B.2: the shape is stored shifted by -2)
+     4 opacity logits [n]             kappa = 1 / (1 + exp(-p))
+     5 SH coefficients [n,(d+1)^2,3]  identity
+   A ges_train_set holds the variables and their Adam moments (device fp32 arrays of those shapes,
+   caller-owned; moments zero-initialised by the caller).  Each pointer must be 16-byte aligned. */
+typedef struct ges_train_set {
+  int64_t n;              /* primitives (rows); for an output set, the capacity */
+  int32_t sh_degree;      /* 0..3 */
+  float* param[6];
+  float* m[6];            /* Adam first moments */
+  float* v[6];            /* Adam second moments */
+} ges_train_set;
+
+/* Physical values written for the renderer (same shapes as ges_scene; device, caller-owned). */
+typedef struct ges_scene_out {
+  float* means;
+  float* scales;
+  float* quats;
+  float* betas;
+  float* opacities;
+  float* shs;
+} ges_scene_out;
+
+typedef struct ges_adam_params {
+  float lr[6];            /* per group; lr[5] is the SH DC rate.  App. B.2: 1.6e-4 (the position
+                             schedule's start, see ges_position_lr), 0.005, 0.001, 0.001, 0.05, 0.0025 */
+  float lr_sh_rest;       /* the SH coefficients of degree >= 1 (0.0025 / 20, as in Gaussian splatting) */
+  float beta1, beta2;     /* 0.9, 0.999 */
+  float eps;              /* 1e-15 */
+} ges_adam_params;
+
+typedef struct ges_density_params {
+  float grad_threshold;   /* densify where the mean screen-space gradient norm >= this (App. B.2: 0.0003) */
+  float percent_dense;    /* clone if max scale <= percent_dense * scene_extent, else split (0.01) */
+  float scene_extent;     /* world units, > 0 (1) */
+  float min_opacity;      /* prune kappa below this (App. B.2: 0.005); 0 disables */
+  float min_beta;         /* shape pruning: prune beta below this; 0 disables (0) */
+  float max_world_size;   /* prune where max scale > max_world_size * scene_extent; 0 disables (0) */
+} ges_density_params;
+
+ges_status ges_adam_params_default(ges_adam_params* out);
+ges_status ges_density_params_default(ges_density_params* out);
+
+/* The position learning rate at `step` (host only): log-linear from lr_init to lr_final over
+   max_steps (constant after), times delay_mult + (1 - delay_mult) sin(pi/2 min(step/delay_steps, 1))
+   when delay_steps > 0.  App. B.2: 1.6e-4, 1.6e-6, 0.01, 30000.  Errors: GES_ERR_INVALID_ARG for a
+   NULL out, max_steps < 1, or a rate <= 0. */
+ges_status ges_position_lr(int64_t step, float lr_init, float lr_final, float delay_mult, int64_t delay_steps,
+                           int64_t max_steps, float* out);
+
+/* One fused Adam step (Kingma & Ba, with bias correction; step >= 1 counts the calls) over every
+   group: the gradient w.r.t. the physical value (grads, as ges_render_bwd writes it) is taken to
+   the variable through its activation, the moments and the variable are updated, and the new
+   physical values are written to phys.  One launch, one pass over the arrays.  Stream-ordered.
+   Errors: GES_ERR_INVALID_ARG for NULL or misaligned pointers, n < 0, step < 1 or
+   beta1/beta2 outside [0,1). */
+ges_status ges_adam_step(ges_ctx* ctx, const ges_train_set* set, const ges_grads* grads, const ges_scene_out* phys,
+                         const ges_adam_params* hp, int64_t step, void* stream);
+
+/* phys = the activations of set's variables (after ges_density_control or a reset).  Stream-ordered. */
+ges_status ges_activate(ges_ctx* ctx, const ges_train_set* set, const ges_scene_out* phys, void* stream);
+
+/* Densification statistics of the frame's last ges_render_bwd: for every primitive the view lists,
+   grad_accum[i] += ||(dL/du W/2, dL/dv H/2)|| (the screen-space mean gradient in NDC units, as in
+   Gaussian splatting) and count[i] += 1.  grad_accum [n] fp32 and count [n] int32 (device,
+   caller-owned, zeroed by the caller before the first view).  Stream-ordered.  Errors:
+   GES_ERR_INVALID_ARG for NULL pointers or no ges_render_bwd since the last ges_preprocess. */
+ges_status ges_densify_stats(ges_frame* frame, float* grad_accum, int32_t* count, void* stream);
+
+/* Density control.  With g = grad_accum / max(count, 1) per row of `in`:
+     clone  g >= grad_threshold and max scale <= percent_dense * extent: the row is kept and copied;
+     split  g >= grad_threshold and max scale > percent_dense * extent: the row is replaced by two
+            children at mu + R(q) (s * xi[i, j]) (j = 0, 1) with scales s / 1.6, the rest copied;
+     prune  kappa < min_opacity, beta < min_beta, or max scale > max_world_size * extent, applied to
+            every resulting row (children with their own scales).
+   The decisions compare the variables with the thresholds mapped into them (log, logit, minus 2;
+   computed in double on the host, rounded once to fp32).  xi: [n,2,3] fp32 standard normals
+   (device), drawn by the caller.  `out` (capacity out->n rows, sh_degree as `in`, no array shared
+   with `in`) receives the kept rows in order, then the clones, then the first and the second
+   children, each in the order of `in`; moments are copied for kept rows and zero for new ones.
+   *n_out (host) gets the row count.  The call synchronises `stream` once (to read the counts).
+   Errors: GES_ERR_INVALID_ARG for NULL/misaligned pointers or parameters out of range;
+   GES_ERR_CAPACITY (nothing written, *n_out = the rows needed) if out->n is too small. */
+ges_status ges_density_control(ges_ctx* ctx, const ges_train_set* in, const float* grad_accum, const int32_t* count,
+                               const float* xi, const ges_density_params* dp, const ges_train_set* out,
+                               int64_t* n_out, void* stream);
+
+/* Opacity reset: kappa <- min(kappa, max_opacity) (Gaussian splatting: 0.01, every 3000 steps);
+   shape reset: beta <- beta (2: back to the Gaussian, every 1000 steps).  The group's moments are
+   zeroed.  Stream-ordered.  Errors: GES_ERR_INVALID_ARG for NULL pointers, max_opacity outside (0,1)
+   or beta <= 0. */
+ges_status ges_reset_opacity(ges_ctx* ctx, const ges_train_set* set, float max_opacity, void* stream);
+ges_status ges_reset_shape(ges_ctx* ctx, const ges_train_set* set, float beta, void* stream);
+
 /* Forward render that allocates no device memory (no counterpart in the paper; it exists for
    callers that cannot allocate).  Some callers cannot call cudaMalloc: code running under another
    runtime's memory manager that has already reserved the device's memory for its own pool, or

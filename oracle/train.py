@@ -124,12 +124,13 @@ def _quat_rot(q):
 def density_thresholds(grad_threshold=0.0003, percent_dense=0.01, extent=1.0, min_opacity=0.005,
                        min_beta=0.0, max_world=0.0):
     """The thresholds mapped into the optimizer's variables and rounded to FP32, as the host side of
-    the kernels computes them (FP64, then one rounding)."""
+    the kernels computes them: from the FP32 parameters, in FP64, then one rounding."""
     f = lambda x: float(np.float32(x))
-    return dict(grad=f(grad_threshold), log_small=f(math.log(percent_dense * extent)),
-                logit_opacity=f(math.log(min_opacity / (1.0 - min_opacity))) if min_opacity > 0 else -math.inf,
-                shifted_beta=f(min_beta - 2.0) if min_beta > 0 else -math.inf,
-                log_big=f(math.log(max_world * extent)) if max_world > 0 else math.inf,
+    pd, ext, mo, mb, mw = (f(x) for x in (percent_dense, extent, min_opacity, min_beta, max_world))  # fp32 inputs
+    return dict(grad=f(grad_threshold), log_small=f(math.log(pd * ext)),
+                logit_opacity=f(math.log(mo / (1.0 - mo))) if mo > 0 else -math.inf,
+                shifted_beta=f(mb - 2.0) if mb > 0 else -math.inf,
+                log_big=f(math.log(mw * ext)) if mw > 0 else math.inf,
                 log_split=f(math.log(1.6)))
 
 

@@ -193,6 +193,62 @@ static ges_status frame_alloc_keys(ges_frame* f, int64_t key_cap) {
   return GES_OK;
 }
 
+// ---------------------------------------------------------------- tracing
+
+cudaEvent_t trace_event(ges_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+
+TraceScope::TraceScope(ges_ctx* c_, const char* name_, cudaStream_t s_) : c(c_), name(name_), s(s_) {
+  nvtxRangePushA(name);
+  if (!c->trace_on) return;
+  std::lock_guard<std::mutex> lk(c->mu);
+  a = trace_event(c);
+  if (a && cudaEventRecord(a, s) != cudaSuccess) {
+    c->event_pool.push_back(a);
+    a = nullptr;
+  }
+}
+
+TraceScope::~TraceScope() {
+  nvtxRangePop();
+  if (!a) return;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaEvent_t b = trace_event(c);
+  if (b && cudaEventRecord(b, s) == cudaSuccess) {
+    c->trace.push_back({name, a, b});
+  } else {
+    c->event_pool.push_back(a);
+    if (b) c->event_pool.push_back(b);
+  }
+}
+
+// grow-only scratch of the context, one buffer per slot (0 mask, 1 loss, 2 density control)
+ges_status ctx_scratch(ges_ctx* ctx, int slot, size_t bytes, void** out) {
+  std::lock_guard<std::mutex> lk(ctx->scratch_mu);
+  if (ctx->scratch_bytes[slot] < bytes) {
+    if (ctx->scratch[slot]) {
+      cudaDeviceSynchronize();  // kernels of an earlier call may still use it
+      ctx_free(ctx, ctx->scratch[slot], ctx->scratch_bytes[slot]);
+    }
+    ctx->scratch[slot] = nullptr;
+    ctx->scratch_bytes[slot] = 0;
+    ges_status st = ctx_alloc(ctx, &ctx->scratch[slot], bytes);
+    if (st != GES_OK) return st;
+    ctx->scratch_bytes[slot] = bytes;
+  }
+  *out = ctx->scratch[slot];
+  return GES_OK;
+}
+
 }  // namespace ges
 
 using namespace ges;
@@ -284,8 +340,10 @@ ges_status ges_ctx_create(int device, size_t hbm_budget_bytes, ges_ctx** out) {
 
 void ges_ctx_destroy(ges_ctx* ctx) {
   if (!ctx) return;
-  if (ctx->scratch[0] || ctx->scratch[1]) cudaDeviceSynchronize();
-  for (int i = 0; i < 2; ++i) ctx_free(ctx, ctx->scratch[i], ctx->scratch_bytes[i]);
+  bool any = false;
+  for (int i = 0; i < kScratchSlots; ++i) any = any || ctx->scratch[i];
+  if (any) cudaDeviceSynchronize();
+  for (int i = 0; i < kScratchSlots; ++i) ctx_free(ctx, ctx->scratch[i], ctx->scratch_bytes[i]);
   for (auto& r : ctx->trace) {
     ctx->event_pool.push_back(r.a);
     ctx->event_pool.push_back(r.b);
@@ -293,53 +351,6 @@ void ges_ctx_destroy(ges_ctx* ctx) {
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   delete ctx;
 }
-
-// ---------------------------------------------------------------- tracing
-namespace {
-
-cudaEvent_t trace_event(ges_ctx* c) {
-  if (!c->event_pool.empty()) {
-    cudaEvent_t e = c->event_pool.back();
-    c->event_pool.pop_back();
-    return e;
-  }
-  cudaEvent_t e = nullptr;
-  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-  return e;
-}
-
-// brackets the launches made in its lifetime with an NVTX range (for profilers) and, when tracing
-// is on, with two events on stream s
-struct TraceScope {
-  ges_ctx* c;
-  const char* name;
-  cudaStream_t s;
-  cudaEvent_t a = nullptr;
-  TraceScope(ges_ctx* c_, const char* name_, cudaStream_t s_) : c(c_), name(name_), s(s_) {
-    nvtxRangePushA(name);
-    if (!c->trace_on) return;
-    std::lock_guard<std::mutex> lk(c->mu);
-    a = trace_event(c);
-    if (a && cudaEventRecord(a, s) != cudaSuccess) {
-      c->event_pool.push_back(a);
-      a = nullptr;
-    }
-  }
-  ~TraceScope() {
-    nvtxRangePop();
-    if (!a) return;
-    std::lock_guard<std::mutex> lk(c->mu);
-    cudaEvent_t b = trace_event(c);
-    if (b && cudaEventRecord(b, s) == cudaSuccess) {
-      c->trace.push_back({name, a, b});
-    } else {
-      c->event_pool.push_back(a);
-      if (b) c->event_pool.push_back(b);
-    }
-  }
-};
-
-}  // namespace
 
 ges_status ges_trace_enable(ges_ctx* ctx, int on) {
   if (!ctx) return fail(GES_ERR_INVALID_ARG, "ctx is NULL");
@@ -508,6 +519,7 @@ ges_status ges_preprocess(ges_frame* f, const ges_scene* scene, const ges_camera
   if (e != cudaSuccess) return cuda_fail(e, "preprocess launch");
   f->have_pre = true;
   f->have_sort = false;
+  f->have_bwd = false;
   return GES_OK;
 }
 
@@ -624,6 +636,7 @@ ges_status ges_render_bwd(ges_frame* f, const ges_scene* scene, const float* fin
     launch_preprocess_bwd<FrameViews>(f->vt, f->n, f->P, f->depth_key, f->g2d, f->ctx->num_sms, s);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "render_bwd launch");
+  f->have_bwd = true;
   return GES_OK;
 }
 

@@ -15,16 +15,18 @@ struct ges_trace_rec {
   cudaEvent_t a, b;
 };
 
+constexpr int kScratchSlots = 3;  // 0 mask, 1 image loss, 2 density control
+
 struct ges_ctx {
   int device = 0;
   size_t budget = 0;   // bytes this context may allocate (0 = unbounded)
   size_t used = 0;
   int num_sms = 0;
   std::mutex mu;
-  // scratch of the image-loss calls (grow-only): 0 mask, 1 loss
+  // grow-only scratch of the calls that keep state in the context (ctx_scratch)
   std::mutex scratch_mu;
-  void* scratch[2] = {nullptr, nullptr};
-  size_t scratch_bytes[2] = {0, 0};
+  void* scratch[kScratchSlots] = {};
+  size_t scratch_bytes[kScratchSlots] = {};
   // kernel tracing (ges_trace_enable / ges_trace_read)
   bool trace_on = false;
   std::vector<ges_trace_rec> trace;
@@ -70,7 +72,7 @@ struct ges_frame {
   uint32_t* sorted_prims = nullptr;
   uint32_t* tile_keys = nullptr;
   uint32_t* tile_vals = nullptr;
-  bool have_pre = false, have_sort = false;
+  bool have_pre = false, have_sort = false, have_bwd = false;
   // scratch for ges_frame_count_work
   float* work_img = nullptr;
   unsigned long long* work_stats = nullptr;
@@ -90,4 +92,18 @@ void fill_view(ViewDesc& v, const ges_camera& c, const ges_scene& s, int64_t pri
                int32_t seg_base, int seg_log2);
 ges_status set_segment_bits(Params& P, int64_t total_segs);
 int bits_for(int64_t count);
+// grow-only device scratch of the context, one buffer per slot; replacing a buffer synchronises the device
+ges_status ctx_scratch(ges_ctx* ctx, int slot, size_t bytes, void** out);
+// brackets the launches made in its lifetime with an NVTX range (for profilers) and, when tracing
+// is on, with two events on stream s
+struct TraceScope {
+  ges_ctx* c;
+  const char* name;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  TraceScope(ges_ctx* c_, const char* name_, cudaStream_t s_);
+  ~TraceScope();
+  TraceScope(const TraceScope&) = delete;
+  TraceScope& operator=(const TraceScope&) = delete;
+};
 }  // namespace ges

@@ -292,24 +292,6 @@ __global__ void k_loss_final(const __grid_constant__ LossArgs A) {
   A.loss[3] = (float)lw;
 }
 
-// grow-only scratch of the context: slot 0 for the mask, slot 1 for the loss
-ges_status loss_scratch(ges_ctx* ctx, int slot, size_t bytes, void** out) {
-  std::lock_guard<std::mutex> lk(ctx->scratch_mu);
-  if (ctx->scratch_bytes[slot] < bytes) {
-    if (ctx->scratch[slot]) {
-      cudaDeviceSynchronize();  // kernels of an earlier call may still use it
-      ctx_free(ctx, ctx->scratch[slot], ctx->scratch_bytes[slot]);
-    }
-    ctx->scratch[slot] = nullptr;
-    ctx->scratch_bytes[slot] = 0;
-    ges_status st = ctx_alloc(ctx, &ctx->scratch[slot], bytes);
-    if (st != GES_OK) return st;
-    ctx->scratch_bytes[slot] = bytes;
-  }
-  *out = ctx->scratch[slot];
-  return GES_OK;
-}
-
 }  // namespace
 }  // namespace ges
 
@@ -339,7 +321,7 @@ ges_status ges_freq_mask(ges_ctx* ctx, const float* gt, int32_t width, int32_t h
   const int w = (width + f - 1) / f, h = (height + f - 1) / f;
   const size_t n = (size_t)w * h;
   void* buf = nullptr;
-  if ((st = loss_scratch(ctx, 0, 256 + sizeof(float) * 4 * n, &buf)) != GES_OK) return st;
+  if ((st = ctx_scratch(ctx, 0, 256 + sizeof(float) * 4 * n, &buf)) != GES_OK) return st;
   unsigned int* dmax = reinterpret_cast<unsigned int*>(buf);
   float* low = reinterpret_cast<float*>(static_cast<char*>(buf) + 256);
   float* a = low + n;
@@ -372,7 +354,7 @@ ges_status ges_image_loss(ges_ctx* ctx, const float* img, const float* gt, const
   if (st != GES_OK) return st;
   const int64_t plane = (int64_t)width * height;
   void* buf = nullptr;
-  if ((st = loss_scratch(ctx, 1, 256 + sizeof(float) * 9 * (size_t)plane, &buf)) != GES_OK) return st;
+  if ((st = ctx_scratch(ctx, 1, 256 + sizeof(float) * 9 * (size_t)plane, &buf)) != GES_OK) return st;
   LossArgs A;
   A.img = img;
   A.gt = gt;

@@ -42,6 +42,8 @@ EXPORTED = ["ges_last_error", "ges_params_default", "ges_ctx_create", "ges_ctx_d
             "ges_frame_status", "ges_frame_keys", "ges_frame_inspect", "ges_frame_count_work",
             "ges_kernel_launches", "ges_trace_enable", "ges_trace_read", "ges_freq_mask", "ges_image_loss",
             "ges_render_fwd_noalloc",
+            "ges_adam_params_default", "ges_density_params_default", "ges_position_lr", "ges_adam_step",
+            "ges_activate", "ges_densify_stats", "ges_density_control", "ges_reset_opacity", "ges_reset_shape",
             "ges_serve_create", "ges_serve_add_scene",
             "ges_serve_submit", "ges_serve_poll", "ges_serve_destroy"]
 
@@ -77,6 +79,27 @@ class ges_grads(ctypes.Structure):
                 ("betas", ctypes.c_void_p), ("opacities", ctypes.c_void_p), ("shs", ctypes.c_void_p)]
 
 
+class ges_train_set(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("sh_degree", ctypes.c_int32), ("param", ctypes.c_void_p * 6),
+                ("m", ctypes.c_void_p * 6), ("v", ctypes.c_void_p * 6)]
+
+
+class ges_scene_out(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("betas", ctypes.c_void_p), ("opacities", ctypes.c_void_p), ("shs", ctypes.c_void_p)]
+
+
+class ges_adam_params(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float * 6), ("lr_sh_rest", ctypes.c_float), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float)]
+
+
+class ges_density_params(ctypes.Structure):
+    _fields_ = [("grad_threshold", ctypes.c_float), ("percent_dense", ctypes.c_float),
+                ("scene_extent", ctypes.c_float), ("min_opacity", ctypes.c_float), ("min_beta", ctypes.c_float),
+                ("max_world_size", ctypes.c_float)]
+
+
 def _load():
     if not os.path.exists(_LIB_PATH):
         raise ImportError(f"libges is not built ({_LIB_PATH} missing); run __graft_entry__.build()")
@@ -103,6 +126,15 @@ def _load():
         "ges_freq_mask": ([P, P, i32, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float, P, P], i32),
         "ges_image_loss": ([P, P, P, P, i32, i32, ctypes.c_float, ctypes.c_float, P, P, P], i32),
         "ges_render_fwd_noalloc": ([P, P, P, P, P, P, P], i32),
+        "ges_adam_params_default": ([P], i32),
+        "ges_density_params_default": ([P], i32),
+        "ges_position_lr": ([i64, ctypes.c_float, ctypes.c_float, ctypes.c_float, i64, i64, P], i32),
+        "ges_adam_step": ([P, P, P, P, P, i64, P], i32),
+        "ges_activate": ([P, P, P, P], i32),
+        "ges_densify_stats": ([P, P, P, P], i32),
+        "ges_density_control": ([P, P, P, P, P, P, P, P, P], i32),
+        "ges_reset_opacity": ([P, P, ctypes.c_float, P], i32),
+        "ges_reset_shape": ([P, P, ctypes.c_float, P], i32),
         "ges_serve_create": ([P, P, i32, P], i32),
         "ges_serve_add_scene": ([P, P, P], i32),
         "ges_serve_submit": ([P, i32, P, P, P], i32),
@@ -298,6 +330,83 @@ def ges_image_loss(ctx: int, img, gt, mask, width: int, height: int, loss, dL_di
     """loss[4] = (L, L1, SSIM, L_omega) and dL_dimg [3,H,W] (device tensors)."""
     _check(_lib.ges_image_loss(ctx, _addr(img), _addr(gt), _addr(mask), width, height, lambda_ssim, lambda_omega,
                                _addr(loss), _addr(dL_dimg), _stream(stream)))
+
+
+# ------------------------------------------------------------------ training-side updates
+TRAIN_GROUPS = ("means", "scales", "quats", "betas", "opacities", "shs")
+
+
+def make_train_set(n: int, sh_degree: int, params, m, v) -> ges_train_set:
+    """From three sequences of six device tensors (the optimizer's variables and their moments, in
+    the group order of TRAIN_GROUPS)."""
+    t = ges_train_set()
+    t.n, t.sh_degree = int(n), int(sh_degree)
+    for g in range(6):
+        t.param[g], t.m[g], t.v[g] = _addr(params[g]), _addr(m[g]), _addr(v[g])
+    return t
+
+
+def make_scene_out(means, scales, quats, betas, opacities, shs) -> ges_scene_out:
+    o = ges_scene_out()
+    o.means, o.scales, o.quats = _addr(means), _addr(scales), _addr(quats)
+    o.betas, o.opacities, o.shs = _addr(betas), _addr(opacities), _addr(shs)
+    return o
+
+
+def adam_params_default() -> ges_adam_params:
+    p = ges_adam_params()
+    _check(_lib.ges_adam_params_default(ctypes.byref(p)))
+    return p
+
+
+def density_params_default(**kw) -> ges_density_params:
+    p = ges_density_params()
+    _check(_lib.ges_density_params_default(ctypes.byref(p)))
+    for k, val in kw.items():
+        setattr(p, k, val)
+    return p
+
+
+def ges_position_lr(step: int, lr_init: float = 1.6e-4, lr_final: float = 1.6e-6, delay_mult: float = 0.01,
+                    delay_steps: int = 0, max_steps: int = 30000) -> float:
+    out = ctypes.c_float()
+    _check(_lib.ges_position_lr(step, lr_init, lr_final, delay_mult, delay_steps, max_steps, ctypes.byref(out)))
+    return out.value
+
+
+def ges_adam_step(ctx: int, tset: ges_train_set, grads: ges_grads, phys: ges_scene_out, hp: ges_adam_params,
+                  step: int, stream=None) -> None:
+    _check(_lib.ges_adam_step(ctx, ctypes.byref(tset), ctypes.byref(grads), ctypes.byref(phys), ctypes.byref(hp),
+                              step, _stream(stream)))
+
+
+def ges_activate(ctx: int, tset: ges_train_set, phys: ges_scene_out, stream=None) -> None:
+    _check(_lib.ges_activate(ctx, ctypes.byref(tset), ctypes.byref(phys), _stream(stream)))
+
+
+def ges_densify_stats(frame: int, grad_accum, count, stream=None) -> None:
+    _check(_lib.ges_densify_stats(frame, _addr(grad_accum), _addr(count), _stream(stream)))
+
+
+def ges_density_control(ctx: int, tin: ges_train_set, grad_accum, count, xi, dp: ges_density_params,
+                        tout: ges_train_set, stream=None) -> int:
+    """Rows written to tout (raises GesError with status GES_ERR_CAPACITY if tout is too small)."""
+    n_out = ctypes.c_int64(0)
+    st = _lib.ges_density_control(ctx, ctypes.byref(tin), _addr(grad_accum), _addr(count), _addr(xi),
+                                  ctypes.byref(dp), ctypes.byref(tout), ctypes.byref(n_out), _stream(stream))
+    if st != GES_OK:
+        err = GesError(st, last_error())
+        err.n_out = n_out.value
+        raise err
+    return n_out.value
+
+
+def ges_reset_opacity(ctx: int, tset: ges_train_set, max_opacity: float = 0.01, stream=None) -> None:
+    _check(_lib.ges_reset_opacity(ctx, ctypes.byref(tset), max_opacity, _stream(stream)))
+
+
+def ges_reset_shape(ctx: int, tset: ges_train_set, beta: float = 2.0, stream=None) -> None:
+    _check(_lib.ges_reset_shape(ctx, ctypes.byref(tset), beta, _stream(stream)))
 
 
 def ges_trace_enable(ctx: int, on: bool) -> None:

@@ -226,3 +226,33 @@ def stress_beta2_workload(n: int = 6_000_000, seed: int = 4):
     sc, cam = stress_workload(n, seed)
     sc.betas[:] = 2.0
     return sc, cam
+
+
+def optimizer_workload(n: int, sh_degree: int = 3, seed: int = 7):
+    """The optimizer's state for n primitives, drawn directly in its variables (means, log-scales,
+    quaternions, shapes shifted by -2, opacity logits, SH) with Adam moments of a run in progress,
+    upstream gradients w.r.t. the physical values, and densification statistics.
+
+    Recipe: means U[-1,1]^3; log-scales U[ln 0.001, ln 0.3] (the largest of the three above
+    0.01, the clone/split boundary at extent 1, for about 90% of rows); quaternions N(0,1); shifted
+    shapes U[-1.7, 6] (beta in [0.3, 8]); opacity logits N(0, 2.5) (about 2% below kappa = 0.005);
+    SH N(0, 0.3); first moments N(0, 1e-3), second moments N(0, 1e-3)^2; gradients N(0, 1e-3)
+    (means 1e-4); gradient-norm sums of U{0..10} views at 2e-4 x U[0.5, 2.5] x Exp(1) per view, so
+    that about 30% of the rows pass the 3e-4 densification threshold; split normals N(0,1) [n,2,3].
+    All float32."""
+    rng = np.random.default_rng(seed)
+    f = np.float32
+    nb = (sh_degree + 1) ** 2
+    raw = dict(means=rng.uniform(-1, 1, (n, 3)), scales=rng.uniform(math.log(0.001), math.log(0.3), (n, 3)),
+               quats=rng.normal(0, 1, (n, 4)), betas=rng.uniform(-1.7, 6.0, n), opacities=rng.normal(0, 2.5, n),
+               shs=rng.normal(0, 0.3, (n, nb, 3)))
+    shapes = {k: a.shape for k, a in raw.items()}
+    m = {k: rng.normal(0, 1e-3, s) for k, s in shapes.items()}
+    v = {k: rng.normal(0, 1e-3, s) ** 2 for k, s in shapes.items()}
+    grads = {k: rng.normal(0, 1e-4 if k == "means" else 1e-3, s) for k, s in shapes.items()}
+    count = rng.integers(0, 11, n)
+    accum = rng.exponential(2e-4, n) * count * rng.uniform(0.5, 2.5, n)
+    xi = rng.normal(0, 1, (n, 2, 3))
+    cast = lambda d: {k: a.astype(f) for k, a in d.items()}
+    return dict(raw=cast(raw), m=cast(m), v=cast(v), grads=cast(grads), accum=accum.astype(f),
+                count=count.astype(np.int32), xi=xi.astype(f), sh_degree=sh_degree)

@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -62,3 +63,61 @@ def test_null_arguments_are_rejected_without_touching_a_gpu(lib):
     lib.ges_bin_sort.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     assert lib.ges_bin_sort(None, None) == ges.GES_ERR_INVALID_ARG
     assert b"NULL" in ctypes.cast(lib.ges_last_error(), ctypes.c_char_p).value or True
+
+
+def test_training_struct_layouts_and_defaults(lib):
+    from paper_2402_10128_gb300 import ges
+    assert ctypes.sizeof(ges.ges_train_set) == 8 + 8 + 18 * 8
+    assert ctypes.sizeof(ges.ges_scene_out) == 6 * 8
+    assert ctypes.sizeof(ges.ges_adam_params) == 4 * 10
+    assert ctypes.sizeof(ges.ges_density_params) == 4 * 6
+    hp = ges.adam_params_default()   # App. B.2 (SH rest as in Gaussian splatting)
+    assert list(np.float32(hp.lr)) == list(np.float32([1.6e-4, 0.005, 0.001, 0.001, 0.05, 0.0025]))
+    assert np.float32(hp.lr_sh_rest) == np.float32(0.0025 / 20) and hp.beta1 == np.float32(0.9)
+    assert hp.beta2 == np.float32(0.999) and hp.eps == np.float32(1e-15)
+    dp = ges.density_params_default()
+    assert dp.grad_threshold == np.float32(0.0003) and dp.percent_dense == np.float32(0.01)
+    assert dp.min_opacity == np.float32(0.005)
+
+
+def test_position_lr_matches_the_oracle_schedule(lib):
+    """ges_position_lr is host-only; compared with the oracle's schedule (pinned by its closed forms)."""
+    from oracle import train as ot
+    from paper_2402_10128_gb300 import ges
+    for step in (0, 1, 500, 7500, 15000, 29999, 30000, 45000):
+        for delay in (0, 1000):
+            got = ges.ges_position_lr(step, delay_steps=delay)
+            assert got == pytest.approx(ot.position_lr(step, delay_steps=delay), rel=1e-6)
+    with pytest.raises(ges.GesError):
+        ges.ges_position_lr(10, max_steps=0)
+
+
+def test_training_calls_validate_on_the_host(lib):
+    """NULL and misaligned pointers are refused before any device work."""
+    from paper_2402_10128_gb300 import ges
+    fake = ctypes.create_string_buffer(64)           # never dereferenced: validation fails first
+    buf = ctypes.create_string_buffer(4096)
+    base = (ctypes.addressof(buf) + 15) & ~15
+    arrs = [base + 256 * k for k in range(6)]
+    ts = ges.make_train_set(10, 0, arrs, arrs, [a + 4 for a in arrs])   # v misaligned
+    ph = ges.make_scene_out(*arrs)
+    gr = ges.ges_grads(*arrs)
+    hp = ges.adam_params_default()
+    st = lib.ges_adam_step(ctypes.addressof(fake), ctypes.byref(ts), ctypes.byref(gr), ctypes.byref(ph),
+                           ctypes.byref(hp), 1, None)
+    assert st == ges.GES_ERR_INVALID_ARG and "aligned" in ges.last_error()
+    ts = ges.make_train_set(10, 0, arrs, arrs, arrs)
+    st = lib.ges_adam_step(ctypes.addressof(fake), ctypes.byref(ts), ctypes.byref(gr), ctypes.byref(ph),
+                           ctypes.byref(hp), 0, None)
+    assert st == ges.GES_ERR_INVALID_ARG and "step" in ges.last_error()
+    ts = ges.make_train_set(10, 4, arrs, arrs, arrs)
+    st = lib.ges_activate(ctypes.addressof(fake), ctypes.byref(ts), ctypes.byref(ph), None)
+    assert st == ges.GES_ERR_INVALID_ARG and "sh_degree" in ges.last_error()
+    assert lib.ges_reset_opacity(ctypes.addressof(fake), ctypes.byref(ts), ctypes.c_float(1.5), None) == \
+        ges.GES_ERR_INVALID_ARG
+    dp = ges.density_params_default(scene_extent=0.0)
+    n_out = ctypes.c_int64()
+    ts = ges.make_train_set(10, 0, arrs, arrs, arrs)
+    st = lib.ges_density_control(ctypes.addressof(fake), ctypes.byref(ts), arrs[0], arrs[0], arrs[0],
+                                 ctypes.byref(dp), ctypes.byref(ts), ctypes.byref(n_out), None)
+    assert st == ges.GES_ERR_INVALID_ARG
