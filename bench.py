@@ -325,6 +325,8 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the differentiation and stress legs")
+    ap.add_argument("--extra", default="image_loss,differentiation,scale_modification,training,stress,stress_beta2",
+                    help="comma-separated extra legs to run (default: all)")
     ap.add_argument("--segment-tiles", type=int, default=16, help="binning granularity (ges_params.segment_tiles)")
     ap.add_argument("--profile", action="store_true",
                     help="minimal run for ncu: no work counters, e2e or CPU baseline; warmup + steps fwd+bwd")
@@ -512,16 +514,23 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sc, cams, args.cpu_pixels, os.cpu_count() or 1)
     if not args.no_extra:
-        out["image_loss"] = loss_bench(50, 3, dev, img)
-        out["differentiation"] = differentiation_bench(20, 3, dev)
-        out["scale_modification"] = scale_modification_bench(10, 3, dev, sc, t, cams[0], args.segment_tiles)
+        legs = set(x for x in args.extra.split(",") if x)
+        if "image_loss" in legs:
+            out["image_loss"] = loss_bench(50, 3, dev, img)
+        if "differentiation" in legs:
+            out["differentiation"] = differentiation_bench(20, 3, dev)
+        if "scale_modification" in legs:
+            out["scale_modification"] = scale_modification_bench(10, 3, dev, sc, t, cams[0], args.segment_tiles)
         torch.cuda.empty_cache()
-        out["training"] = training_bench(20, 3, dev, sc, cams, args.segment_tiles)
-        torch.cuda.empty_cache()
-        out["stress"] = stress_bench(5, 3, dev, beta2=False, segment_tiles=256)
-        torch.cuda.empty_cache()
-        out["stress_beta2"] = stress_bench(5, 3, dev, beta2=True, segment_tiles=args.segment_tiles)
-        torch.cuda.empty_cache()
+        if "training" in legs:
+            out["training"] = training_bench(20, 3, dev, sc, cams, args.segment_tiles)
+            torch.cuda.empty_cache()
+        if "stress" in legs:
+            out["stress"] = stress_bench(5, 3, dev, beta2=False, segment_tiles=256)
+            torch.cuda.empty_cache()
+        if "stress_beta2" in legs:
+            out["stress_beta2"] = stress_bench(5, 3, dev, beta2=True, segment_tiles=args.segment_tiles)
+            torch.cuda.empty_cache()
     if not args.no_serve:
         del t, grads
         frame.close()
