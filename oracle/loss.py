@@ -115,4 +115,4 @@ def image_loss(img, gt, mask, lambda_ssim: float = 0.2, lambda_omega: float = 0.
     lam_l1 = 1.0 - lambda_ssim - lambda_omega
     L = lam_l1 * l1 + lambda_ssim * (1.0 - ssim) + lambda_omega * lw
     (g,) = torch.autograd.grad(L, x)
-    return float(L.detach()), g.numpy(), dict(l1=float(l1), ssim=float(ssim.detach()), l_omega=float(lw))
+    return float(L.detach()), g.numpy(), dict(l1=float(l1.detach()), ssim=float(ssim.detach()), l_omega=float(lw.detach()))

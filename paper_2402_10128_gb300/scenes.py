@@ -256,3 +256,24 @@ def optimizer_workload(n: int, sh_degree: int = 3, seed: int = 7):
     cast = lambda d: {k: a.astype(f) for k, a in d.items()}
     return dict(raw=cast(raw), m=cast(m), v=cast(v), grads=cast(grads), accum=accum.astype(f),
                 count=count.astype(np.int32), xi=xi.astype(f), sh_degree=sh_degree)
+
+
+def synthetic_image(width: int, height: int, seed: int = 12):
+    """A [3,H,W] float32 image with the mix of structure the training loss meets in a rendered view:
+    a smooth field (a sum of 12 random low-frequency cosines per channel, amplitude 0.15 around 0.4),
+    40 axis-aligned rectangles with sharp edges (values U[0,1]), and stripes of period 6 px in one
+    band (fine detail).  Values clipped to [0, 1.2]."""
+    rng = np.random.default_rng(seed)
+    y, x = np.mgrid[0:height, 0:width].astype(np.float64)
+    img = np.full((3, height, width), 0.4)
+    for c in range(3):
+        for _ in range(12):
+            fx, fy = rng.uniform(0, 6, 2) * 2 * math.pi
+            img[c] += 0.15 / 12 * 4 * np.cos(fx * x / width + fy * y / height + rng.uniform(0, 2 * math.pi))
+    for _ in range(40):
+        x0, y0 = int(rng.integers(0, width)), int(rng.integers(0, height))
+        w, h = int(rng.integers(4, max(5, width // 6))), int(rng.integers(4, max(5, height // 6)))
+        img[:, y0:y0 + h, x0:x0 + w] = rng.uniform(0, 1, 3)[:, None, None]
+    band = slice(height // 3, height // 3 + max(1, height // 10))
+    img[:, band, :] += 0.2 * (np.sin(2 * math.pi * x[band] / 6.0) > 0)[None]
+    return np.clip(img, 0.0, 1.2).astype(np.float32)
