@@ -361,6 +361,57 @@ ges_status ges_density_control(ges_ctx* ctx, const ges_train_set* in, const floa
 ges_status ges_reset_opacity(ges_ctx* ctx, const ges_train_set* set, float max_opacity, void* stream);
 ges_status ges_reset_shape(ges_ctx* ctx, const ges_train_set* set, float beta, void* stream);
 
+/* The 1D mixture-fitting study (Sec. 3.5; App. A), batched: many independent fits of one model
+   with N components to 1D signals by full-batch Adam on the mean squared error.
+
+   Models (App. A; eps = mix_eps, per component i):
+     GES_MIX_GAUSSIAN  w exp(-(x - mu)^2 / (2 s^2 + eps))
+     GES_MIX_DOG       w [exp(-(x - mu)^2 / (2 s^2 + eps)) - exp(-(x - mu)^2 / (2 s^2 / nu + eps))]
+     GES_MIX_LOG       w (1 - (x - mu)^2 / s^2) exp(-(x - mu)^2 / (2 s^2 + eps))
+     GES_MIX_GEF       w exp(-|x - mu|^beta / (2 s^2 + eps))   (beta learnt per component)
+   Parameters of a run: [rows][N] with rows omega, mu, s (and beta for the GEF); w = |omega| when
+   positive_weights, else omega.  Signals (App. A, width s_w, zero outside (-s_w/2, s_w/2) except
+   the Gaussian): square 1, triangle s_w/2 - |x|, parabolic (s_w/2)^2 - x^2,
+   half sinusoid sin((x + s_w/2) pi / s_w), exponential exp(-|x|), Gaussian exp(-x^2 / (2 s_w^2)). */
+typedef enum ges_mix_model { GES_MIX_GAUSSIAN = 0, GES_MIX_DOG = 1, GES_MIX_LOG = 2, GES_MIX_GEF = 3 } ges_mix_model;
+typedef enum ges_signal_kind {
+  GES_SIGNAL_SQUARE = 0, GES_SIGNAL_TRIANGLE = 1, GES_SIGNAL_PARABOLIC = 2, GES_SIGNAL_HALF_SINUSOID = 3,
+  GES_SIGNAL_EXPONENTIAL = 4, GES_SIGNAL_GAUSSIAN = 5
+} ges_signal_kind;
+
+typedef struct ges_fit1d_params {
+  int32_t model;            /* ges_mix_model (GEF) */
+  int32_t n_components;     /* N, 1..128 (5) */
+  int32_t positive_weights; /* 1 (1) */
+  int32_t epochs;           /* Adam steps, >= 0 (1000) */
+  int32_t precision;        /* arithmetic and array element type: 32 (float) or 64 (double) (32) */
+  double lr, beta1, beta2, adam_eps;  /* Adam (0.01, 0.9, 0.999, 1e-8) */
+  double nu;                /* DoG variance ratio (4) */
+  double mix_eps;           /* the models' eps (1e-8) */
+} ges_fit1d_params;
+
+ges_status ges_fit1d_params_default(ges_fit1d_params* out);
+
+/* x[i] = x0 + (x1 - x0) i / (n_points - 1) and y[i] = the signal at x[i] (device arrays of the
+   given precision, caller-owned).  Stream-ordered.  Errors: GES_ERR_INVALID_ARG for NULL
+   pointers, an unknown kind, n_points < 1, width <= 0 or a precision other than 32/64. */
+ges_status ges_signal1d(ges_ctx* ctx, int32_t kind, double width, int32_t n_points, double x0, double x1,
+                        int32_t precision, void* x, void* y, void* stream);
+
+/* `runs` fits in one launch (one CTA each).  x [n_points] (n_points <= 4096) is shared; run r fits
+   y + r * y_stride (y_stride 0: one target for all).  params [runs][rows][N] holds the initial
+   parameters and receives the final ones; loss_hist [runs][epochs + 1] (optional) the MSE before
+   each step and after the last; final_loss [runs] the MSE after the last step; grad
+   [runs][rows][N] (optional) the MSE's gradient at the final parameters.  A run whose loss stops
+   being finite ends there: its later losses, its parameters and its gradient are NaN (the
+   study's unstable runs).  All arrays on the device in the chosen precision.  Stream-ordered;
+   without loss_hist the history lives in context scratch (calls on one context must then be
+   ordered on one stream).  Errors: GES_ERR_INVALID_ARG for NULL pointers or parameters out of
+   range; GES_ERR_OOM for the scratch. */
+ges_status ges_fit1d(ges_ctx* ctx, const ges_fit1d_params* p, int32_t runs, int32_t n_points, const void* x,
+                     const void* y, int64_t y_stride, void* params, void* loss_hist, void* final_loss, void* grad,
+                     void* stream);
+
 /* Forward render that allocates no device memory (no counterpart in the paper; it exists for
    callers that cannot allocate).  Some callers cannot call cudaMalloc: code running under another
    runtime's memory manager that has already reserved the device's memory for its own pool, or

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libges.so")
-SOURCES = ["preprocess.cu", "sort.cu", "raster.cu", "api.cu", "serve.cu", "noalloc.cu", "loss.cu", "train.cu"]
+SOURCES = ["preprocess.cu", "sort.cu", "raster.cu", "api.cu", "serve.cu", "noalloc.cu", "loss.cu", "train.cu", "mixture1d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 

@@ -44,6 +44,7 @@ EXPORTED = ["ges_last_error", "ges_params_default", "ges_ctx_create", "ges_ctx_d
             "ges_render_fwd_noalloc",
             "ges_adam_params_default", "ges_density_params_default", "ges_position_lr", "ges_adam_step",
             "ges_activate", "ges_densify_stats", "ges_density_control", "ges_reset_opacity", "ges_reset_shape",
+            "ges_fit1d_params_default", "ges_signal1d", "ges_fit1d",
             "ges_serve_create", "ges_serve_add_scene",
             "ges_serve_submit", "ges_serve_poll", "ges_serve_destroy"]
 
@@ -100,6 +101,18 @@ class ges_density_params(ctypes.Structure):
                 ("max_world_size", ctypes.c_float)]
 
 
+class ges_fit1d_params(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("n_components", ctypes.c_int32), ("positive_weights", ctypes.c_int32),
+                ("epochs", ctypes.c_int32), ("precision", ctypes.c_int32), ("lr", ctypes.c_double),
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("adam_eps", ctypes.c_double),
+                ("nu", ctypes.c_double), ("mix_eps", ctypes.c_double)]
+
+
+GES_MIX_GAUSSIAN, GES_MIX_DOG, GES_MIX_LOG, GES_MIX_GEF = 0, 1, 2, 3
+MIX_MODELS = {"gaussian": 0, "dog": 1, "log": 2, "gef": 3}
+SIGNAL_KINDS = {"square": 0, "triangle": 1, "parabolic": 2, "half_sinusoid": 3, "exponential": 4, "gaussian": 5}
+
+
 def _load():
     if not os.path.exists(_LIB_PATH):
         raise ImportError(f"libges is not built ({_LIB_PATH} missing); run __graft_entry__.build()")
@@ -135,6 +148,9 @@ def _load():
         "ges_density_control": ([P, P, P, P, P, P, P, P, P], i32),
         "ges_reset_opacity": ([P, P, ctypes.c_float, P], i32),
         "ges_reset_shape": ([P, P, ctypes.c_float, P], i32),
+        "ges_fit1d_params_default": ([P], i32),
+        "ges_signal1d": ([P, i32, ctypes.c_double, i32, ctypes.c_double, ctypes.c_double, i32, P, P, P], i32),
+        "ges_fit1d": ([P, P, i32, i32, P, P, i64, P, P, P, P, P], i32),
         "ges_serve_create": ([P, P, i32, P], i32),
         "ges_serve_add_scene": ([P, P, P], i32),
         "ges_serve_submit": ([P, i32, P, P, P], i32),
@@ -407,6 +423,32 @@ def ges_reset_opacity(ctx: int, tset: ges_train_set, max_opacity: float = 0.01, 
 
 def ges_reset_shape(ctx: int, tset: ges_train_set, beta: float = 2.0, stream=None) -> None:
     _check(_lib.ges_reset_shape(ctx, ctypes.byref(tset), beta, _stream(stream)))
+
+
+# ------------------------------------------------------------------ 1D mixture fitting
+def fit1d_params_default(**kw) -> ges_fit1d_params:
+    p = ges_fit1d_params()
+    _check(_lib.ges_fit1d_params_default(ctypes.byref(p)))
+    for k, val in kw.items():
+        setattr(p, k, val)
+    return p
+
+
+def ges_signal1d(ctx: int, kind, x, y, width: float = 1.0, x0: float = -1.0, x1: float = 1.0, stream=None) -> None:
+    """x = linspace(x0, x1, len(x)) and y = the signal (device tensors, float32 or float64)."""
+    import torch
+    k = SIGNAL_KINDS[kind] if isinstance(kind, str) else int(kind)
+    prec = 64 if x.dtype == torch.float64 else 32
+    _check(_lib.ges_signal1d(ctx, k, width, x.numel(), x0, x1, prec, _addr(x), _addr(y), _stream(stream)))
+
+
+def ges_fit1d(ctx: int, p: ges_fit1d_params, x, y, params, final_loss, loss_hist=None, grad=None, y_stride=None,
+              stream=None) -> None:
+    """params [runs, rows, N] (in: initial, out: final); y [runs, S] or [S] (shared)."""
+    runs = params.shape[0]
+    stride = y_stride if y_stride is not None else (x.numel() if y.dim() == 2 else 0)
+    _check(_lib.ges_fit1d(ctx, ctypes.byref(p), runs, x.numel(), _addr(x), _addr(y), stride, _addr(params),
+                          _addr(loss_hist), _addr(final_loss), _addr(grad), _stream(stream)))
 
 
 def ges_trace_enable(ctx: int, on: bool) -> None:

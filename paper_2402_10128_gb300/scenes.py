@@ -277,3 +277,14 @@ def synthetic_image(width: int, height: int, seed: int = 12):
     band = slice(height // 3, height // 3 + max(1, height // 10))
     img[:, band, :] += 0.2 * (np.sin(2 * math.pi * x[band] / 6.0) > 0)[None]
     return np.clip(img, 0.0, 1.2).astype(np.float32)
+
+
+def mixture_init(model: str, n_components: int, runs: int, seed: int = 0):
+    """Initial parameters [runs, rows, N] of 1D mixture fits, float64: weights U[0,1], means
+    U[-1,1], scales U[0.05, 0.5], and for the GEF shapes U[1,3] (rows 0..3 in that order)."""
+    rng = np.random.default_rng(seed)
+    rows = [rng.uniform(0, 1, (runs, n_components)), rng.uniform(-1, 1, (runs, n_components)),
+            rng.uniform(0.05, 0.5, (runs, n_components))]
+    if model == "gef":
+        rows.append(rng.uniform(1, 3, (runs, n_components)))
+    return np.stack(rows, axis=1)
