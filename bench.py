@@ -325,7 +325,8 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the differentiation and stress legs")
-    ap.add_argument("--extra", default="image_loss,differentiation,scale_modification,training,stress,stress_beta2",
+    ap.add_argument("--extra", default="image_loss,differentiation,scale_modification,training,mixture_study,stress,"
+                                       "stress_beta2",
                     help="comma-separated extra legs to run (default: all)")
     ap.add_argument("--segment-tiles", type=int, default=16, help="binning granularity (ges_params.segment_tiles)")
     ap.add_argument("--profile", action="store_true",
@@ -522,6 +523,8 @@ def main():
         if "scale_modification" in legs:
             out["scale_modification"] = scale_modification_bench(10, 3, dev, sc, t, cams[0], args.segment_tiles)
         torch.cuda.empty_cache()
+        if "mixture_study" in legs:
+            out["mixture_study"] = mixture_study_bench(dev)
         if "training" in legs:
             out["training"] = training_bench(20, 3, dev, sc, cams, args.segment_tiles)
             torch.cuda.empty_cache()
@@ -757,6 +760,80 @@ def training_bench(steps, warmup, dev, sc, cams, segment_tiles):
                                   "frac": adam_gbs / hbm, "bytes_per_element": 32}},
             "density_control": {"ms": d0.elapsed_time(d1), "rows_in": n, "rows_out": int(n_out),
                                 "views_accumulated": steps + warmup}}
+
+
+def mixture_study_bench(dev, epochs=1000, runs_per=20, n_points=1000, cpu_fits=2):
+    """The 1D mixture study of App. A on the GPU: every model (Gaussian, DoG, LoG, GEF) x N in
+    {2, 5, 8, 10, 15, 20} x positive or unrestricted weights x the six signals x 20 seeded runs
+    (5,760 fits), 1000 full-batch Adam steps each on 1000 samples of [-1, 1], signal width 1.
+    One ges_fit1d launch per (model, N, weight mode) with the 120 runs of the six signals, spread
+    over 8 streams.  Reported: the study's wall time in FP32 and FP64, fits/s, component
+    evaluations/s (forward and gradient passes), and the study's result per model and signal
+    (mean final MSE over the stable runs, and the share of stable runs), as in its figures.
+    cpu_baseline: the oracle (torch FP64 on the host) on `cpu_fits` fits of the same kind."""
+    import time
+    import torch
+    from paper_2402_10128_gb300 import ges, render, scenes
+    ctx = render.default_context(dev.index or 0)
+    models, Ns, signals = ["gaussian", "dog", "log", "gef"], [2, 5, 8, 10, 15, 20], list(ges.SIGNAL_KINDS)
+    out = {}
+    for prec, dtype in ((32, torch.float32), (64, torch.float64)):
+        x = torch.empty(n_points, dtype=dtype, device=dev)
+        ys = torch.empty((len(signals), n_points), dtype=dtype, device=dev)
+        for i, k in enumerate(signals):
+            ges.ges_signal1d(ctx.handle, k, x, ys[i])
+        y = ys.repeat_interleave(runs_per, dim=0).contiguous()          # run r fits signal r // runs_per
+        jobs = []
+        for model in models:
+            for n in Ns:
+                for pos in (1, 0):
+                    p0 = scenes.mixture_init(model, n, len(signals) * runs_per, seed=1000 * n + pos)
+                    prm = torch.as_tensor(p0, dtype=dtype, device=dev).contiguous()
+                    fl = torch.empty(prm.shape[0], dtype=dtype, device=dev)
+                    fp = ges.fit1d_params_default(model=ges.MIX_MODELS[model], n_components=n, positive_weights=pos,
+                                                  epochs=epochs, precision=prec)
+                    jobs.append((model, n, pos, p0, prm, fl, fp))
+        streams = [torch.cuda.Stream(device=dev) for _ in range(8)]
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for j, (model, n, pos, p0, prm, fl, fp) in enumerate(jobs):
+            st = streams[j % len(streams)]
+            st.wait_event(e0)
+            ges.ges_fit1d(ctx.handle, fp, x, y, prm, fl, stream=st.cuda_stream)
+        for st in streams:
+            torch.cuda.current_stream().wait_stream(st)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        fits = sum(j[4].shape[0] for j in jobs)
+        evals = sum(j[4].shape[0] * n_points * j[1] * 2 * (epochs + 1) for j in jobs)
+        res = {}
+        for model, n, pos, p0, prm, fl, fp in jobs:
+            if not pos:
+                continue
+            f = fl.cpu().double().numpy().reshape(len(signals), runs_per)
+            for i, k in enumerate(signals):
+                ok = np.isfinite(f[i])
+                r = res.setdefault(model, {}).setdefault(k, {"N": Ns, "mean_mse": [], "stable": []})
+                r["mean_mse"].append(float(f[i][ok].mean()) if ok.any() else None)
+                r["stable"].append(float(ok.mean()))
+        out["fp%d" % prec] = {"ms": ms, "fits": fits, "fits_per_s": fits / (ms / 1e3),
+                              "component_evals_per_s": evals / (ms / 1e3), "positive_weights_result": res}
+    # the oracle on a bounded sample of the same work
+    from oracle import mixture1d as om
+    xs = np.linspace(-1.0, 1.0, n_points)
+    t0 = time.perf_counter()
+    for r in range(cpu_fits):
+        p0 = scenes.mixture_init("gef", 10, 1, seed=r)[0]
+        om.fit("gef", p0, xs, om.signal("square", xs), epochs)
+    cpu_s = time.perf_counter() - t0
+    out["workload"] = ("1D mixture study: 4 models x N in {2,5,8,10,15,20} x 2 weight modes x 6 signals x 20 runs, "
+                       "1000 Adam steps on 1000 samples")
+    out["cpu_baseline"] = {"value": cpu_fits / cpu_s, "unit": "fits/s", "kind": "oracle",
+                           "cores": torch.get_num_threads(),
+                           "sample": f"{cpu_fits} GEF fits, N = 10, square, {epochs} steps (torch FP64 on the host)"}
+    return out
 
 
 def _time_c_abi_steps(sc, t, cam, params, steps, warmup, dev):

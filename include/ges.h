@@ -404,10 +404,9 @@ ges_status ges_signal1d(ges_ctx* ctx, int32_t kind, double width, int32_t n_poin
    each step and after the last; final_loss [runs] the MSE after the last step; grad
    [runs][rows][N] (optional) the MSE's gradient at the final parameters.  A run whose loss stops
    being finite ends there: its later losses, its parameters and its gradient are NaN (the
-   study's unstable runs).  All arrays on the device in the chosen precision.  Stream-ordered;
-   without loss_hist the history lives in context scratch (calls on one context must then be
-   ordered on one stream).  Errors: GES_ERR_INVALID_ARG for NULL pointers or parameters out of
-   range; GES_ERR_OOM for the scratch. */
+   study's unstable runs).  All arrays on the device in the chosen precision.  Stream-ordered; the
+   call keeps no state, so calls may run concurrently on several streams.  Errors:
+   GES_ERR_INVALID_ARG for NULL pointers or parameters out of range. */
 ges_status ges_fit1d(ges_ctx* ctx, const ges_fit1d_params* p, int32_t runs, int32_t n_points, const void* x,
                      const void* y, int64_t y_stride, void* params, void* loss_hist, void* final_loss, void* grad,
                      void* stream);

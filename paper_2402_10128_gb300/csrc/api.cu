@@ -231,7 +231,7 @@ TraceScope::~TraceScope() {
   }
 }
 
-// grow-only scratch of the context, one buffer per slot (0 mask, 1 loss, 2 density control, 3 1D fits)
+// grow-only scratch of the context, one buffer per slot (0 mask, 1 loss, 2 density control)
 ges_status ctx_scratch(ges_ctx* ctx, int slot, size_t bytes, void** out) {
   std::lock_guard<std::mutex> lk(ctx->scratch_mu);
   if (ctx->scratch_bytes[slot] < bytes) {

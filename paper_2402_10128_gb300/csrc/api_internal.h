@@ -15,7 +15,7 @@ struct ges_trace_rec {
   cudaEvent_t a, b;
 };
 
-constexpr int kScratchSlots = 4;  // 0 mask, 1 image loss, 2 density control, 3 1D fit losses
+constexpr int kScratchSlots = 3;  // 0 mask, 1 image loss, 2 density control
 
 struct ges_ctx {
   int device = 0;

@@ -34,15 +34,26 @@ struct FitArgs {
   void* grad;
 };
 
+// In float the fits use the hardware's exp2 / log2 and multiply by reciprocals (the study's float
+// runs are not reproducible to the last bit anyway); in double they use the library's exp, log,
+// pow and true divisions, to follow the FP64 oracle as closely as rounding allows.
 template <class T> __device__ __forceinline__ T t_exp(T v);
-template <> __device__ __forceinline__ float t_exp<float>(float v) { return expf(v); }
+template <> __device__ __forceinline__ float t_exp<float>(float v) { return exp2f(v * 1.4426950408889634f); }
 template <> __device__ __forceinline__ double t_exp<double>(double v) { return exp(v); }
 template <class T> __device__ __forceinline__ T t_log(T v);
-template <> __device__ __forceinline__ float t_log<float>(float v) { return logf(v); }
+template <> __device__ __forceinline__ float t_log<float>(float v) { return __log2f(v) * 0.6931471805599453f; }
 template <> __device__ __forceinline__ double t_log<double>(double v) { return log(v); }
 template <class T> __device__ __forceinline__ T t_pow(T a, T b);  // a >= 0
-template <> __device__ __forceinline__ float t_pow<float>(float a, float b) { return powf(a, b); }
+template <> __device__ __forceinline__ float t_pow<float>(float a, float b) { return exp2f(b * __log2f(a)); }
 template <> __device__ __forceinline__ double t_pow<double>(double a, double b) { return pow(a, b); }
+// a / b, with ib = 1 / b precomputed: a multiplication in float, the division in double
+template <class T> __device__ __forceinline__ T t_div(T a, T b, T ib);
+template <> __device__ __forceinline__ float t_div<float>(float a, float, float ib) { return a * ib; }
+template <> __device__ __forceinline__ double t_div<double>(double a, double b, double) { return a / b; }
+// a / b without a precomputed reciprocal: the fast approximate division in float
+template <class T> __device__ __forceinline__ T t_fdiv(T a, T b);
+template <> __device__ __forceinline__ float t_fdiv<float>(float a, float b) { return __fdividef(a, b); }
+template <> __device__ __forceinline__ double t_fdiv<double>(double a, double b) { return a / b; }
 template <class T> __device__ __forceinline__ T t_sqrt(T v);
 template <> __device__ __forceinline__ float t_sqrt<float>(float v) { return sqrtf(v); }
 template <> __device__ __forceinline__ double t_sqrt<double>(double v) { return sqrt(v); }
@@ -57,6 +68,9 @@ struct Comp {  // per-component constants of an epoch
   T w, dw;     // weight and d w / d omega
   T mu, s, beta;
   T D1, D2;    // 2 s^2 + eps; DoG: 2 s^2 / nu + eps
+  T iD1, iD2;  // their reciprocals
+  T s2, is2, is3;  // s^2, 1 / s^2 and 1 / s^3 (LoG)
+  T s4nu;      // 4 s / nu (DoG)
   T nu;
 };
 
@@ -64,11 +78,12 @@ struct Comp {  // per-component constants of an epoch
 template <class T, int M>
 __device__ __forceinline__ T comp_value(const Comp<T>& c, T x) {
   const T d = x - c.mu;
-  if (M == 0) return c.w * t_exp<T>(-(d * d) / c.D1);
-  if (M == 1) return c.w * (t_exp<T>(-(d * d) / c.D1) - t_exp<T>(-(d * d) / c.D2));
-  if (M == 2) return c.w * ((T(1) - (d * d) / (c.s * c.s)) * t_exp<T>(-(d * d) / c.D1));
+  const T d2 = d * d;
+  if (M == 0) return c.w * t_exp<T>(-t_div<T>(d2, c.D1, c.iD1));
+  if (M == 1) return c.w * (t_exp<T>(-t_div<T>(d2, c.D1, c.iD1)) - t_exp<T>(-t_div<T>(d2, c.D2, c.iD2)));
+  if (M == 2) return c.w * ((T(1) - t_div<T>(d2, c.s2, c.is2)) * t_exp<T>(-t_div<T>(d2, c.D1, c.iD1)));
   const T a = d < T(0) ? -d : d;
-  return c.w * t_exp<T>(-t_pow<T>(a, c.beta) / c.D1);
+  return c.w * t_exp<T>(-t_div<T>(t_pow<T>(a, c.beta), c.D1, c.iD1));
 }
 
 // adds r * d(component)/d(omega, mu, sigma[, beta]) at x to g[0..rows)
@@ -77,32 +92,37 @@ __device__ __forceinline__ void comp_grad(const Comp<T>& c, T x, T r, T* g) {
   const T d = x - c.mu;
   const T d2 = d * d;
   if (M == 0) {
-    const T e = t_exp<T>(-d2 / c.D1);
-    g[0] += r * e * c.dw;
-    g[1] += r * c.w * e * (T(2) * d / c.D1);
-    g[2] += r * c.w * e * d2 * (T(4) * c.s) / (c.D1 * c.D1);
+    const T e = t_exp<T>(-t_div<T>(d2, c.D1, c.iD1));
+    const T re = r * e;
+    g[0] += re * c.dw;
+    g[1] += re * c.w * t_div<T>(T(2) * d, c.D1, c.iD1);
+    g[2] += re * c.w * t_div<T>(d2 * (T(4) * c.s), c.D1 * c.D1, c.iD1 * c.iD1);
   } else if (M == 1) {
-    const T e1 = t_exp<T>(-d2 / c.D1), e2 = t_exp<T>(-d2 / c.D2);
+    const T e1 = t_exp<T>(-t_div<T>(d2, c.D1, c.iD1)), e2 = t_exp<T>(-t_div<T>(d2, c.D2, c.iD2));
     g[0] += r * (e1 - e2) * c.dw;
-    g[1] += r * c.w * (e1 * (T(2) * d / c.D1) - e2 * (T(2) * d / c.D2));
-    g[2] += r * c.w * d2 * (e1 * (T(4) * c.s) / (c.D1 * c.D1) - e2 * (T(4) * c.s / c.nu) / (c.D2 * c.D2));
+    g[1] += r * c.w * (e1 * t_div<T>(T(2) * d, c.D1, c.iD1) - e2 * t_div<T>(T(2) * d, c.D2, c.iD2));
+    g[2] += r * c.w * d2 *
+            (e1 * t_div<T>(T(4) * c.s, c.D1 * c.D1, c.iD1 * c.iD1) -
+             e2 * t_div<T>(c.s4nu, c.D2 * c.D2, c.iD2 * c.iD2));
   } else if (M == 2) {
-    const T e = t_exp<T>(-d2 / c.D1);
-    const T s2 = c.s * c.s;
-    const T u = T(1) - d2 / s2;
-    g[0] += r * u * e * c.dw;
-    g[1] += r * c.w * e * (T(2) * d / s2 + u * (T(2) * d / c.D1));
-    g[2] += r * c.w * e * d2 * (T(2) / (s2 * c.s) + u * (T(4) * c.s) / (c.D1 * c.D1));
+    const T e = t_exp<T>(-t_div<T>(d2, c.D1, c.iD1));
+    const T u = T(1) - t_div<T>(d2, c.s2, c.is2);
+    const T re = r * e;
+    g[0] += re * u * c.dw;
+    g[1] += re * c.w * (t_div<T>(T(2) * d, c.s2, c.is2) + u * t_div<T>(T(2) * d, c.D1, c.iD1));
+    g[2] += re * c.w * d2 *
+            (t_div<T>(T(2), c.s2 * c.s, c.is3) + u * t_div<T>(T(4) * c.s, c.D1 * c.D1, c.iD1 * c.iD1));
   } else {
     const T a = d < T(0) ? -d : d;
     const T p = t_pow<T>(a, c.beta);
-    const T e = t_exp<T>(-p / c.D1);
-    g[0] += r * e * c.dw;
+    const T e = t_exp<T>(-t_div<T>(p, c.D1, c.iD1));
+    const T re = r * e;
+    g[0] += re * c.dw;
     if (a > T(0)) {  // at a = 0 the mean and shape derivatives are taken as 0 (|.|^beta has no slope there)
-      g[1] += r * c.w * e * c.beta * (p / a) * t_sign<T>(d) / c.D1;
-      g[3] += r * c.w * e * (-p * t_log<T>(a) / c.D1);
+      g[1] += re * c.w * t_div<T>(c.beta * t_fdiv<T>(p, a) * t_sign<T>(d), c.D1, c.iD1);
+      g[3] += re * c.w * t_div<T>(-p * t_log<T>(a), c.D1, c.iD1);
     }
-    g[2] += r * c.w * e * p * (T(4) * c.s) / (c.D1 * c.D1);
+    g[2] += re * c.w * t_div<T>(p * (T(4) * c.s), c.D1 * c.D1, c.iD1 * c.iD1);
   }
 }
 
@@ -171,6 +191,7 @@ __global__ void __launch_bounds__(kFitThreads) k_fit1d(const __grid_constant__ F
   const T eps = T(A.mix_eps), nu = T(A.nu), b1 = T(A.b1), b2 = T(A.b2), aeps = T(A.adam_eps);
   T* hist = A.loss_hist ? static_cast<T*>(A.loss_hist) + (int64_t)run * (A.epochs + 1) : nullptr;
   bool dead = false;
+  T last_loss = T(0);
   __syncthreads();
   for (int ep = 0; ep <= A.epochs; ++ep) {
     // (a) per-component constants
@@ -184,6 +205,12 @@ __global__ void __launch_bounds__(kFitThreads) k_fit1d(const __grid_constant__ F
       c.beta = rows > 3 ? sh.p[3 * n + i] : T(2);
       c.D1 = T(2) * c.s * c.s + eps;
       c.D2 = T(2) * (c.s * c.s / nu) + eps;
+      c.iD1 = T(1) / c.D1;
+      c.iD2 = T(1) / c.D2;
+      c.s2 = c.s * c.s;
+      c.is2 = T(1) / c.s2;
+      c.is3 = c.is2 / c.s;
+      c.s4nu = T(4) * c.s / nu;
       c.nu = nu;
       sh.c[i] = c;
     }
@@ -200,8 +227,11 @@ __global__ void __launch_bounds__(kFitThreads) k_fit1d(const __grid_constant__ F
     }
     const T loss = block_sum<T>(ls, sh.red) / T(S);
     if (threadIdx.x == 0 && hist) hist[ep] = loss;
+    last_loss = loss;
     if (!t_finite<T>(loss)) {
       dead = true;
+      if (threadIdx.x == 0 && hist)
+        for (int e2 = ep + 1; e2 <= A.epochs; ++e2) hist[e2] = T(NAN);
       break;
     }
     const bool last = ep == A.epochs;
@@ -240,17 +270,10 @@ __global__ void __launch_bounds__(kFitThreads) k_fit1d(const __grid_constant__ F
     }
     __syncthreads();
   }
-  if (dead && threadIdx.x == 0 && hist) {
-    for (int ep = 0; ep <= A.epochs; ++ep)
-      if (!t_finite<T>(hist[ep])) {
-        for (int e2 = ep + 1; e2 <= A.epochs; ++e2) hist[e2] = T(NAN);
-        break;
-      }
-  }
   if (dead && A.grad)
     for (int j = threadIdx.x; j < P; j += blockDim.x) static_cast<T*>(A.grad)[(int64_t)run * P + j] = T(NAN);
   for (int j = threadIdx.x; j < P; j += blockDim.x) gp[j] = dead ? T(NAN) : sh.p[j];
-  if (threadIdx.x == 0) static_cast<T*>(A.final_loss)[run] = dead ? T(NAN) : (hist ? hist[A.epochs] : T(0));
+  if (threadIdx.x == 0) static_cast<T*>(A.final_loss)[run] = dead ? T(NAN) : last_loss;
 }
 
 template <class T>
@@ -375,16 +398,8 @@ ges_status ges_fit1d(ges_ctx* ctx, const ges_fit1d_params* p, int32_t runs, int3
   A.params = params;
   A.final_loss = final_loss;
   A.grad = grad;
+  A.loss_hist = loss_hist;
   cudaStream_t s = (cudaStream_t)stream;
-  // without a caller history the kernel keeps one in context scratch (it reads the last entry)
-  const size_t esz = p->precision == 32 ? 4 : 8;
-  if (loss_hist) {
-    A.loss_hist = loss_hist;
-  } else {
-    void* buf = nullptr;
-    if ((st = ctx_scratch(ctx, 3, esz * (size_t)runs * (size_t)(p->epochs + 1), &buf)) != GES_OK) return st;
-    A.loss_hist = buf;
-  }
   cudaError_t e;
   {
     TraceScope tr(ctx, "k_fit1d", s);
