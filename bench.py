@@ -199,10 +199,31 @@ def cpu_baseline(sc, cams, pixels, cores):
     t0 = time.perf_counter()
     oracle.backward(sc, cam, g, pixels=pix, nthreads=cores)
     dt = time.perf_counter() - t0
+    # one thread on a smaller sample; the tiled FP64 renderer (the same algorithm as the GPU) on a
+    # whole frame (fwd); the small 128x128 case end to end (fwd + bwd, brute force)
+    from paper_2402_10128_gb300 import scenes
+    n1 = max(1, pixels // 50)
+    t0 = time.perf_counter()
+    oracle.backward(sc, cam, g[:, :n1], pixels=pix[:n1], nthreads=1)
+    dt1 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.render(sc, cam, tiled=True, nthreads=cores)
+    dtt = time.perf_counter() - t0
+    tsc, tcam = scenes.tiny_workload()
+    t0 = time.perf_counter()
+    tref = oracle.render(tsc, tcam, nthreads=cores)
+    oracle.backward(tsc, tcam, np.ones_like(tref["img"]), nthreads=cores)
+    dts = time.perf_counter() - t0
     return {"value": pixels / dt / 1e6, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
             "seconds": dt,
             "sample": f"{pixels} uniformly random pixels of one 1245x825 view of the 1.5M-primitive scene, "
-                      f"fwd+bwd (FP64 brute force over all primitives); Mpix/s extrapolated from the sampled pixels"}
+                      f"fwd+bwd (FP64 brute force over all primitives); Mpix/s extrapolated from the sampled pixels",
+            "one_thread": {"value": n1 / dt1 / 1e6, "unit": "Mpix/s", "sample": f"{n1} of the same pixels, fwd+bwd"},
+            "tiled_full_frame_fwd": {"value": cam.width * cam.height / dtt / 1e6, "unit": "Mpix/s", "seconds": dtt,
+                                     "sample": "the whole view, the oracle's tiled FP64 renderer (tile lists from its "
+                                               "key module), forward"},
+            "small_case_fwd_bwd_s": {"value": dts, "unit": "s",
+                                     "sample": "the 2,000-primitive 128x128 case end to end, brute force fwd + bwd"}}
 
 
 def serving_bench(n_requests, rate_mults, slots, dev, seed=40):
