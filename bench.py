@@ -665,13 +665,25 @@ def loss_bench(steps, warmup, dev, img):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     px = W * H
     b_mask, b_loss = px * (12 + 1), px * (12 + 12 + 1 + 12)
+    # the oracle (FP64, numpy / torch on the host) on the same images, once each
+    from oracle import loss as ol
+    gt_h, img_h = gt.cpu().numpy().astype(np.float64), img.cpu().numpy().astype(np.float64)
+    t0 = time.perf_counter()
+    m_ref, _ = ol.freq_mask(gt_h, 0.7, 0.2)
+    t_mask = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ol.image_loss(img_h, gt_h, m_ref)
+    t_loss = time.perf_counter() - t0
     return {"workload": "training image loss of the rendered 1245x825 view: frequency mask (omega 0.7, scale 0.2) "
                         "and L = 0.3 L1 + 0.2 (1 - SSIM) + 0.5 L_omega with dL/dI",
             "mask_ms": ms_mask, "loss_ms": ms_loss, "loss": [float(v) for v in loss.cpu()],
             "roofline": {"bound": "hbm", "unit": "GB/s", "peak": hbm,
                          "mask_achieved": b_mask / (ms_mask / 1e3) / 1e9, "mask_frac": b_mask / (ms_mask / 1e3) / 1e9 / hbm,
                          "loss_achieved": b_loss / (ms_loss / 1e3) / 1e9, "loss_frac": b_loss / (ms_loss / 1e3) / 1e9 / hbm,
-                         "bytes_per_pixel": {"mask": 13, "loss": 37}}}
+                         "bytes_per_pixel": {"mask": 13, "loss": 37}},
+            "cpu_baseline": {"kind": "oracle", "mask_ms": t_mask * 1e3, "loss_ms": t_loss * 1e3,
+                             "cores": torch.get_num_threads(),
+                             "sample": "the same 1245x825 images once: oracle.loss.freq_mask and image_loss (FP64)"}}
 
 
 def training_bench(steps, warmup, dev, sc, cams, segment_tiles):
@@ -772,6 +784,19 @@ def training_bench(steps, warmup, dev, sc, cams, segment_tiles):
     n_out = ges.ges_density_control(ctx.handle, tset, acc, cnt, xi, dp, tout)
     d1.record()
     torch.cuda.synchronize()
+    # the oracle's Adam step and density control (numpy FP64 on the host) on the same state
+    from oracle import train as ot
+    names = ("means", "scales", "quats", "betas", "opacities", "shs")
+    r_h = {k: a.cpu().double().numpy() for k, a in zip(names, raw)}
+    m_h = {k: a.cpu().double().numpy() for k, a in zip(names, mom)}
+    v_h = {k: a.cpu().double().numpy() for k, a in zip(names, vel)}
+    g_h = {k: a.cpu().double().numpy() for k, a in zip(names, grads)}
+    t0 = time.perf_counter()
+    ot.adam_step(r_h, m_h, v_h, g_h, steps + warmup + 1)
+    t_adam = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ot.density_control(r_h, m_h, v_h, acc.cpu().numpy(), cnt.cpu().numpy(), xi.cpu().double().numpy())
+    t_dens = time.perf_counter() - t0
     return {"workload": "training iteration: scene-scale, 1.5M primitives, SH3, 1245x825, 20 views; fwd + frequency "
                         "mask + image loss + bwd + densification statistics + Adam over all primitives",
             "steps": steps, "ms_per_step": ms, "iterations_per_s": 1e3 / ms,
@@ -780,7 +805,11 @@ def training_bench(steps, warmup, dev, sc, cams, segment_tiles):
                      "roofline": {"bound": "hbm", "achieved": adam_gbs, "peak": hbm, "unit": "GB/s",
                                   "frac": adam_gbs / hbm, "bytes_per_element": 32}},
             "density_control": {"ms": d0.elapsed_time(d1), "rows_in": n, "rows_out": int(n_out),
-                                "views_accumulated": steps + warmup}}
+                                "views_accumulated": steps + warmup},
+            "cpu_baseline": {"kind": "oracle", "adam_ms": t_adam * 1e3, "density_control_ms": t_dens * 1e3,
+                             "cores": torch.get_num_threads(),
+                             "sample": "one Adam step and one density control over the same 1.5M primitives "
+                                       "(oracle.train, numpy FP64)"}}
 
 
 def mixture_study_bench(dev, epochs=1000, runs_per=20, n_points=1000, cpu_fits=2):
@@ -839,8 +868,22 @@ def mixture_study_bench(dev, epochs=1000, runs_per=20, n_points=1000, cpu_fits=2
                 r = res.setdefault(model, {}).setdefault(k, {"N": Ns, "mean_mse": [], "stable": []})
                 r["mean_mse"].append(float(f[i][ok].mean()) if ok.any() else None)
                 r["stable"].append(float(ok.mean()))
-        out["fp%d" % prec] = {"ms": ms, "fits": fits, "fits_per_s": fits / (ms / 1e3),
-                              "component_evals_per_s": evals / (ms / 1e3), "positive_weights_result": res}
+        entry = {"ms": ms, "fits": fits, "fits_per_s": fits / (ms / 1e3),
+                 "component_evals_per_s": evals / (ms / 1e3), "positive_weights_result": res}
+        if prec == 32:
+            # MUFU work per (sample, component, epoch), forward + gradient pass, in SM clocks at the
+            # measured per-SM rates: Gaussian and LoG 2 ex2, DoG 4 ex2, GEF 4 ex2 + 3 lg2 + 1 rcp
+            sfu = sfu_rates()
+            per = sfu.get("per_sm_per_clk", {})
+            ex2, lg2, rcp = per.get("ex2", 31.4), per.get("lg2", 15.9), per.get("rcp", 15.9)
+            clk = {"gaussian": 2 / ex2, "dog": 4 / ex2, "log": 2 / ex2, "gef": 4 / ex2 + 3 / lg2 + 1 / rcp}
+            sm_clk = sum(j[4].shape[0] * n_points * j[1] * (epochs + 1) * clk[j[0]] for j in jobs)
+            t_peak = sm_clk / (sfu.get("sms", 152) * sfu.get("max_clock_mhz", 2070) * 1e6)
+            entry["roofline"] = {"kernel": "k_fit1d", "bound": "alu", "unit": "ms (MUFU-limited time)",
+                                 "peak_time_ms": t_peak * 1e3, "achieved_ms": ms, "frac": t_peak * 1e3 / ms,
+                                 "work": "ex2/lg2/rcp per (sample, component, epoch) by model at the measured MUFU "
+                                         "rates; 152 SMs at the maximum clock"}
+        out["fp%d" % prec] = entry
     # the oracle on a bounded sample of the same work
     from oracle import mixture1d as om
     xs = np.linspace(-1.0, 1.0, n_points)
