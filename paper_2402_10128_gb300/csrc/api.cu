@@ -535,7 +535,7 @@ ges_status ges_bin_sort(ges_frame* f, void* stream) {
   int cur = 0;
   {
     TraceScope tr(f->ctx, "depth_sort", s);
-    if (!radix_sort_pairs(f->dk, f->pv, cur, f->n, nullptr, f->n, 32, f->hist, f->hist_cap, f->scan, s))
+    if (!radix_sort_pairs(f->dk, f->pv, cur, f->n, nullptr, f->n, 32, f->hist, f->hist_cap, f->scan, s, f->d_flags))
       return fail(GES_ERR_CUDA, "internal: depth-sort histogram exceeds its buffer");
   }
   f->sorted_prims = f->pv[cur];
@@ -568,7 +568,8 @@ ges_status ges_bin_sort(ges_frame* f, void* stream) {
   int tcur = 0;
   {
     TraceScope tr(f->ctx, "list_sort", s);
-    if (!radix_sort_pairs(f->tk, f->tv, tcur, 0, f->d_K, f->key_cap, f->P.seg_bits, f->hist, f->hist_cap, f->scan, s))
+    if (!radix_sort_pairs(f->tk, f->tv, tcur, 0, f->d_K, f->key_cap, f->P.seg_bits, f->hist, f->hist_cap, f->scan, s,
+                          f->d_flags))
       return fail(GES_ERR_CUDA, "internal: list-sort histogram exceeds its buffer");
   }
   f->tile_keys = f->tk[tcur];
@@ -654,6 +655,8 @@ ges_status ges_frame_status(ges_frame* f, void* stream, int64_t* num_keys) {
   if (num_keys) *num_keys = (int64_t)K;
   if (flags & kFlagOverflow)
     return fail(GES_ERR_CAPACITY, "K=%llu duplicates exceed key capacity %lld", K, (long long)f->key_cap);
+  if (flags & kFlagSortWait)
+    return fail(GES_ERR_DEVICE_WAIT, "a radix sort's bounded look-back gave up; the frame's lists are invalid");
   return GES_OK;
 }
 

@@ -44,8 +44,13 @@ void launch_gather_touched(const uint32_t* sorted_vals, const uint32_t* tprim, i
 // n_dev (device) if non-null, else n_host; buffers hold n_cap elements.  keys[cur]/vals[cur] hold the
 // input; on return `cur` indexes the sorted output.  hist holds hist_cap entries; returns false,
 // launching nothing, if a pass's histogram would not fit (radix_hist_entries gives the need).
+// With hist_cap >= radix_hist_entries(n_cap, .), a sort of three or four passes runs in one sweep
+// (digit counts in one read, one kernel per pass with a bounded decoupled look-back; a look-back
+// that gives up sets kFlagSortWait in *flags when flags is given), else as hist / scan / scatter
+// per pass.
 bool radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_host, const unsigned long long* n_dev,
-                      int64_t n_cap, int total_bits, uint32_t* hist, int64_t hist_cap, ScanScratch& sc, cudaStream_t s);
+                      int64_t n_cap, int total_bits, uint32_t* hist, int64_t hist_cap, ScanScratch& sc, cudaStream_t s,
+                      uint32_t* flags = nullptr);
 int64_t radix_hist_entries(int64_t n_cap, int max_bits);
 
 // n: primitives (the capacity when n_dev gives the count on the device); touched: tiles per
@@ -62,6 +67,7 @@ void launch_ranges(const uint32_t* tile_keys, const unsigned long long* K_dev, i
                    uint2* ranges, int num_sms, cudaStream_t s);
 
 constexpr uint32_t kFlagOverflow = 1u;
+constexpr uint32_t kFlagSortWait = 2u;  // a radix sort's bounded look-back gave up (results invalid)
 
 // ---- compositing (raster.cu)
 // ranges: per segment; keys, vals: the sorted list (segment key, primitive id).

@@ -24,7 +24,9 @@ namespace {
 constexpr int64_t kNaMaxPrims = 65536;     // primitives
 constexpr int64_t kNaMaxKeys = 1 << 20;    // (tile, primitive) duplicates
 constexpr int64_t kNaMaxTiles = 16384;     // 16x16 tiles (e.g. 2048 x 2048 pixels)
-constexpr int64_t kNaHistEntries = 256 * ((kNaMaxKeys + 4095) / 4096);  // radix histograms, any pass
+// radix-sort scratch of the one-sweep form: counters and digit counts (8 + 4 x 256), two status
+// regions of 256 per 4096-key chunk
+constexpr int64_t kNaHistEntries = 8 + 4 * 256 + 2 * 256 * ((kNaMaxKeys + 4095) / 4096);
 constexpr int64_t kNaScanBytes = 4096;     // multi-level scan scratch for <= 2^20 elements
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -172,14 +174,14 @@ extern "C" ges_status ges_render_fwd_noalloc(const ges_scene* scene, const ges_c
   uint32_t* tprim = at<uint32_t>(b, kL.tprim);
   launch_preprocess<FrameViews>(vt, n, P, depth_key, dk[0], pv[0], rect, rec, ext, tprim, ds->num_sms, s);
   int cur = 0;
-  if (!radix_sort_pairs(dk, pv, cur, n, nullptr, n, 32, hist, kNaHistEntries, scan, s))
+  if (!radix_sort_pairs(dk, pv, cur, n, nullptr, n, 32, hist, kNaHistEntries, scan, s, flags))
     return fail(GES_ERR_CUDA, "internal: depth-sort histogram exceeds its buffer");
   launch_gather_touched(pv[cur], tprim, n, touched, s);
   scan_exclusive<uint32_t, unsigned long long>(touched, offsets, n, dK, scan, s);
   launch_keygen<FrameViews>(vt, offsets, touched, dK, n, pv[cur], rect, ext, rec, P, kNaMaxKeys,
                             tk[0], tv[0], flags, s);
   int tcur = 0;
-  if (!radix_sort_pairs(tk, tv, tcur, 0, dK, kNaMaxKeys, P.seg_bits, hist, kNaHistEntries, scan, s))
+  if (!radix_sort_pairs(tk, tv, tcur, 0, dK, kNaMaxKeys, P.seg_bits, hist, kNaHistEntries, scan, s, flags))
     return fail(GES_ERR_CUDA, "internal: list-sort histogram exceeds its buffer");
   launch_ranges(tk[tcur], dK, kNaMaxKeys, (uint32_t)((1ull << P.seg_bits) - 1), ranges, ds->num_sms, s);
   vt.t.v[0].img = img;
@@ -196,5 +198,6 @@ extern "C" ges_status ges_render_fwd_noalloc(const ges_scene* scene, const ges_c
   if (h_flags & kFlagOverflow)
     return fail(GES_ERR_CAPACITY, "no-alloc render: %llu duplicates exceed the limit of %lld (outputs hold the background only)", h_K,
                 (long long)kNaMaxKeys);
+  if (h_flags & kFlagSortWait) return fail(GES_ERR_DEVICE_WAIT, "no-alloc render: a radix sort's bounded look-back gave up");
   return GES_OK;
 }

@@ -186,13 +186,13 @@ ges_status ws_alloc(ges_server* S, Workspace& w, int64_t P_cap, int64_t T_cap, i
   launch_preprocess<BatchViews>(vs, P_cap, S->P, w.depth_key, w.dk[0], w.pv[0], w.rect, w.rec, w.ext, w.tprim, S->num_sms,
                                 s);
   int cur = 0;
-  bool fits = radix_sort_pairs(w.dk, w.pv, cur, 0, n_dev, P_cap, 32, w.hist, w.hist_cap, w.scan, s);
+  bool fits = radix_sort_pairs(w.dk, w.pv, cur, 0, n_dev, P_cap, 32, w.hist, w.hist_cap, w.scan, s, flags);
   launch_gather_touched(w.pv[cur], w.tprim, P_cap, w.touched, s, n_dev);
   scan_exclusive<uint32_t, unsigned long long>(w.touched, w.offsets, P_cap, dK, w.scan, s, n_dev);
   launch_keygen<BatchViews>(vs, w.offsets, w.touched, dK, P_cap, w.pv[cur], w.rect, w.ext, w.rec, S->P, K_cap,
                             w.tk[0], w.tv[0], flags, s, n_dev);
   int tcur = 0;
-  fits = radix_sort_pairs(w.tk, w.tv, tcur, 0, dK, K_cap, tile_bits, w.hist, w.hist_cap, w.scan, s) && fits;
+  fits = radix_sort_pairs(w.tk, w.tv, tcur, 0, dK, K_cap, tile_bits, w.hist, w.hist_cap, w.scan, s, flags) && fits;
   launch_ranges(w.tk[tcur], dK, K_cap, (uint32_t)((1ull << tile_bits) - 1), w.ranges, S->num_sms, s);
   launch_render_fwd<BatchViews>(vs, T_cap, w.ranges, w.tk[tcur], w.tv[tcur], w.rec, S->P, s, nullptr, counter,
                                 S->num_sms);
@@ -325,9 +325,16 @@ void take_batch(ges_server* S, Workspace& w) {
 // Completes a finished batch (caller does not hold the lock).
 void ws_finish(ges_server* S, Workspace& w) {
   const bool overflow = (w.h_stat[1] & kFlagOverflow) != 0;
+  const bool sort_wait = (w.h_stat[1] & kFlagSortWait) != 0;
   const auto now = Clock::now();
   std::lock_guard<std::mutex> lk(S->mu);
-  if (overflow) {
+  if (sort_wait) {
+    for (Request* r : w.reqs) {
+      r->state = kFailed;
+      r->status = GES_ERR_DEVICE_WAIT;
+      r->err = "a radix sort's bounded look-back gave up";
+    }
+  } else if (overflow) {
     if (w.reqs.size() > 1) {
       for (auto it = w.reqs.rbegin(); it != w.reqs.rend(); ++it) {
         (*it)->solo = true;

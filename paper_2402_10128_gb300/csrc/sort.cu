@@ -273,6 +273,227 @@ __global__ void __launch_bounds__(kScThreads) k_radix_scatter(const uint32_t* __
   }  // chunk loop
 }
 
+// ---------------------------------------------------------------- one-sweep radix sort
+// The same stable LSD sort with one read of the keys for every pass's digit counts and one kernel
+// per pass: a CTA takes the next chunk from a counter (so a chunk's predecessors are always
+// running or done), ranks its elements as k_radix_scatter does, publishes its per-digit counts,
+// and finds the counts of all earlier chunks by a decoupled look-back (Merrill & Garland): a chunk
+// publishes its digit count as an aggregate (flag 1) at once and, when its own prefix is known,
+// the inclusive prefix (flag 2); a successor adds aggregates walking back until it meets a prefix.
+// Status words: flag in bits 30-31, count in bits 0-29 (so at most 2^30 elements).  Two status
+// regions alternate between passes; each pass's CTAs zero their chunk's entries of the other one.
+// Every wait is bounded: a CTA that gives up publishes a prefix of 0, writes nothing, and sets
+// kFlagSortWait in the caller's flags (its successors then finish with wrong offsets but every
+// store is bounds-checked).
+constexpr int kOsMaxPasses = 4;
+constexpr int64_t kOsHeader = 8 + kOsMaxPasses * 256;  // chunk counters per pass, digit counts per pass
+constexpr uint32_t kOsAgg = 1u << 30, kOsPre = 2u << 30, kOsValue = (1u << 30) - 1u;
+constexpr int kOsSpinLimit = 1 << 22;
+
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
+  return *reinterpret_cast<const volatile uint32_t*>(p);
+}
+__device__ __forceinline__ void st_volatile_u32(uint32_t* p, uint32_t v) { *reinterpret_cast<volatile uint32_t*>(p) = v; }
+
+__global__ void __launch_bounds__(kThreads) k_os_counts(const uint32_t* __restrict__ keys, int64_t n_host,
+                                                        const unsigned long long* __restrict__ n_dev, int64_t cap,
+                                                        int passes, int bits_per, int total_bits,
+                                                        uint32_t* __restrict__ counts) {
+  constexpr int kWarps = kThreads / 32;
+  __shared__ uint32_t cnt[kWarps / 2][kOsMaxPasses][256];  // one histogram per warp pair
+  for (int i = threadIdx.x; i < (kWarps / 2) * kOsMaxPasses * 256; i += kThreads) (&cnt[0][0][0])[i] = 0;
+  __syncthreads();
+  const int64_t n = element_count(n_host, n_dev, cap);
+  const int h = (threadIdx.x >> 5) >> 1;
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+    const uint32_t k = keys[i];
+    for (int p = 0; p < passes; ++p) {
+      const int shift = p * bits_per;
+      const int bits = (total_bits - shift) < bits_per ? (total_bits - shift) : bits_per;
+      atomicAdd(&cnt[h][p][(k >> shift) & ((1u << bits) - 1u)], 1u);
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < passes * 256; j += kThreads) {
+    uint32_t t = 0;
+#pragma unroll
+    for (int hh = 0; hh < kWarps / 2; ++hh) t += (&cnt[hh][0][0])[j];
+    if (t) atomicAdd(&counts[j], t);
+  }
+}
+
+__global__ void __launch_bounds__(kScThreads) k_os_scatter(const uint32_t* __restrict__ keys_in,
+                                                         const uint32_t* __restrict__ vals_in,
+                                                         uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+                                                         int64_t n_host, const unsigned long long* __restrict__ n_dev,
+                                                         int64_t cap, int shift, int bits, int pass, int zero_next,
+                                                         uint32_t* __restrict__ os, int64_t nchunks_cap,
+                                                         uint32_t* __restrict__ flags) {
+  constexpr int kWarps = kScThreads / 32;
+  __shared__ __align__(16) uint32_t wcnt[kWarps][256];
+  __shared__ uint32_t goff[256];
+  __shared__ uint32_t dbase[256];
+  __shared__ uint32_t bstart[257];
+  __shared__ uint32_t wsum[kWarps];
+  __shared__ uint32_t skeys[kChunk];
+  __shared__ uint32_t svals[kChunk];
+  __shared__ int64_t s_chunk;
+  __shared__ int s_fail;
+  const int nbins = 1 << bits;
+  const uint32_t mask = (uint32_t)nbins - 1u;
+  const int64_t n = element_count(n_host, n_dev, cap);
+  const int64_t nchunks = (n + kChunk - 1) / kChunk;
+  const int w = threadIdx.x >> 5;
+  const unsigned lane = lane_id();
+  uint32_t* counter = os + pass;
+  const uint32_t* counts = os + 8 + pass * 256;
+  uint32_t* st_cur = os + kOsHeader + (int64_t)(pass & 1) * 256 * nchunks_cap;  // [chunk][digit]
+  uint32_t* st_next = os + kOsHeader + (int64_t)((pass + 1) & 1) * 256 * nchunks_cap;
+  // exclusive digit offsets of this pass (the same in every CTA)
+  if (threadIdx.x < 32) {
+    uint32_t run = 0;
+    for (int b0 = 0; b0 < nbins; b0 += 32) {
+      const int b = b0 + (int)lane;
+      const uint32_t c = b < nbins ? counts[b] : 0u;
+      uint32_t inc = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if ((int)lane >= o) inc += y;
+      }
+      if (b < nbins) dbase[b] = run + inc - c;
+      run += __shfl_sync(0xffffffffu, inc, 31);
+    }
+  }
+  for (;;) {
+    __syncthreads();  // the previous chunk's readers of the shared arrays (and of s_chunk) are done
+    if (threadIdx.x == 0) {
+      s_chunk = (int64_t)atomicAdd(counter, 1u);
+      s_fail = 0;
+    }
+    {
+      uint4* z = reinterpret_cast<uint4*>(&wcnt[0][0]);
+      for (int i = threadIdx.x; i < kWarps * 256 / 4; i += kScThreads) z[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    __syncthreads();
+    const int64_t c = s_chunk;
+    if (c >= nchunks) break;
+    const int64_t base = c * kChunk;
+    const int count = (int)min((int64_t)kChunk, n - base);
+    const unsigned lt_mask = (1u << lane) - 1u;
+    uint32_t key[kScItems], val[kScItems], rank[kScItems];
+#pragma unroll
+    for (int r = 0; r < kScItems; ++r) {
+      const int li = w * (kScItems * 32) + r * 32 + (int)lane;
+      const bool ok = li < count;
+      key[r] = ok ? keys_in[base + li] : 0u;
+      val[r] = ok ? vals_in[base + li] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < kScItems; ++r) {
+      const int li = w * (kScItems * 32) + r * 32 + (int)lane;
+      const bool ok = li < count;
+      const uint32_t d = (key[r] >> shift) & mask;
+      unsigned peers = __ballot_sync(0xffffffffu, ok);
+      for (int b = 0; b < bits; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const unsigned bal = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? bal : ~bal;
+      }
+      const int leader = peers ? __ffs(peers) - 1 : 0;
+      uint32_t prev = 0;
+      if (ok && (int)lane == leader) prev = atomicAdd(&wcnt[w][d], (uint32_t)__popc(peers));
+      prev = __shfl_sync(0xffffffffu, prev, leader);
+      rank[r] = prev + (uint32_t)__popc(peers & lt_mask);
+    }
+    __syncthreads();
+    uint32_t total = 0;
+    if ((int)threadIdx.x < nbins) {
+      const int b = threadIdx.x;
+#pragma unroll
+      for (int ww = 0; ww < kWarps; ++ww) {
+        const uint32_t cw = wcnt[ww][b];
+        wcnt[ww][b] = total;
+        total += cw;
+      }
+      // decoupled look-back for digit b
+      uint32_t* my = st_cur + c * 256 + b;
+      if (zero_next) st_next[c * 256 + b] = 0u;
+      uint32_t prefix = 0;
+      if (c == 0) {
+        st_volatile_u32(my, kOsPre | total);
+      } else {
+        st_volatile_u32(my, kOsAgg | total);
+        int64_t look = c - 1;
+        int spins = 0;
+        for (;;) {
+          const uint32_t v = ld_volatile_u32(st_cur + look * 256 + b);
+          const uint32_t flag = v & ~kOsValue;
+          if (flag == 0u) {
+            if (++spins > kOsSpinLimit) {
+              s_fail = 1;
+              prefix = 0;
+              break;
+            }
+            __nanosleep(32);
+            continue;
+          }
+          prefix += v & kOsValue;
+          if (flag == kOsPre || look == 0) break;
+          --look;
+        }
+        st_volatile_u32(my, kOsPre | ((prefix + total) & kOsValue));
+      }
+      goff[b] = dbase[b] + prefix;
+    }
+    // exclusive scan of the digit totals over the CTA (thread b holds digit b)
+    uint32_t inc = total;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if ((int)lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t run = 0;
+      for (int ww = 0; ww < kWarps; ++ww) {
+        const uint32_t cc = wsum[ww];
+        wsum[ww] = run;
+        run += cc;
+      }
+      if (s_fail && flags) atomicOr(flags, kFlagSortWait);
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nbins) bstart[threadIdx.x] = wsum[w] + inc - total;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kScItems; ++r) {
+      const int li = w * (kScItems * 32) + r * 32 + (int)lane;
+      if (li < count) {
+        const int d = (int)((key[r] >> shift) & mask);
+        const uint32_t pos = bstart[d] + wcnt[w][d] + rank[r];
+        skeys[pos] = key[r];
+        svals[pos] = val[r];
+      }
+    }
+    __syncthreads();
+    if (!s_fail) {
+      for (int i = threadIdx.x; i < count; i += kScThreads) {
+        const uint32_t k = skeys[i];
+        const int d = (int)((k >> shift) & mask);
+        const int64_t gpos = (int64_t)goff[d] + ((uint32_t)i - bstart[d]);
+        if (gpos < n) {
+          keys_out[gpos] = k;
+          vals_out[gpos] = svals[i];
+        } else if (flags) {
+          atomicOr(flags, kFlagSortWait);
+        }
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------- K2 input
 // touched[j] for j < count: the tile count of the j-th primitive in depth order (count = the
 // device count n_dev when given, else len)
@@ -496,19 +717,41 @@ void launch_gather_touched(const uint32_t* sorted_vals, const uint32_t* tprim, i
   count_launches(1);
 }
 
-// histogram entries that a sort of n_cap keys on up to max_bits bits may need in one pass: the
-// digit of a pass is at most 8 bits wide (and at most max_bits)
+// scratch entries (uint32) of a sort of n_cap keys: the one-sweep layout (counters, digit counts,
+// two status regions of 256 per chunk), which also holds the per-pass histogram of the classic
+// form (at most 8-bit digits: 256 per chunk)
 int64_t radix_hist_entries(int64_t n_cap, int max_bits) {
-  const int bits = max_bits < 1 ? 1 : (max_bits > 8 ? 8 : max_bits);
-  return ((int64_t)1 << bits) * cdiv(n_cap > 0 ? n_cap : 1, kChunk);
+  (void)max_bits;
+  return kOsHeader + 2 * 256 * cdiv(n_cap > 0 ? n_cap : 1, kChunk);
 }
 
 bool radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_host, const unsigned long long* n_dev,
-                      int64_t n_cap, int total_bits, uint32_t* hist, int64_t hist_cap, ScanScratch& sc, cudaStream_t s) {
+                      int64_t n_cap, int total_bits, uint32_t* hist, int64_t hist_cap, ScanScratch& sc, cudaStream_t s,
+                      uint32_t* flags) {
   if (n_cap <= 0 || total_bits <= 0) return true;
   const int passes = (total_bits + 7) / 8;
   const int bits_per = (total_bits + passes - 1) / passes;
   const int64_t nchunks = cdiv(n_cap, kChunk);
+  // one sweep for sorts of three or four passes (the depth sort); shorter sorts over many chunks (the
+  // list sort) measured faster in the classic form, whose passes have no look-back chain
+  if (passes >= 3 && n_cap < (int64_t)kOsValue && hist_cap >= kOsHeader + 2 * 256 * nchunks) {
+    // zero the counters, the digit counts and the first status region
+    cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)(kOsHeader + 256 * nchunks), s);
+    k_os_counts<<<grid_cap(cdiv(n_cap, kThreads * 4), 8), kThreads, 0, s>>>(keys[cur], n_host, n_dev, n_cap, passes,
+                                                                           bits_per, total_bits, hist + 8);
+    // CTAs take chunks from a counter, so the grid size does not affect the result: two per SM
+    // (the register limit of 512 threads at 64 registers); no device query, as serving captures this
+    const unsigned grid = grid_cap(nchunks, 2);
+    for (int p = 0; p < passes; ++p) {
+      const int shift = p * bits_per;
+      const int bits = (total_bits - shift) < bits_per ? (total_bits - shift) : bits_per;
+      k_os_scatter<<<grid, kScThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_host, n_dev,
+                                               n_cap, shift, bits, p, p + 1 < passes ? 1 : 0, hist, nchunks, flags);
+      cur ^= 1;
+    }
+    count_launches(1 + passes);
+    return true;
+  }
   if (((int64_t)1 << bits_per) * nchunks > hist_cap) return false;  // the histogram would not fit
   for (int p = 0; p < passes; ++p) {
     const int shift = p * bits_per;
