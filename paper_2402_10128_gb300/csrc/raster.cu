@@ -380,9 +380,12 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
   const unsigned lane = threadIdx.x & 31u;
   const int slot = reduce10_slot(lane);
   const bool adder = (lane & 1u) == 0 && slot >= 0;
+  // the constant factor each summed value still lacks (see the loop)
+  const float kSlotScale[10] = {1.0f, 1.0f, -0.5f, -1.0f, -0.5f, 1.0f, -0.34657359027997264f, 1.0f, 1.0f, 1.0f};
+  float slot_scale = 1.0f;
+#pragma unroll
+  for (int k = 0; k < 10; ++k) slot_scale = slot == k ? kSlotScale[k] : slot_scale;
   const float2 ONE = make_float2(1.0f, 1.0f), NEG1 = make_float2(-1.0f, -1.0f), ZERO = make_float2(0.f, 0.f);
-  const float2 NHALF = make_float2(-0.5f, -0.5f);
-  const float2 LN2 = make_float2(0.69314718055994531f, 0.69314718055994531f);
 
   for (uint32_t end = rg.x + max_last; end > rg.x;) {
     const uint32_t start = (end - rg.x > (uint32_t)kBatch) ? end - kBatch : rg.x;
@@ -392,8 +395,8 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
     const int cnt = stage_kept<kBatch>(st, keep, idx, rg.x, vals, [&](RecPairB& d, uint32_t g) {
       const Rec r = rec[g];
       stage_pair(d, r);
-      d.n0 = make_float4(-2.0f * r.b.x, -2.0f * r.b.x, -2.0f * r.b.y, -2.0f * r.b.y);
-      d.n1 = make_float4(-2.0f * r.b.z, -2.0f * r.b.z, 0.f, 0.f);
+      d.n0 = make_float4(r.b.x, r.b.x, r.b.y, r.b.y);
+      d.n1 = make_float4(r.b.z, r.b.z, 0.f, 0.f);
     });
     for (int j = cnt - 1; j >= 0; --j) {
       const uint32_t kpos = st.pos[j];  // 1-based position in the segment's list
@@ -405,7 +408,10 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
       const bool act0 = kpos <= last[0] && al0 >= P.alpha_min;
       const bool act1 = kpos <= last[1] && al1 >= P.alpha_min;
       if (!__any_sync(0xffffffffu, act0 || act1)) continue;
-      // gradient terms of both pixels (zero for an inactive one, whose T and S stay as they are)
+      // gradient terms of both pixels (zero for an inactive one, whose T and S stay as they are).
+      // Constant factors are left out here and applied to the warp's sums (slot_scale): the
+      // derivative of G = 2^(-p log2(e)/2) w.r.t. p is taken as G (true: -G/2), the record's conic
+      // terms as (a, b, c) (true: -2 (a, b, c)), 2 dx dy as dx dy, and ln q as log2 q.
       const float4 n0 = st.rec[j].n0, n1 = st.rec[j].n1, k0 = st.rec[j].k0, k1 = st.rec[j].k1;
       const float4 e = st.rec[j].e, c1 = st.rec[j].c1;
       const float2 dx = f.dx, dy = f.dy, p = f.p, lq = f.lq, G = f.G;
@@ -419,29 +425,28 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
       const float2 B0 = __ffma2_rn(S0, ninv, __fmul2_rn(lo2(k0), T));
       const float2 B1 = __ffma2_rn(S1, ninv, __fmul2_rn(hi2(k0), T));
       const float2 B2 = __ffma2_rn(S2, ninv, __fmul2_rn(lo2(k1), T));
-      float2 dLda = __ffma2_rn(GC2, B2, __ffma2_rn(GC1, B1, __fmul2_rn(GC0, B0)));
-      dLda = sel2(act0, act1, dLda, ZERO);
+      const float2 dLda_all = __ffma2_rn(GC2, B2, __ffma2_rn(GC1, B1, __fmul2_rn(GC0, B0)));
+      // dalpha/dG = kappa and dalpha/dkappa = G, both 0 where alpha is clamped or the pixel inactive
+      const float2 dLdaG = sel2(act0 && !cl0, act1 && !cl1, dLda_all, ZERO);
       S0 = __ffma2_rn(lo2(k0), w, S0);
       S1 = __ffma2_rn(hi2(k0), w, S1);
       S2 = __ffma2_rn(lo2(k1), w, S2);
       const float2 gr = __fmul2_rn(GC0, w), gg = __fmul2_rn(GC1, w), gbl = __fmul2_rn(GC2, w);
-      const float2 kG = sel2(!cl0, !cl1, hi2(c1), ZERO);
-      const float2 Gm = sel2(!cl0, !cl1, G, ZERO);
-      const float2 dG = __fmul2_rn(dLda, kG);
-      const float2 gk = __fmul2_rn(dLda, Gm);
-      const float2 dp = __fmul2_rn(dG, __fmul2_rn(NHALF, G));
+      const float2 gk = __fmul2_rn(dLdaG, G);
+      const float2 dp = __fmul2_rn(__fmul2_rn(dLdaG, hi2(c1)), G);  // x (-1/2)
       float2 dq, gbeta = ZERO;
       if (gef) {
+        // only where the pixel takes the fragment (elsewhere p may overflow) and q > 1e-12
         const bool m0 = act0 && q0 > 1e-12f, m1 = act1 && q1 > 1e-12f;
         if (hb == 1.0f) {
           dq = sel2(m0, m1, dp, ZERO);
           const float2 l2 = make_float2(m0 ? mufu_lg2(q0) : 0.f, m1 ? mufu_lg2(q1) : 0.f);
-          gbeta = __fmul2_rn(__fmul2_rn(dq, make_float2(q0, q1)), __fmul2_rn(l2, LN2));
+          gbeta = __fmul2_rn(__fmul2_rn(dq, make_float2(q0, q1)), l2);  // x (-ln 2 / 2)
         } else {
-          const float2 pm = sel2(m0, m1, p, ZERO);
-          const float2 rq = make_float2(m0 ? rcp_approx(q0) : 0.f, m1 ? rcp_approx(q1) : 0.f);
-          dq = __fmul2_rn(__fmul2_rn(dp, hi2(e)), __fmul2_rn(pm, rq));
-          gbeta = __fmul2_rn(__fmul2_rn(dp, pm), __fmul2_rn(sel2(m0, m1, lq, ZERO), LN2));
+          const float2 rq = make_float2(rcp_approx(q0), rcp_approx(q1));
+          const float2 dpp = __fmul2_rn(dp, p);
+          dq = sel2(m0, m1, __fmul2_rn(__fmul2_rn(dpp, hi2(e)), rq), ZERO);
+          gbeta = sel2(m0, m1, __fmul2_rn(dpp, lq), ZERO);                // x (-ln 2 / 2)
         }
       } else {
         dq = dp;
@@ -449,13 +454,13 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
       const float2 dqdx = __fmul2_rn(dq, dx), dqdy = __fmul2_rn(dq, dy);
       const float2 gmx = __ffma2_rn(dqdy, hi2(n0), __fmul2_rn(dqdx, lo2(n0)));
       const float2 gmy = __ffma2_rn(dqdy, lo2(n1), __fmul2_rn(dqdx, hi2(n0)));
-      const float2 ga = __fmul2_rn(dqdx, dx);
-      const float2 gb = __fmul2_rn(dqdx, __fadd2_rn(dy, dy));
-      const float2 gcc = __fmul2_rn(dqdy, dy);
+      const float2 ga = __fmul2_rn(dqdx, dx);   // x (-1/2)
+      const float2 gb = __fmul2_rn(dqdx, dy);   // x (-1)
+      const float2 gcc = __fmul2_rn(dqdy, dy);  // x (-1/2)
       float v[10] = {gmx.x + gmx.y, gmy.x + gmy.y, ga.x + ga.y,   gb.x + gb.y,   gcc.x + gcc.y,
                      gk.x + gk.y,   gbeta.x + gbeta.y, gr.x + gr.y, gg.x + gg.y, gbl.x + gbl.y};
       const float sum = warp_reduce_scatter10(v);
-      if (adder) atomicAdd(reinterpret_cast<float*>(g2d + 3 * (int64_t)st.id[j]) + slot, sum);
+      if (adder) atomicAdd(reinterpret_cast<float*>(g2d + 3 * (int64_t)st.id[j]) + slot, sum * slot_scale);
     }
     end = start;
   }
