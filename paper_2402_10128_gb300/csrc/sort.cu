@@ -112,12 +112,13 @@ __device__ __forceinline__ int64_t element_count(int64_t n_host, const unsigned 
 
 // hist layout: [bin][chunk] over the active chunks (ceil(count / kChunk)); the matrix size goes to
 // *entries (device) for the scan that follows
+template <int NB>
 __global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restrict__ keys, int64_t n_host,
                                                          const unsigned long long* __restrict__ n_dev, int64_t cap,
                                                          int shift, int bits, uint32_t* __restrict__ hist,
                                                          unsigned long long* __restrict__ entries) {
   constexpr int kWarps = kThreads / 32;
-  __shared__ uint32_t cnt[kWarps][256];  // one private histogram per warp: less atomic contention
+  __shared__ uint32_t cnt[kWarps][NB];  // one private histogram per warp: less atomic contention
   const int nbins = 1 << bits;
   const int64_t n = element_count(n_host, n_dev, cap);
   const uint32_t mask = (uint32_t)nbins - 1u;
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restr
   for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
     const int64_t base = c * kChunk;
     __syncthreads();
-    for (int i = threadIdx.x; i < kWarps * 256; i += kThreads) (&cnt[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < kWarps * NB; i += kThreads) (&cnt[0][0])[i] = 0;
     __syncthreads();
     if (base + kChunk <= n) {
       const uint4* k4 = reinterpret_cast<const uint4*>(keys + base);
@@ -164,6 +165,18 @@ __global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restr
 constexpr int kScThreads = 512;                 // scatter CTA: twice the warps of the other kernels
 constexpr int kScItems = kChunk / kScThreads;   // 8 items per thread, same chunk
 
+// shared memory of k_radix_scatter<NB> (dynamic: above 48 KB for NB = 512)
+template <int NB>
+struct ScatterSmem {
+  uint32_t wcnt[kScThreads / 32][NB];  // per warp and digit: running count, then prefix
+  uint32_t goff[NB];
+  uint32_t bstart[NB + 1];
+  uint32_t wsum[kScThreads / 32];
+  uint32_t skeys[kChunk];
+  uint32_t svals[kChunk];
+};
+
+template <int NB>
 __global__ void __launch_bounds__(kScThreads) k_radix_scatter(const uint32_t* __restrict__ keys_in,
                                                             const uint32_t* __restrict__ vals_in,
                                                             uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
@@ -171,12 +184,14 @@ __global__ void __launch_bounds__(kScThreads) k_radix_scatter(const uint32_t* __
                                                             int64_t cap, int shift, int bits,
                                                             const uint32_t* __restrict__ hist_scanned) {
   constexpr int kWarps = kScThreads / 32;
-  __shared__ __align__(16) uint32_t wcnt[kWarps][256];  // per warp and digit: running count, then prefix
-  __shared__ uint32_t goff[256];
-  __shared__ uint32_t bstart[257];
-  __shared__ uint32_t wsum[kWarps];
-  __shared__ uint32_t skeys[kChunk];
-  __shared__ uint32_t svals[kChunk];
+  extern __shared__ __align__(16) unsigned char sc_smem[];
+  ScatterSmem<NB>& sm = *reinterpret_cast<ScatterSmem<NB>*>(sc_smem);
+  auto& wcnt = sm.wcnt;
+  auto& goff = sm.goff;
+  auto& bstart = sm.bstart;
+  auto& wsum = sm.wsum;
+  auto& skeys = sm.skeys;
+  auto& svals = sm.svals;
   const int nbins = 1 << bits;
   const uint32_t mask = (uint32_t)nbins - 1u;
   const int64_t n = element_count(n_host, n_dev, cap);
@@ -189,7 +204,7 @@ __global__ void __launch_bounds__(kScThreads) k_radix_scatter(const uint32_t* __
   __syncthreads();  // the previous chunk's readers of the shared arrays are done
   {
     uint4* z = reinterpret_cast<uint4*>(&wcnt[0][0]);
-    for (int i = threadIdx.x; i < kWarps * 256 / 4; i += kScThreads) z[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = threadIdx.x; i < kWarps * NB / 4; i += kScThreads) z[i] = make_uint4(0u, 0u, 0u, 0u);
   }
   for (int b = threadIdx.x; b < nbins; b += kScThreads) goff[b] = hist_scanned[(int64_t)b * nchunks + c];
   __syncthreads();
@@ -752,16 +767,37 @@ bool radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_
     count_launches(1 + passes);
     return true;
   }
-  if (((int64_t)1 << bits_per) * nchunks > hist_cap) return false;  // the histogram would not fit
-  for (int p = 0; p < passes; ++p) {
-    const int shift = p * bits_per;
-    const int bits = (total_bits - shift) < bits_per ? (total_bits - shift) : bits_per;
+  // keys of 9 bits (the list sort's segment ids at the usual sizes) in one pass of 512 bins
+  const bool wide = total_bits == 9;
+  const int passes_c = wide ? 1 : passes;
+  const int bits_c = wide ? 9 : bits_per;
+  if (((int64_t)1 << bits_c) * nchunks > hist_cap) return false;  // the histogram would not fit
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_radix_scatter<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ScatterSmem<256>));
+    cudaFuncSetAttribute(k_radix_scatter<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ScatterSmem<512>));
+    attr_set = true;
+  }
+  for (int p = 0; p < passes_c; ++p) {
+    const int shift = p * bits_c;
+    const int bits = (total_bits - shift) < bits_c ? (total_bits - shift) : bits_c;
     const int64_t entries = ((int64_t)1 << bits) * nchunks;  // capacity of the matrix
     unsigned long long* n_entries = reinterpret_cast<unsigned long long*>(sc.buf);
-    k_radix_hist<<<grid_cap(nchunks, 8), kThreads, 0, s>>>(keys[cur], n_host, n_dev, n_cap, shift, bits, hist, n_entries);
+    if (wide) {
+      k_radix_hist<512><<<grid_cap(nchunks, 8), kThreads, 0, s>>>(keys[cur], n_host, n_dev, n_cap, shift, bits, hist,
+                                                                  n_entries);
+    } else {
+      k_radix_hist<256><<<grid_cap(nchunks, 8), kThreads, 0, s>>>(keys[cur], n_host, n_dev, n_cap, shift, bits, hist,
+                                                                  n_entries);
+    }
     scan_exclusive<uint32_t, uint32_t>(hist, hist, entries, (uint32_t*)nullptr, sc, s, n_entries);
-    k_radix_scatter<<<grid_cap(nchunks, 4), kScThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_host,
-                                                           n_dev, n_cap, shift, bits, hist);
+    if (wide) {
+      k_radix_scatter<512><<<grid_cap(nchunks, 2), kScThreads, sizeof(ScatterSmem<512>), s>>>(
+          keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_host, n_dev, n_cap, shift, bits, hist);
+    } else {
+      k_radix_scatter<256><<<grid_cap(nchunks, 4), kScThreads, sizeof(ScatterSmem<256>), s>>>(
+          keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_host, n_dev, n_cap, shift, bits, hist);
+    }
     count_launches(2);
     cur ^= 1;
   }
