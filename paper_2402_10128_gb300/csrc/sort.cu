@@ -10,6 +10,8 @@
 //   K3  keygen: load-balanced expansion, one thread per output entry
 //   K4  stable LSD radix passes (<= 8-bit digits): per-chunk histogram, scan, stable scatter
 //   K5  per-tile [start, end) from the sorted tile ids
+#include <atomic>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -772,11 +774,14 @@ bool radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_
   const int passes_c = wide ? 1 : passes;
   const int bits_c = wide ? 9 : bits_per;
   if (((int64_t)1 << bits_c) * nchunks > hist_cap) return false;  // the histogram would not fit
-  static bool attr_set = false;
-  if (!attr_set) {
+  // the scatter's shared memory exceeds the 48 KB default: opt in once per device
+  static std::atomic<bool> attr_set[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !attr_set[dev].load(std::memory_order_acquire)) {
     cudaFuncSetAttribute(k_radix_scatter<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ScatterSmem<256>));
     cudaFuncSetAttribute(k_radix_scatter<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ScatterSmem<512>));
-    attr_set = true;
+    if (dev >= 0 && dev < 64) attr_set[dev].store(true, std::memory_order_release);
   }
   for (int p = 0; p < passes_c; ++p) {
     const int shift = p * bits_c;
