@@ -121,3 +121,28 @@ def test_training_calls_validate_on_the_host(lib):
     st = lib.ges_density_control(ctypes.addressof(fake), ctypes.byref(ts), arrs[0], arrs[0], arrs[0],
                                  ctypes.byref(dp), ctypes.byref(ts), ctypes.byref(n_out), None)
     assert st == ges.GES_ERR_INVALID_ARG
+
+
+def test_fit1d_calls_validate_on_the_host(lib):
+    """Out-of-range sizes and constants of the 1D fits are refused before any device work."""
+    from paper_2402_10128_gb300 import ges
+    lib = ges._lib   # the binding's handle, whose functions carry their argument types
+    fake = ctypes.create_string_buffer(64)
+    buf = ctypes.create_string_buffer(4096)
+    a = ctypes.addressof(buf)
+    p = ges.fit1d_params_default()
+    assert p.model == ges.GES_MIX_GEF and p.n_components == 5 and p.epochs == 1000 and p.precision == 32
+    assert p.lr == 0.01 and p.beta1 == 0.9 and p.beta2 == 0.999 and p.adam_eps == 1e-8 and p.nu == 4.0
+    cases = [dict(n_components=0), dict(n_components=129), dict(model=7), dict(precision=16), dict(epochs=-1),
+             dict(lr=0.0), dict(beta1=1.0), dict(nu=0.0)]
+    for kw in cases:
+        q = ges.fit1d_params_default(**kw)
+        st = lib.ges_fit1d(ctypes.addressof(fake), ctypes.byref(q), 4, 100, a, a, 0, a, None, a, None, None)
+        assert st == ges.GES_ERR_INVALID_ARG, kw
+    st = lib.ges_fit1d(ctypes.addressof(fake), ctypes.byref(p), 4, 5000, a, a, 0, a, None, a, None, None)
+    assert st == ges.GES_ERR_INVALID_ARG and "n_points" in ges.last_error()
+    st = lib.ges_fit1d(ctypes.addressof(fake), ctypes.byref(p), 4, 100, a, a, 0, None, None, a, None, None)
+    assert st == ges.GES_ERR_INVALID_ARG
+    assert lib.ges_signal1d(ctypes.addressof(fake), 9, 1.0, 10, -1.0, 1.0, 32, a, a, None) == ges.GES_ERR_INVALID_ARG
+    assert lib.ges_signal1d(ctypes.addressof(fake), 0, 0.0, 10, -1.0, 1.0, 32, a, a, None) == ges.GES_ERR_INVALID_ARG
+    assert lib.ges_signal1d(ctypes.addressof(fake), 0, 1.0, 10, -1.0, 1.0, 8, a, a, None) == ges.GES_ERR_INVALID_ARG
