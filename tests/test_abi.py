@@ -95,6 +95,7 @@ def test_position_lr_matches_the_oracle_schedule(lib):
 def test_training_calls_validate_on_the_host(lib):
     """NULL and misaligned pointers are refused before any device work."""
     from paper_2402_10128_gb300 import ges
+    lib = ges._lib   # the binding's handle, whose functions carry their argument types
     fake = ctypes.create_string_buffer(64)           # never dereferenced: validation fails first
     buf = ctypes.create_string_buffer(4096)
     base = (ctypes.addressof(buf) + 15) & ~15
