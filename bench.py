@@ -471,7 +471,8 @@ def main():
     pix = WIDTH * HEIGHT
     direct = aggregate_mpix_s(ws, pix, args.steps, ms_fb)
     value = graph["mpix_s"]
-    fwd_rate = aggregate_mpix_s(ws, pix, args.steps, ms_f)
+    fwd_direct = aggregate_mpix_s(ws, pix, args.steps, ms_f)
+    fwd_rate = graph["fwd_mpix_s"]
     st_mean = stage.mean(0)
 
     # roofline of the dominant kernel: the composites are bound by the special-function unit
@@ -524,7 +525,7 @@ def main():
                       "n_prims": sc.n, "width": WIDTH, "height": HEIGHT, "cameras": len(cams),
                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                       "l2": "inputs larger than L2 (scene 360 MB, key lists ~%d MB)" % int(mean_K * 16 / 1e6)},
-           "fwd_mpix_s": fwd_rate, "fwd_ms_per_frame": ms_f / args.steps,
+           "fwd_mpix_s": fwd_rate, "fwd_ms_per_frame": graph["fwd_ms_per_frame"],
            "stage_ms": dict(zip(stage_names, [float(x) for x in st_mean])),
            "dominant_stage": stage_names[dom],
            "frame_stats": {"K_mean": mean_K, "evaluated_pairs_mean": mean_eval, "in_extent_pairs_mean": mean_inr,
@@ -533,7 +534,8 @@ def main():
            "preprocess_hbm": {"kernel": "k_preprocess", "achieved_gbs": pre_gbs, "peak_gbs": hbm, "frac": pre_gbs / hbm,
                               "bytes_per_prim": 328},
            "kernel_ms": kernel_ms, "graph_replay": graph,
-           "direct_calls": {"mpix_s": direct, "ms_per_step": ms_fb / args.steps,
+           "direct_calls": {"mpix_s": direct, "ms_per_step": ms_fb / args.steps, "fwd_mpix_s": fwd_direct,
+                            "fwd_ms_per_frame": ms_f / args.steps,
                             "what": "the same steps as four C-ABI calls each, traced (the per-kernel times above)"},
            "gpu_launches": int(launches), "clocks": clocks}
 
@@ -704,16 +706,18 @@ def graph_replay_bench(frame, scene_c, gcam, params, img, T, nc, dL, grads, grad
     s = torch.cuda.Stream(device=dev)
     s.wait_stream(torch.cuda.current_stream())
     sp0 = torch.cuda.current_stream().cuda_stream
-    graphs = []
+    graphs, fwd_graphs = [], []
     for cam in gcam:
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=s):
-            sp = s.cuda_stream
-            ges.ges_preprocess(frame.handle, scene_c, cam, params, sp)
-            ges.ges_bin_sort(frame.handle, sp)
-            ges.ges_render_fwd(frame.handle, img, T, nc, sp)
-            ges.ges_render_bwd(frame.handle, scene_c, T, nc, dL, grads_c, sp)
-        graphs.append(g)
+        for bwd in (True, False):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                sp = s.cuda_stream
+                ges.ges_preprocess(frame.handle, scene_c, cam, params, sp)
+                ges.ges_bin_sort(frame.handle, sp)
+                ges.ges_render_fwd(frame.handle, img, T, nc, sp)
+                if bwd:
+                    ges.ges_render_bwd(frame.handle, scene_c, T, nc, dL, grads_c, sp)
+            (graphs if bwd else fwd_graphs).append(g)
     # the replays do the direct calls' work: equal outputs, bit for bit, for every camera
     def direct(cam):
         ges.ges_preprocess(frame.handle, scene_c, cam, params, sp0)
@@ -736,25 +740,35 @@ def graph_replay_bench(frame, scene_c, gcam, params, img, T, nc, dL, grads, grad
         assert torch.equal(ref[0], got[0]), f"graph replay image differs from the direct calls ({k})"
         for a, a2, b in zip(ref[1:], ref2[1:], got[1:]):
             assert rel(a, b) <= max(10 * rel(a, a2), 1e-4), f"graph replay gradients differ ({k}): {rel(a, b)}"
-    for i in range(warmup):
-        graphs[i % len(graphs)].replay()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    cur = torch.cuda.current_stream()
-    e0.record(cur)
-    for i in range(steps):
-        graphs[i % len(graphs)].replay()
-    e1.record(cur)
-    torch.cuda.synchronize()
-    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+        img.zero_()
+        fwd_graphs[k].replay()
+        torch.cuda.synchronize()
+        assert torch.equal(ref[0], img), f"forward graph replay image differs from the direct calls ({k})"
+    def timed(gs):
+        for i in range(warmup):
+            gs[i % len(gs)].replay()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        cur = torch.cuda.current_stream()
+        e0.record(cur)
+        for i in range(steps):
+            gs[i % len(gs)].replay()
+        e1.record(cur)
+        torch.cuda.synchronize()
+        return max_over_ranks(e0.elapsed_time(e1), dist, dev)
+
+    ms = timed(graphs)
+    ms_f = timed(fwd_graphs)
     assert ges.ges_frame_status(frame.handle)[0] == ges.GES_OK
-    del graphs
-    return {"mpix_s": aggregate_mpix_s(ws, img.shape[1] * img.shape[2], steps, ms), "ms_per_step": ms / steps,
-            "what": "the fwd+bwd step captured per camera as a CUDA graph and replayed (checked against the "
-                    "direct calls)"}
+    del graphs, fwd_graphs
+    px = img.shape[1] * img.shape[2]
+    return {"mpix_s": aggregate_mpix_s(ws, px, steps, ms), "ms_per_step": ms / steps,
+            "fwd_mpix_s": aggregate_mpix_s(ws, px, steps, ms_f), "fwd_ms_per_frame": ms_f / steps,
+            "what": "the fwd+bwd step (and the fwd alone) captured per camera as a CUDA graph and replayed "
+                    "(checked against the direct calls)"}
 
 
 def training_bench(steps, warmup, dev, sc, cams, segment_tiles):
