@@ -165,7 +165,13 @@ ges_status ges_preprocess(ges_frame* frame, const ges_scene* scene, const ges_ca
    depth order; a stable radix sort by segment id; per-segment [start,end) ranges.  An entry
    carries the columns of its span inside the segment, so a tile's list (the entries of its
    segment whose span contains the tile, in order) equals a stable sort of the 64-bit keys
-   (tile << 32 | depth bits) with values = primitive index, restricted to that tile. */
+   (tile << 32 | depth bits) with values = primitive index, restricted to that tile.
+   The depth sort runs in one sweep with a bounded decoupled look-back; should a wait ever give
+   up, ges_frame_status reports GES_ERR_DEVICE_WAIT and the lists must not be used.
+   With a fixed key_capacity, ges_preprocess, ges_bin_sort, ges_render_fwd and ges_render_bwd
+   enqueue work only (no host synchronisation, no allocation), so one frame's sequence can be
+   captured into a CUDA graph and replayed; the camera, parameters and array pointers of the
+   calls are fixed in the graph. */
 ges_status ges_bin_sort(ges_frame* frame, void* stream);
 
 /* Forward composite (Sec. 3.2): per pixel, front to back over its tile's list,
