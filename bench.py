@@ -551,7 +551,8 @@ def main():
         if "differentiation" in legs:
             out["differentiation"] = differentiation_bench(20, 3, dev)
         if "scale_modification" in legs:
-            out["scale_modification"] = scale_modification_bench(10, 3, dev, sc, t, cams[0], args.segment_tiles)
+            out["scale_modification"] = scale_modification_bench(10, 3, dev, sc, t, cams[0], args.segment_tiles,
+                                                                 mufu_roofline)
         torch.cuda.empty_cache()
         if "mixture_study" in legs:
             out["mixture_study"] = mixture_study_bench(dev)
@@ -985,15 +986,20 @@ def mixture_study_bench(dev, epochs=1000, runs_per=20, n_points=1000, cpu_fits=2
     return out
 
 
-def _time_c_abi_steps(sc, t, cam, params, steps, warmup, dev):
+def _time_c_abi_steps(sc, t, cam, params, steps, warmup, dev, detail=None):
     """fwd (K1-K4) and fwd+bwd (K1-K8) through the C-ABI on device-resident scene tensors `t`,
-    timed with CUDA events; returns (K entries, {"fwd": ..., "fwd_bwd": ...})."""
+    timed with CUDA events; returns (K entries, {"fwd": ..., "fwd_bwd": ...}).  With a dict
+    `detail`, also fills in the frame's (fragment, pixel) pair counts and the traced per-launch
+    device time of every kernel of the fwd+bwd steps."""
     import torch
     from paper_2402_10128_gb300 import ges, render
     probe = render.Frame(sc.n, cam.width, cam.height, key_capacity=0)
     probe.forward(t, sc.sh_degree, cam, {"segment_tiles": params.segment_tiles, "mode": params.falloff,
                                          "rho": params.rho, "phi_mode": params.phi_mode})
     K = probe.status()[1]
+    if detail is not None:
+        ev, inr, comp, _ = ges.ges_frame_count_work(probe.handle)
+        detail.update(evaluated_pairs=int(ev), in_extent_pairs=int(inr), composited_pairs=int(comp))
     probe.close()
     frame = render.Frame(sc.n, cam.width, cam.height, key_capacity=int(K * 1.02) + 4096)
     gcam = ges.make_camera(cam)
@@ -1013,6 +1019,7 @@ def _time_c_abi_steps(sc, t, cam, params, steps, warmup, dev):
             ges.ges_render_bwd(frame.handle, scene_c, T, nc, dL, grads_c)
 
     out = {}
+    ctx = render.default_context(dev.index or 0)
     for bwd in (False, True):
         for _ in range(warmup):
             step(bwd)
@@ -1025,6 +1032,14 @@ def _time_c_abi_steps(sc, t, cam, params, steps, warmup, dev):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
         out["fwd_bwd" if bwd else "fwd"] = {"mpix_s": W * H / (ms / 1e3) / 1e6, "ms_per_frame": ms}
+    if detail is not None:  # per-kernel times from a separate traced run (tracing adds events per launch)
+        ges.ges_trace_enable(ctx.handle, True)
+        for _ in range(steps):
+            step(True)
+        torch.cuda.synchronize()
+        tr = ges.ges_trace_read(ctx.handle)
+        ges.ges_trace_enable(ctx.handle, False)
+        detail["kernel_ms"] = {k: ms / n for k, (n, ms) in tr.items()}
     assert frame.status()[0] == 0
     assert all(torch.isfinite(g).all() for g in grads)
     frame.close()
@@ -1046,7 +1061,7 @@ def stress_bench(steps, warmup, dev, beta2, segment_tiles):
             "K_entries": K, "steps": steps, **out}
 
 
-def scale_modification_bench(steps, warmup, dev, sc, t, cam, segment_tiles):
+def scale_modification_bench(steps, warmup, dev, sc, t, cam, segment_tiles, roofline_fn=None, cpu_pixels=1000):
     """The scale-modification variants (Sec. 3.2 and the ablation's shape strengths) on one view of
     the scene-scale workload: phi_bar_rho at rho = 0.1 (default), 0 and 10, the exact normalised
     Gamma ratio on the scale vector and on the variance, and the Gaussian-form rasterizer.  The
@@ -1057,14 +1072,36 @@ def scale_modification_bench(steps, warmup, dev, sc, t, cam, segment_tiles):
                 "phi_exact": {"phi_mode": ges.GES_PHI_EXACT},
                 "phi_exact_variance": {"phi_mode": ges.GES_PHI_EXACT_VARIANCE},
                 "gaussian_form_phi_bar": {"falloff": ges.GES_FALLOFF_PAPER_APPROX}}
+    import oracle
+    rng = np.random.default_rng(5)
+    pix = rng.choice(cam.width * cam.height, cpu_pixels, replace=False)
+    gpx = rng.standard_normal((3, cpu_pixels))
     res = {}
     for name, kw in variants.items():
         params = ges.params_default()
         params.segment_tiles = segment_tiles
         for k, v in kw.items():
             setattr(params, k, v)
-        K, out = _time_c_abi_steps(sc, t, cam, params, steps, warmup, dev)
-        res[name] = {"K_entries": K, **out}
+        detail = {}
+        K, out = _time_c_abi_steps(sc, t, cam, params, steps, warmup, dev, detail)
+        entry = {"K_entries": K, **out, "pairs": {k: detail[k] for k in ("evaluated_pairs", "in_extent_pairs",
+                                                                        "composited_pairs")},
+                 "k_render_bwd_ms": detail["kernel_ms"].get("k_render_bwd"),
+                 "k_render_fwd_ms": detail["kernel_ms"].get("k_render_fwd")}
+        if roofline_fn is not None:
+            inr, comp = detail["in_extent_pairs"], detail["composited_pairs"]
+            gef = params.falloff == ges.GES_FALLOFF_GEF
+            # per pair: GEF lg2 + 2 ex2 (fwd and bwd) and 2 rcp (bwd); Gaussian form 1 ex2 and 1 rcp (bwd)
+            entry["roofline_bwd"] = roofline_fn("k_render_bwd", entry["k_render_bwd_ms"], inr if gef else 0,
+                                                2 * inr if gef else inr, 2 * comp if gef else comp,
+                                                "MUFU work of this variant's pairs")
+        # the oracle (FP64 brute force on the host) on a sample of pixels of the same view and variant
+        op = {"rho": float(params.rho), "mode": int(params.falloff), "phi_mode": int(params.phi_mode)}
+        t0 = time.perf_counter()
+        oracle.backward(sc, cam, gpx, params=op, pixels=pix, nthreads=os.cpu_count() or 1)
+        entry["cpu_baseline"] = {"kind": "oracle", "value": cpu_pixels / (time.perf_counter() - t0) / 1e6,
+                                 "unit": "Mpix/s", "sample": f"{cpu_pixels} random pixels, fwd+bwd, FP64 brute force"}
+        res[name] = entry
     return {"workload": "scene-scale view 0: 1.5M clustered primitives, SH3, beta log-U[0.5,8], 1245x825",
             "steps": steps, "segment_tiles": segment_tiles, "variants": res}
 
