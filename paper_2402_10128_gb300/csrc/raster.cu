@@ -317,7 +317,7 @@ __device__ __forceinline__ int reduce10_slot(unsigned lane) {
 
 // Backward.  Per pixel, walks its contributors back to front, recovering T_i = T_{i+1}/(1-alpha_i)
 // from the saved final transmittance; S is the colour composited behind the current fragment.
-//   dC/dalpha_i = c_i T_i - S_i / (1 - alpha_i)
+//   dC/dalpha_i = c_i T_i - S_i / (1 - alpha_i)   (summed over the channels against dL/dC)
 //   dalpha/dkappa = G, dalpha/dG = kappa (0 where alpha is clamped)
 //   dG/dp = -G/2,  p = q^hb:  dp/dq = hb p / q,  dp/dhb = p ln q  (0 for q < 1e-12)
 //   q = a dx^2 + 2 b dx dy + c dy^2, dx = px - mx
@@ -367,9 +367,11 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
   const float2 GC0 = make_float2(gc[0][0], gc[0][1]), GC1 = make_float2(gc[1][0], gc[1][1]),
                GC2 = make_float2(gc[2][0], gc[2][1]);
   float2 T = make_float2(Tk[0], Tk[1]);
-  float2 S0 = __fmul2_rn(T, make_float2(vd.bg[0], vd.bg[0]));
-  float2 S1 = __fmul2_rn(T, make_float2(vd.bg[1], vd.bg[1]));
-  float2 S2 = __fmul2_rn(T, make_float2(vd.bg[2], vd.bg[2]));
+  // U = sum_c dL/dC_c S_c, S_c the colour composited behind the current fragment (at the start,
+  // T_final bg_c): dL/dalpha_i needs S only through this sum, so one float2 carries it.
+  float2 U = __fmul2_rn(T, __ffma2_rn(GC2, make_float2(vd.bg[2], vd.bg[2]),
+                                      __ffma2_rn(GC1, make_float2(vd.bg[1], vd.bg[1]),
+                                                 __fmul2_rn(GC0, make_float2(vd.bg[0], vd.bg[0])))));
   if (threadIdx.x == 0) s_max_last = 0;
   __syncthreads();
   atomicMax(&s_max_last, max(last[0], last[1]));
@@ -421,16 +423,12 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
       const float2 inv = make_float2(act0 ? rcp_approx(om.x) : 1.0f, act1 ? rcp_approx(om.y) : 1.0f);
       T = __fmul2_rn(T, inv);
       const float2 w = __fmul2_rn(alpha, T);
-      const float2 ninv = __fmul2_rn(inv, NEG1);
-      const float2 B0 = __ffma2_rn(S0, ninv, __fmul2_rn(lo2(k0), T));
-      const float2 B1 = __ffma2_rn(S1, ninv, __fmul2_rn(hi2(k0), T));
-      const float2 B2 = __ffma2_rn(S2, ninv, __fmul2_rn(lo2(k1), T));
-      const float2 dLda_all = __ffma2_rn(GC2, B2, __ffma2_rn(GC1, B1, __fmul2_rn(GC0, B0)));
+      // D = sum_c dL/dC_c c_c;  dL/dalpha = D T_i - U / (1 - alpha_i);  U += D alpha_i T_i
+      const float2 D = __ffma2_rn(GC2, lo2(k1), __ffma2_rn(GC1, hi2(k0), __fmul2_rn(GC0, lo2(k0))));
+      const float2 dLda_all = __ffma2_rn(U, __fmul2_rn(inv, NEG1), __fmul2_rn(D, T));
       // dalpha/dG = kappa and dalpha/dkappa = G, both 0 where alpha is clamped or the pixel inactive
       const float2 dLdaG = sel2(act0 && !cl0, act1 && !cl1, dLda_all, ZERO);
-      S0 = __ffma2_rn(lo2(k0), w, S0);
-      S1 = __ffma2_rn(hi2(k0), w, S1);
-      S2 = __ffma2_rn(lo2(k1), w, S2);
+      U = __ffma2_rn(D, w, U);
       const float2 gr = __fmul2_rn(GC0, w), gg = __fmul2_rn(GC1, w), gbl = __fmul2_rn(GC2, w);
       const float2 gk = __fmul2_rn(dLdaG, G);
       const float2 dp = __fmul2_rn(__fmul2_rn(dLdaG, hi2(c1)), G);  // x (-1/2)
