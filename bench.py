@@ -182,6 +182,25 @@ def run_reference(args, ws, rank):
     print(json.dumps(out))
 
 
+# FP32 arithmetic (adds, multiplies, FMAs; not compares or selects) that the composites' math needs,
+# counted from the equations:
+# * per in-extent (fragment, pixel) pair, the falloff: d = p - mean (2), q = (a dx + 2b dy) dx + c dy^2
+#   (5), the exponent's scale beta/2 log2 q (1), G's scale -log2(e)/2 p (1), kappa G (1): 10; 9 in the
+#   Gaussian form (no q^(beta/2));
+# * forward, per composited pair: 1 - alpha, T (1 - alpha), alpha T and the three colour FMAs: 6;
+# * backward, per composited pair: 1 - alpha, T_i = T_(i+1) / (1 - alpha), w = alpha T (3); D = sum_c
+#   dL/dC_c c_c (3); dL/dalpha = D T - U / (1 - alpha) (2); U += D w (1); dL/dkappa (1); dL/dp (2); dL/dq
+#   (3) and dL/dbeta (1), GEF only; dq/d(dx, dy) (2); the mean (4), conic (3) and colour (3) terms; and
+#   the 10 adds that sum each pair's 10 terms into the fragment's totals: 38 (34 in the Gaussian form)
+FP32_EVAL_GEF, FP32_EVAL_GAUSS, FP32_FWD, FP32_BWD_GEF, FP32_BWD_GAUSS = 10, 9, 6, 38, 34
+
+
+def composite_fp32_ops(gef, in_extent, composited):
+    """(forward, backward) FP32 op counts of one frame's composites from its pair counts."""
+    ev = (FP32_EVAL_GEF if gef else FP32_EVAL_GAUSS) * in_extent
+    return ev + FP32_FWD * composited, ev + (FP32_BWD_GEF if gef else FP32_BWD_GAUSS) * composited
+
+
 def sfu_rates():
     """Measured MUFU rates (results per SM per clock) from the SFU microbenchmark."""
     from paper_2402_10128_gb300 import build
@@ -475,8 +494,9 @@ def main():
     fwd_rate = graph["fwd_mpix_s"]
     st_mean = stage.mean(0)
 
-    # roofline of the dominant kernel: the composites are bound by the special-function unit
-    # (MUFU); its per-instruction rates are measured live by the SFU microbenchmark
+    # roofline of the dominant kernel: the composites' algorithmic work per (fragment, pixel) pair is
+    # transcendental (MUFU) and FP32 arithmetic; both pipes' rates are measured live by the SFU
+    # microbenchmark, and the binding one is reported
     peaks, src = _peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     stage_names = ["preprocess", "bin_sort", "render_fwd", "render_bwd+preprocess_bwd"]
@@ -490,27 +510,42 @@ def main():
     r_ex2, r_lg2, r_rcp = (sfu["per_sm_per_clk"][k] for k in ("ex2", "lg2", "rcp"))
     clk = nsm * sm_mhz * 1e6
 
-    def mufu_roofline(kernel, ms, n_lg2, n_ex2, n_rcp, work):
-        ops = n_lg2 + n_ex2 + n_rcp
-        t_peak = (n_lg2 / r_lg2 + n_ex2 / r_ex2 + n_rcp / r_rcp) / clk  # seconds at the measured rates
-        peak = ops / t_peak / 1e12
-        achieved = ops / (ms / 1e3) / 1e12
-        return {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (MUFU)",
-                "frac": achieved / peak, "traffic": _traffic(kernel.split()[0]), "work": work,
-                "peak_source": (f"{nsm} SMs x {sm_mhz:.0f} MHz ({src} max clock) x measured MUFU rates per SM per clock "
-                                f"(ex2 {r_ex2:.1f}, lg2 {r_lg2:.1f}, rcp {r_rcp:.1f}; sfu_rates microbenchmark) "
-                                f"weighted by the kernel's instruction mix")}
+    r_fma = float(sfu["per_sm_per_clk"].get("fma", 128.0))
+
+    def composite_roofline(kernel, ms, n_lg2, n_ex2, n_rcp, n_fp32, work):
+        """Two floors for a launch: its MUFU ops at the measured per-instruction rates, and its FP32
+        ops (adds, multiplies, FMAs) at the measured FMA-pipe rate; the larger one binds."""
+        mufu_ops = n_lg2 + n_ex2 + n_rcp
+        t_mufu = (n_lg2 / r_lg2 + n_ex2 / r_ex2 + n_rcp / r_rcp) / clk  # seconds at the measured rates
+        t_fp32 = n_fp32 / r_fma / clk
+        sec = ms / 1e3
+        res = {"mufu": {"ops": mufu_ops, "achieved": mufu_ops / sec / 1e12,
+                        "peak": (mufu_ops / t_mufu / 1e12) if t_mufu > 0 else None, "unit": "Tops/s",
+                        "frac": t_mufu / sec, "floor_ms": t_mufu * 1e3},
+               "fp32": {"ops": n_fp32, "achieved": n_fp32 / sec / 1e12, "peak": r_fma * clk / 1e12, "unit": "Tops/s",
+                        "frac": t_fp32 / sec, "floor_ms": t_fp32 * 1e3}}
+        bind = "fp32" if t_fp32 >= t_mufu else "mufu"
+        r = res[bind]
+        return {"kernel": kernel, "bound": "alu", "binding": bind, "achieved": r["achieved"], "peak": r["peak"],
+                "unit": "Tops/s (%s)" % ("FP32 pipe" if bind == "fp32" else "MUFU"), "frac": r["frac"],
+                "traffic": _traffic(kernel.split()[0]), "work": work, "resources": res,
+                "peak_source": (f"{nsm} SMs x {sm_mhz:.0f} MHz ({src} max clock) x rates per SM per clock measured "
+                                f"by the sfu_rates microbenchmark: FP32 FMA {r_fma:.1f}; MUFU ex2 {r_ex2:.1f}, "
+                                f"lg2 {r_lg2:.1f}, rcp {r_rcp:.1f}, weighted by the kernel's MUFU mix")}
 
     # average device time per launch of each traced kernel over the timed steps
     kernel_ms = {k: ms / n for k, (n, ms) in trace.items()}
     bwd_ms = kernel_ms["k_render_bwd"]
     fwd_ms = kernel_ms["k_render_fwd"]
-    roofline = mufu_roofline("k_render_bwd (backward composite)", bwd_ms,
-                             mean_inr, 2 * mean_inr, 2 * mean_comp,
-                             f"per frame: lg2 + 2 ex2 per in-extent pair ({mean_inr:.3e}) + 2 rcp per composited "
-                             f"pair ({mean_comp:.3e})")
-    roofline_fwd = mufu_roofline("k_render_fwd (forward composite)", fwd_ms, mean_inr, 2 * mean_inr, 0,
-                                 f"per frame: lg2 + 2 ex2 per in-extent pair ({mean_inr:.3e})")
+    fp32_fwd, fp32_bwd = composite_fp32_ops(True, mean_inr, mean_comp)
+    roofline = composite_roofline("k_render_bwd (backward composite)", bwd_ms,
+                                  mean_inr, 2 * mean_inr, 2 * mean_comp, fp32_bwd,
+                                  f"per frame: lg2 + 2 ex2 and {FP32_EVAL_GEF} FP32 ops per in-extent pair "
+                                  f"({mean_inr:.3e}); 2 rcp and {FP32_BWD_GEF} FP32 ops per composited pair "
+                                  f"({mean_comp:.3e})")
+    roofline_fwd = composite_roofline("k_render_fwd (forward composite)", fwd_ms, mean_inr, 2 * mean_inr, 0, fp32_fwd,
+                                      f"per frame: lg2 + 2 ex2 and {FP32_EVAL_GEF} FP32 ops per in-extent pair "
+                                      f"({mean_inr:.3e}); {FP32_FWD} FP32 ops per composited pair ({mean_comp:.3e})")
     # preprocess: HBM bytes per primitive (read 240 B at SH3; write 88 B: depth key x2, sort value,
     # rect, 48-B record, extent shape, tile count)
     pre_bytes = sc.n * (240 + 88)
@@ -552,7 +587,7 @@ def main():
             out["differentiation"] = differentiation_bench(20, 3, dev)
         if "scale_modification" in legs:
             out["scale_modification"] = scale_modification_bench(10, 3, dev, sc, t, cams[0], args.segment_tiles,
-                                                                 mufu_roofline)
+                                                                 composite_roofline)
         torch.cuda.empty_cache()
         if "mixture_study" in legs:
             out["mixture_study"] = mixture_study_bench(dev)
@@ -1094,7 +1129,8 @@ def scale_modification_bench(steps, warmup, dev, sc, t, cam, segment_tiles, roof
             # per pair: GEF lg2 + 2 ex2 (fwd and bwd) and 2 rcp (bwd); Gaussian form 1 ex2 and 1 rcp (bwd)
             entry["roofline_bwd"] = roofline_fn("k_render_bwd", entry["k_render_bwd_ms"], inr if gef else 0,
                                                 2 * inr if gef else inr, 2 * comp if gef else comp,
-                                                "MUFU work of this variant's pairs")
+                                                composite_fp32_ops(gef, inr, comp)[1],
+                                                "MUFU and FP32 work of this variant's pairs")
         # the oracle (FP64 brute force on the host) on a sample of pixels of the same view and variant
         op = {"rho": float(params.rho), "mode": int(params.falloff), "phi_mode": int(params.phi_mode)}
         t0 = time.perf_counter()
