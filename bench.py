@@ -766,16 +766,21 @@ def graph_replay_bench(frame, scene_c, gcam, params, img, T, nc, dL, grads, grad
     def rel(a, b):
         return float((a - b).norm()) / max(float(a.norm()), 1e-30)
 
+    names = ("means", "scales", "quats", "betas", "opacities", "shs")
+    worst = {n: [0.0, 0.0] for n in names}  # largest replay-vs-direct and direct-vs-direct differences
     for k, cam in enumerate(gcam):
         ref, ref2 = direct(cam), direct(cam)
         graphs[k].replay()
         torch.cuda.synchronize()
         got = [img] + list(grads)
         # the image is deterministic; the gradients are sums of atomics, equal up to their order: the
-        # replay must differ from the direct calls no more than two direct runs do (x10, or 1e-4)
+        # replay must differ from the direct calls no more than two direct runs do (x10), or than the
+        # gradients' parity tolerance (1e-3 relative)
         assert torch.equal(ref[0], got[0]), f"graph replay image differs from the direct calls ({k})"
-        for a, a2, b in zip(ref[1:], ref2[1:], got[1:]):
-            assert rel(a, b) <= max(10 * rel(a, a2), 1e-4), f"graph replay gradients differ ({k}): {rel(a, b)}"
+        for n, a, a2, b in zip(names, ref[1:], ref2[1:], got[1:]):
+            d, noise = rel(a, b), rel(a, a2)
+            worst[n] = [max(worst[n][0], d), max(worst[n][1], noise)]
+            assert d <= max(10 * noise, 1e-3), f"graph replay gradients differ ({k}, {n}): {d} (direct runs: {noise})"
         img.zero_()
         fwd_graphs[k].replay()
         torch.cuda.synchronize()
@@ -804,7 +809,10 @@ def graph_replay_bench(frame, scene_c, gcam, params, img, T, nc, dL, grads, grad
     return {"mpix_s": aggregate_mpix_s(ws, px, steps, ms), "ms_per_step": ms / steps,
             "fwd_mpix_s": aggregate_mpix_s(ws, px, steps, ms_f), "fwd_ms_per_frame": ms_f / steps,
             "what": "the fwd+bwd step (and the fwd alone) captured per camera as a CUDA graph and replayed "
-                    "(checked against the direct calls)"}
+                    "(checked against the direct calls)",
+            "check": {"image": "bitwise equal to the direct calls, every camera",
+                      "gradients_rel_l2_max": {n: {"replay_vs_direct": v[0], "direct_vs_direct": v[1]}
+                                               for n, v in worst.items()}}}
 
 
 def training_bench(steps, warmup, dev, sc, cams, segment_tiles):
