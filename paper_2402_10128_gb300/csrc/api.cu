@@ -546,7 +546,7 @@ ges_status ges_bin_sort(ges_frame* f, void* stream) {
   }
   {
     TraceScope tr(f->ctx, "scan_touched", s);
-    scan_exclusive<uint32_t, unsigned long long>(f->touched, f->offsets, f->n, f->d_K, f->scan, s);
+    scan_exclusive_onepass(f->touched, f->offsets, f->n, f->d_K, f->scan, f->d_flags, s);
   }
   if (f->auto_cap) {
     if ((e = cudaMemcpyAsync(f->h_K, f->d_K, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(e, "read K");

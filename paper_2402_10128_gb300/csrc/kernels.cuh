@@ -35,6 +35,12 @@ template <typename TIn, typename TOut>
 void scan_exclusive(const TIn* in, TOut* out, int64_t n, TOut* total, ScanScratch& sc, cudaStream_t s,
                     const unsigned long long* n_dev = nullptr);
 
+// the same for uint32 counts into 64-bit offsets, in one launch (decoupled look-back); a bounded
+// wait that gives up sets kFlagSortWait in *flags (when given).  Uses the scratch that
+// scan_exclusive would, so the two must not run at the same time on one ScanScratch.
+void scan_exclusive_onepass(const uint32_t* in, unsigned long long* out, int64_t n, unsigned long long* total,
+                            ScanScratch& sc, uint32_t* flags, cudaStream_t s, const unsigned long long* n_dev = nullptr);
+
 // per-primitive tile counts in depth order: touched[j] = tprim[sorted_vals[j]] for j < count
 // (count = min(*n_dev, n) if n_dev is given, else n)
 void launch_gather_touched(const uint32_t* sorted_vals, const uint32_t* tprim, int64_t n, uint32_t* touched,

@@ -721,6 +721,125 @@ void scan_exclusive(const TIn* in, TOut* out, int64_t n, TOut* total, ScanScratc
   scan_level<TIn, TOut>(in, out, n, n_dev, total, reinterpret_cast<char*>(sc.buf) + ScanScratch::kReserved, s);
 }
 
+// ---------------------------------------------------------------- single-pass scan
+// Exclusive scan of uint32 counts into 64-bit offsets in one launch, by the decoupled look-back of
+// the one-sweep sort: a CTA takes the next chunk from a counter (so a chunk's predecessors are
+// always running or done), publishes its chunk sum as an aggregate at once and its inclusive
+// prefix when its own is known; warp 0 looks back over 32 predecessors at a time.  Status words
+// are 64-bit: flag in bits 62-63 (1 aggregate, 2 inclusive prefix), value in bits 0-61.  The wait
+// is bounded: a CTA that gives up takes 0 for what it did not see, publishes its prefix, and sets
+// kFlagSortWait in *flags (the offsets are then wrong, the run ends).
+constexpr unsigned long long kScAgg = 1ull << 62, kScPre = 2ull << 62, kScValue = (1ull << 62) - 1ull;
+
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
+  return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+__device__ __forceinline__ void st_volatile_u64(unsigned long long* p, unsigned long long v) {
+  *reinterpret_cast<volatile unsigned long long*>(p) = v;
+}
+
+// status: [0] the chunk counter (low 32 bits), [1 + c] chunk c's word; all zero at launch
+__global__ void __launch_bounds__(kThreads) k_scan_onepass(const uint32_t* __restrict__ in,
+                                                           unsigned long long* __restrict__ out, int64_t cap,
+                                                           const unsigned long long* __restrict__ n_dev,
+                                                           unsigned long long* __restrict__ status,
+                                                           unsigned long long* __restrict__ total,
+                                                           uint32_t* __restrict__ flags) {
+  const int64_t n = scan_count(cap, n_dev);
+  const int64_t nchunks = (n + kChunk - 1) / kChunk;
+  __shared__ unsigned long long ws[kThreads / 32 + 1];
+  __shared__ unsigned long long s_prefix;
+  __shared__ int64_t s_chunk;
+  if (threadIdx.x == 0) s_chunk = (int64_t)atomicAdd(reinterpret_cast<unsigned int*>(status), 1u);
+  __syncthreads();
+  const int64_t c = s_chunk;
+  if (c >= nchunks) {
+    if (c == 0 && total && threadIdx.x == 0) *total = 0ull;  // nothing to scan
+    return;
+  }
+  const int64_t base = c * kChunk + (int64_t)threadIdx.x * kItems;
+  uint32_t v[kItems];
+  unsigned long long acc = 0;
+#pragma unroll
+  for (int k = 0; k < kItems; ++k) {
+    v[k] = (base + k < n) ? in[base + k] : 0u;
+    acc += v[k];
+  }
+  const unsigned long long inc = warp_inclusive_scan(acc);
+  const int w = threadIdx.x >> 5;
+  const unsigned lane = threadIdx.x & 31u;
+  if (lane == 31) ws[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    const unsigned long long x = (lane < kThreads / 32) ? ws[lane] : 0ull;
+    const unsigned long long xi = warp_inclusive_scan(x);
+    if (lane < kThreads / 32) ws[lane] = xi - x;
+    const unsigned long long agg = __shfl_sync(0xffffffffu, xi, 31);  // the chunk's sum
+    unsigned long long* my = status + 1 + c;
+    unsigned long long prefix = 0;
+    if (c == 0) {
+      if (lane == 0) st_volatile_u64(my, kScPre | (agg & kScValue));
+    } else {
+      if (lane == 0) st_volatile_u64(my, kScAgg | (agg & kScValue));
+      int64_t end = c;  // the window is chunks [end - 32, end), lane l reading end - 1 - l
+      int spins = 0;
+      bool fail = false;
+      for (;;) {
+        const int64_t idx = end - 1 - (int64_t)lane;
+        const unsigned long long sw = idx >= 0 ? ld_volatile_u64(status + 1 + idx) : kScPre;
+        const unsigned long long flag = sw & ~kScValue;
+        const unsigned pre = __ballot_sync(0xffffffffu, flag == kScPre);
+        const unsigned unset = __ballot_sync(0xffffffffu, flag == 0ull);
+        const int first = pre ? __ffs(pre) - 1 : 32;  // nearest predecessor with a prefix
+        const unsigned need = first >= 31 ? 0xffffffffu : ((2u << first) - 1u);
+        if (unset & need) {
+          if (++spins > kOsSpinLimit) {
+            fail = true;
+            break;
+          }
+          __nanosleep(32);
+          continue;
+        }
+        unsigned long long part = ((int)lane <= first) ? (sw & kScValue) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        prefix += part;
+        if (first < 32) break;
+        end -= 32;
+      }
+      if (lane == 0) {
+        st_volatile_u64(my, kScPre | ((prefix + agg) & kScValue));
+        if (fail && flags) atomicOr(flags, kFlagSortWait);
+      }
+    }
+    if (lane == 0) {
+      s_prefix = prefix;
+      if (c == nchunks - 1 && total) *total = prefix + agg;
+    }
+  }
+  __syncthreads();
+  unsigned long long run = inc - acc + ws[w] + s_prefix;
+#pragma unroll
+  for (int k = 0; k < kItems; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+}
+
+void scan_exclusive_onepass(const uint32_t* in, unsigned long long* out, int64_t n, unsigned long long* total,
+                            ScanScratch& sc, uint32_t* flags, cudaStream_t s, const unsigned long long* n_dev) {
+  if (n <= 0) {
+    if (total) cudaMemsetAsync(total, 0, sizeof(unsigned long long), s);
+    return;
+  }
+  const int64_t nchunks = cdiv(n, kChunk);
+  unsigned long long* status =
+      reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(sc.buf) + ScanScratch::kReserved);
+  cudaMemsetAsync(status, 0, (size_t)(nchunks + 1) * sizeof(unsigned long long), s);
+  k_scan_onepass<<<(unsigned)nchunks, kThreads, 0, s>>>(in, out, n, n_dev, status, total, flags);
+  count_launches(1);
+}
+
 template void scan_exclusive<uint32_t, uint32_t>(const uint32_t*, uint32_t*, int64_t, uint32_t*, ScanScratch&, cudaStream_t,
                                                  const unsigned long long*);
 template void scan_exclusive<uint32_t, unsigned long long>(const uint32_t*, unsigned long long*, int64_t,
