@@ -40,6 +40,8 @@ void scan_exclusive(const TIn* in, TOut* out, int64_t n, TOut* total, ScanScratc
 // scan_exclusive would, so the two must not run at the same time on one ScanScratch.
 void scan_exclusive_onepass(const uint32_t* in, unsigned long long* out, int64_t n, unsigned long long* total,
                             ScanScratch& sc, uint32_t* flags, cudaStream_t s, const unsigned long long* n_dev = nullptr);
+void scan_exclusive_onepass(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total, ScanScratch& sc,
+                            uint32_t* flags, cudaStream_t s, const unsigned long long* n_dev = nullptr);
 
 // per-primitive tile counts in depth order: touched[j] = tprim[sorted_vals[j]] for j < count
 // (count = min(*n_dev, n) if n_dev is given, else n)

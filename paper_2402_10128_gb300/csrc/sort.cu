@@ -738,13 +738,13 @@ __device__ __forceinline__ void st_volatile_u64(unsigned long long* p, unsigned 
   *reinterpret_cast<volatile unsigned long long*>(p) = v;
 }
 
-// status: [0] the chunk counter (low 32 bits), [1 + c] chunk c's word; all zero at launch
-__global__ void __launch_bounds__(kThreads) k_scan_onepass(const uint32_t* __restrict__ in,
-                                                           unsigned long long* __restrict__ out, int64_t cap,
+// status: [0] the chunk counter (low 32 bits), [1 + c] chunk c's word; all zero at launch.  in may
+// equal out: a CTA writes its chunk only after reading it.
+template <typename TOut>
+__global__ void __launch_bounds__(kThreads) k_scan_onepass(const uint32_t* in, TOut* out, int64_t cap,
                                                            const unsigned long long* __restrict__ n_dev,
                                                            unsigned long long* __restrict__ status,
-                                                           unsigned long long* __restrict__ total,
-                                                           uint32_t* __restrict__ flags) {
+                                                           TOut* __restrict__ total, uint32_t* __restrict__ flags) {
   const int64_t n = scan_count(cap, n_dev);
   const int64_t nchunks = (n + kChunk - 1) / kChunk;
   __shared__ unsigned long long ws[kThreads / 32 + 1];
@@ -754,7 +754,7 @@ __global__ void __launch_bounds__(kThreads) k_scan_onepass(const uint32_t* __res
   __syncthreads();
   const int64_t c = s_chunk;
   if (c >= nchunks) {
-    if (c == 0 && total && threadIdx.x == 0) *total = 0ull;  // nothing to scan
+    if (c == 0 && total && threadIdx.x == 0) *total = TOut(0);  // nothing to scan
     return;
   }
   const int64_t base = c * kChunk + (int64_t)threadIdx.x * kItems;
@@ -814,30 +814,41 @@ __global__ void __launch_bounds__(kThreads) k_scan_onepass(const uint32_t* __res
     }
     if (lane == 0) {
       s_prefix = prefix;
-      if (c == nchunks - 1 && total) *total = prefix + agg;
+      if (c == nchunks - 1 && total) *total = (TOut)(prefix + agg);
     }
   }
   __syncthreads();
   unsigned long long run = inc - acc + ws[w] + s_prefix;
 #pragma unroll
   for (int k = 0; k < kItems; ++k) {
-    if (base + k < n) out[base + k] = run;
+    if (base + k < n) out[base + k] = (TOut)run;
     run += v[k];
   }
 }
 
-void scan_exclusive_onepass(const uint32_t* in, unsigned long long* out, int64_t n, unsigned long long* total,
-                            ScanScratch& sc, uint32_t* flags, cudaStream_t s, const unsigned long long* n_dev) {
+template <typename TOut>
+static void scan_onepass_launch(const uint32_t* in, TOut* out, int64_t n, TOut* total, ScanScratch& sc,
+                                uint32_t* flags, cudaStream_t s, const unsigned long long* n_dev) {
   if (n <= 0) {
-    if (total) cudaMemsetAsync(total, 0, sizeof(unsigned long long), s);
+    if (total) cudaMemsetAsync(total, 0, sizeof(TOut), s);
     return;
   }
   const int64_t nchunks = cdiv(n, kChunk);
   unsigned long long* status =
       reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(sc.buf) + ScanScratch::kReserved);
   cudaMemsetAsync(status, 0, (size_t)(nchunks + 1) * sizeof(unsigned long long), s);
-  k_scan_onepass<<<(unsigned)nchunks, kThreads, 0, s>>>(in, out, n, n_dev, status, total, flags);
+  k_scan_onepass<TOut><<<(unsigned)nchunks, kThreads, 0, s>>>(in, out, n, n_dev, status, total, flags);
   count_launches(1);
+}
+
+void scan_exclusive_onepass(const uint32_t* in, unsigned long long* out, int64_t n, unsigned long long* total,
+                            ScanScratch& sc, uint32_t* flags, cudaStream_t s, const unsigned long long* n_dev) {
+  scan_onepass_launch<unsigned long long>(in, out, n, total, sc, flags, s, n_dev);
+}
+
+void scan_exclusive_onepass(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total, ScanScratch& sc,
+                            uint32_t* flags, cudaStream_t s, const unsigned long long* n_dev) {
+  scan_onepass_launch<uint32_t>(in, out, n, total, sc, flags, s, n_dev);
 }
 
 template void scan_exclusive<uint32_t, uint32_t>(const uint32_t*, uint32_t*, int64_t, uint32_t*, ScanScratch&, cudaStream_t,
@@ -914,7 +925,7 @@ bool radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_
       k_radix_hist<256><<<grid_cap(nchunks, 8), kThreads, 0, s>>>(keys[cur], n_host, n_dev, n_cap, shift, bits, hist,
                                                                   n_entries);
     }
-    scan_exclusive<uint32_t, uint32_t>(hist, hist, entries, (uint32_t*)nullptr, sc, s, n_entries);
+    scan_exclusive_onepass(hist, hist, entries, (uint32_t*)nullptr, sc, flags, s, n_entries);
     if (wide) {
       k_radix_scatter<512><<<grid_cap(nchunks, 2), kScThreads, sizeof(ScatterSmem<512>), s>>>(
           keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_host, n_dev, n_cap, shift, bits, hist);
