@@ -440,6 +440,9 @@ ges_status ges_frame_create(ges_ctx* ctx, int64_t n_capacity, int32_t width, int
   A((void**)&f->offsets, 8 * N);
   A((void**)&f->g2d, sizeof(float4) * 3 * N);
   A((void**)&f->ranges, sizeof(uint2) * f->n_tiles);
+  A((void**)&f->tile_bucket, 4 * f->n_tiles);
+  A((void**)&f->tile_order, 4 * f->n_tiles);
+  A((void**)&f->order_count, 4 * 2 * kOrderBuckets);
   A((void**)&f->d_K, 8);
   A((void**)&f->d_flags, 4);
   if (st == GES_OK) {
@@ -479,6 +482,9 @@ void ges_frame_destroy(ges_frame* f) {
   ctx_free(c, f->offsets, 8 * N);
   ctx_free(c, f->g2d, sizeof(float4) * 3 * N);
   ctx_free(c, f->ranges, sizeof(uint2) * f->n_tiles);
+  ctx_free(c, f->tile_bucket, 4 * f->n_tiles);
+  ctx_free(c, f->tile_order, 4 * f->n_tiles);
+  ctx_free(c, f->order_count, 4 * 2 * kOrderBuckets);
   ctx_free(c, f->d_K, 8);
   ctx_free(c, f->d_flags, 4);
   frame_free_keys(f);
@@ -629,8 +635,13 @@ ges_status ges_render_bwd(ges_frame* f, const ges_scene* scene, const float* fin
   if (f->n > 0 && (e = cudaMemsetAsync(f->g2d, 0, sizeof(float4) * 3 * f->n, s)) != cudaSuccess)
     return cuda_fail(e, "memset g2d");
   {
+    TraceScope tr(f->ctx, "tile_order", s);
+    launch_tile_order<FrameViews>(f->vt, f->n_tiles, f->tile_bucket, f->order_count, f->tile_order, s);
+  }
+  {
     TraceScope tr(f->ctx, "k_render_bwd", s);
-    launch_render_bwd<FrameViews>(f->vt, f->n_tiles, f->ranges, f->tile_keys, f->tile_vals, f->rec, f->P, f->g2d, s);
+    launch_render_bwd<FrameViews>(f->vt, f->n_tiles, f->ranges, f->tile_keys, f->tile_vals, f->rec, f->P, f->g2d, s,
+                                  f->tile_order);
   }
   {
     TraceScope tr(f->ctx, "k_preprocess_bwd", s);

@@ -60,6 +60,9 @@ struct ges_frame {
   ges::ScanScratch scan;
   // per tile
   uint2* ranges = nullptr;
+  uint32_t* tile_bucket = nullptr;   // the backward's cost class per tile
+  uint32_t* tile_order = nullptr;    // the backward's launch order: heavy tiles first
+  uint32_t* order_count = nullptr;   // [2 * kOrderBuckets]: tiles per class, then cursors
   // counters
   unsigned long long* d_K = nullptr;
   uint32_t* d_flags = nullptr;

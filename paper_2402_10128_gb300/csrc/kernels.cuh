@@ -89,6 +89,15 @@ void launch_render_fwd(const VS& vs, int64_t total_tiles, const uint2* ranges, c
                        unsigned long long* stats = nullptr, unsigned int* tile_counter = nullptr, int num_sms = 0);
 template <class VS>
 void launch_render_bwd(const VS& vs, int64_t total_tiles, const uint2* ranges, const uint32_t* keys,
-                       const uint32_t* vals, const Rec* rec, const Params& P, float4* g2d, cudaStream_t s);
+                       const uint32_t* vals, const Rec* rec, const Params& P, float4* g2d, cudaStream_t s,
+                       const uint32_t* order = nullptr);
+
+// Launch order of the backward's tiles, heaviest first: a tile's cost is the sum over its four 8x8
+// warp blocks of the largest n_contrib, binned on a log scale (kOrderBuckets classes, 8 per
+// octave); counts (2 * kOrderBuckets uint32, zeroed here) give each class its range of order[].
+constexpr int kOrderBuckets = 256;
+template <class VS>
+void launch_tile_order(const VS& vs, int64_t total_tiles, uint32_t* bucket, uint32_t* counts, uint32_t* order,
+                       cudaStream_t s);
 
 }  // namespace ges

@@ -331,11 +331,13 @@ template <class VS>
 __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__ VS vs, const uint2* __restrict__ ranges,
                                                          const uint32_t* __restrict__ keys,
                                                          const uint32_t* __restrict__ vals, const Rec* __restrict__ rec,
-                                                         const Params P, float4* __restrict__ g2d) {
+                                                         const Params P, float4* __restrict__ g2d,
+                                                         const uint32_t* __restrict__ order) {
   __shared__ Stage<RecPairB, kBatch> st;
   __shared__ uint32_t s_max_last;
   const auto& vt = vs.get();
-  const int64_t tile = blockIdx.x;
+  const int64_t tile = order ? (int64_t)order[blockIdx.x] : (int64_t)blockIdx.x;
+  if (tile >= (int64_t)vt.total_tiles) return;  // (order is a permutation of the tiles)
   const ViewDesc& vd = vt.v[view_of_tile(vt, tile)];
   const int lt = (int)(tile - vd.tile_base);
   const int tx = lt % vd.tiles_x, ty = lt / vd.tiles_x;
@@ -464,7 +466,88 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
   }
 }
 
+// The backward's tiles, heaviest first.  Tiles run in launch order as CTA slots free up, so with
+// the row-major order the heavy tiles of the image's middle meet the last wave and the kernel ends
+// on a few of them; longest-first keeps the SMs busy to the end.  A tile's cost is the sum over its
+// four 8x8 warp blocks of the block's largest n_contrib (each warp walks the list that far), plus
+// a constant for the staging; classes of 8 per octave are ordered by a counting sort (the order
+// inside a class follows the atomics, which changes nothing but the order of the gradient sums).
+template <class VS>
+__global__ void __launch_bounds__(kThreads) k_tile_cost(const __grid_constant__ VS vs, uint32_t* __restrict__ bucket,
+                                                        uint32_t* __restrict__ counts) {
+  __shared__ uint32_t s_cost;
+  const auto& vt = vs.get();
+  const int64_t tile = blockIdx.x;
+  const ViewDesc& vd = vt.v[view_of_tile(vt, tile)];
+  const WarpBlock wb = warp_block((int)(tile - vd.tile_base), vd.tiles_x);
+  uint32_t m = 0;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int y = wb.y + 4 * k;
+    if (wb.x < vd.W && y < vd.H) m = max(m, vd.n_contrib[(int64_t)y * vd.W + wb.x]);
+  }
+  m = __reduce_max_sync(0xffffffffu, m);
+  if (threadIdx.x == 0) s_cost = 0;
+  __syncthreads();
+  if ((threadIdx.x & 31u) == 0) atomicAdd(&s_cost, m);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const float c = (float)s_cost + 16.0f;
+    const int b = min(kOrderBuckets - 1, (int)(log2f(c) * 8.0f));
+    bucket[tile] = (uint32_t)b;
+    atomicAdd(&counts[b], 1u);
+  }
+}
+
+// order[start(b) + i] = the i-th tile of class b to arrive, start(b) = the tiles of heavier classes
+__global__ void __launch_bounds__(kThreads) k_tile_order(int64_t total, const uint32_t* __restrict__ bucket,
+                                                         uint32_t* __restrict__ counts, uint32_t* __restrict__ order) {
+  __shared__ uint32_t start[kOrderBuckets];
+  for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) start[b] = counts[b];
+  __syncthreads();
+  if (threadIdx.x < 32) {  // exclusive scan from the heaviest class down, 8 classes per lane
+    const unsigned lane = threadIdx.x;
+    uint32_t v[kOrderBuckets / 32], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kOrderBuckets / 32; ++k) {
+      v[k] = start[kOrderBuckets - 1 - (int)(lane * (kOrderBuckets / 32) + k)];
+      sum += v[k];
+    }
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if ((int)lane >= o) inc += y;
+    }
+    uint32_t run = inc - sum;
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < kOrderBuckets / 32; ++k) {
+      start[kOrderBuckets - 1 - (int)(lane * (kOrderBuckets / 32) + k)] = run;
+      run += v[k];
+    }
+  }
+  __syncthreads();
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < total) {
+    const uint32_t b = bucket[t];
+    const uint32_t pos = start[b] + atomicAdd(&counts[kOrderBuckets + b], 1u);
+    if ((int64_t)pos < total) order[pos] = (uint32_t)t;
+  }
+}
+
 }  // namespace
+
+template <class VS>
+void launch_tile_order(const VS& vs, int64_t total_tiles, uint32_t* bucket, uint32_t* counts, uint32_t* order,
+                       cudaStream_t s) {
+  if (total_tiles <= 0) return;
+  cudaMemsetAsync(counts, 0, sizeof(uint32_t) * 2 * kOrderBuckets, s);
+  k_tile_cost<VS><<<(unsigned)total_tiles, kThreads, 0, s>>>(vs, bucket, counts);
+  k_tile_order<<<(unsigned)((total_tiles + kThreads - 1) / kThreads), kThreads, 0, s>>>(total_tiles, bucket, counts,
+                                                                                          order);
+  count_launches(2);
+}
 
 template <class VS>
 void launch_render_fwd(const VS& vs, int64_t total_tiles, const uint2* ranges, const uint32_t* keys,
@@ -487,9 +570,10 @@ void launch_render_fwd(const VS& vs, int64_t total_tiles, const uint2* ranges, c
 
 template <class VS>
 void launch_render_bwd(const VS& vs, int64_t total_tiles, const uint2* ranges, const uint32_t* keys,
-                       const uint32_t* vals, const Rec* rec, const Params& P, float4* g2d, cudaStream_t s) {
+                       const uint32_t* vals, const Rec* rec, const Params& P, float4* g2d, cudaStream_t s,
+                       const uint32_t* order) {
   if (total_tiles <= 0) return;
-  k_render_bwd<VS><<<(unsigned)total_tiles, kThreads, 0, s>>>(vs, ranges, keys, vals, rec, P, g2d);
+  k_render_bwd<VS><<<(unsigned)total_tiles, kThreads, 0, s>>>(vs, ranges, keys, vals, rec, P, g2d, order);
   count_launches(1);
 }
 
@@ -500,6 +584,7 @@ template void launch_render_fwd<BatchViews>(const BatchViews&, int64_t, const ui
                                             const Rec*, const Params&, cudaStream_t, unsigned long long*, unsigned int*,
                                             int);
 template void launch_render_bwd<FrameViews>(const FrameViews&, int64_t, const uint2*, const uint32_t*, const uint32_t*,
-                                            const Rec*, const Params&, float4*, cudaStream_t);
+                                            const Rec*, const Params&, float4*, cudaStream_t, const uint32_t*);
+template void launch_tile_order<FrameViews>(const FrameViews&, int64_t, uint32_t*, uint32_t*, uint32_t*, cudaStream_t);
 
 }  // namespace ges
