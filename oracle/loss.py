@@ -1,4 +1,4 @@
-"""FP64 oracle of the training image loss (Sec. 3.3, Eq. mask, Eq. laplace, Eq. final) -- TEST
+"""FP64 oracle of the training image loss (Sec. 4.3, Eq. mask, Eq. laplace, Eq. final) -- TEST
 INFRASTRUCTURE ONLY, like the rest of this package.
 
     L = lambda_L1 L1 + lambda_ssim (1 - SSIM) + lambda_omega L_omega,
@@ -7,7 +7,7 @@ INFRASTRUCTURE ONLY, like the rest of this package.
     M_omega = 1(|DoG_omega(I_gt)| / max |DoG_omega(I_gt)| > 0.5)                  (Eq. mask)
     DoG_omega = G(., 0.2 + 20 omega) - G(., 0.1 + 10 omega), on the ground truth's channel mean
                 downsampled by the image-frequency scale (App. Implementation Details, 0.2)
-    for omega <= 1/2 the mask is 1 - M_(1 - omega) (Sec. 3.3, last paragraph)
+    for omega <= 1/2 the mask is 1 - M_(1 - omega) (Sec. 4.3, last paragraph)
 
 Readings of the passages the paper leaves open (the kernels implement the same):
   * blur: separable, weights exp(-k^2 / (2 sigma^2)) for |k| <= ceil(3 sigma), normalised to sum 1,

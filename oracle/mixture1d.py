@@ -1,4 +1,4 @@
-"""FP64 oracle of the 1D mixture-fitting study (Sec. 3.5 "Assessing 1D GEF Mixtures"; App. A) --
+"""FP64 oracle of the 1D mixture-fitting study (Sec. 3.2 "Assessing 1D GEF Mixtures"; App. A) --
 TEST INFRASTRUCTURE ONLY, like the rest of this package.
 
 Models, N components, parameters per component (weight w, mean mu, scale sigma (gamma for the LoG),

@@ -1,4 +1,4 @@
-"""FP64 oracle of the training-side updates (Sec. 3.4; App. B.2) -- TEST INFRASTRUCTURE ONLY,
+"""FP64 oracle of the training-side updates (Sec. 4.4; App. B.2) -- TEST INFRASTRUCTURE ONLY,
 like the rest of this package.
 
 The paper keeps the optimisation and density control of Gaussian splatting (Kerbl et al. 2023)

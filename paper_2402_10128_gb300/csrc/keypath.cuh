@@ -74,7 +74,7 @@ __device__ __forceinline__ float key_lgamma(float x) {
   return ksub(lg, kmul(key_log2(acc), ln2));
 }
 
-// The scale modification phi(beta) (Sec. 3.2) applied to the scale vector:
+// The scale modification phi(beta) (Sec. 4.2) applied to the scale vector:
 //   phi_mode 0: phi_bar_rho(beta) = 2 / (1 + 2^(-rho (beta - 2) log2 e))                   Eq. approx
 //   phi_mode 1: phi_n(beta) = 2 Gamma(3/beta) / Gamma(1/beta)                            Eq. probablity
 //               = 2^((ln Gamma(3/beta) - ln Gamma(1/beta) + ln 2) log2 e), 1 at beta = 2

@@ -1,4 +1,4 @@
-// The training image loss that consumes the rendered image (Sec. 3.3 and Eq. final):
+// The training image loss that consumes the rendered image (Sec. 4.3 and Eq. final):
 //   L = lambda_L1 L1 + lambda_ssim (1 - SSIM) + lambda_omega L_omega,  lambda_L1 = 1 - lambda_ssim - lambda_omega,
 //   L_omega = mean |(I - I_gt) M_omega|                                               (Eq. laplace)
 //   M_omega = 1(|DoG_omega(I_gt)| / max |DoG_omega(I_gt)| > threshold)                (Eq. mask)

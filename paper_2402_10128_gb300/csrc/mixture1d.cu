@@ -1,4 +1,4 @@
-// The 1D mixture-fitting study (Sec. 3.5; App. A): mixtures of N Gaussians, differences of
+// The 1D mixture-fitting study (Sec. 3.2; App. A): mixtures of N Gaussians, differences of
 // Gaussians (variance ratio nu = 4), Laplacians of Gaussians or generalized exponentials
 //   GEF: h(x) = sum_i w_i exp(-|x - mu_i|^beta_i / (2 sigma_i^2 + eps))            (Eq. genmixture)
 // fitted to 1D signals by full-batch Adam on the mean squared error, many runs at once; and the

@@ -1,4 +1,4 @@
-// Training-side updates over the primitives' SoA parameters (Sec. 3.4; App. B.2): the fused Adam
+// Training-side updates over the primitives' SoA parameters (Sec. 4.4; App. B.2): the fused Adam
 // step, the densification statistics, density control (clone, split, prune) and the opacity and
 // shape resets.  The paper keeps Gaussian splatting's optimisation and density control and adds
 // the shape reset and shape pruning; App. B.2 lists the constants.

@@ -6,11 +6,11 @@ the CUDA path's callers and the FP64 oracle's tests take their inputs from.
 
 Every generator uses ``numpy.random.default_rng(seed)`` (PCG64), so a scene is
 a pure function of its arguments.  Shapes follow the paper's primitive set
-(Sec. 3.1): mean mu[N,3], scale s[N,3] (> 0), quaternion q[N,4] in (w,x,y,z)
+(Sec. 4.1): mean mu[N,3], scale s[N,3] (> 0), quaternion q[N,4] in (w,x,y,z)
 order, shape beta[N] (> 0), opacity kappa[N] in (0,1), and spherical-harmonic
 coefficients sh[N,(d+1)^2,3].
 
-Workload recipes (sizes of the paper's scenes, Sec. 4 and Table 1; the
+Workload recipes (sizes of the paper's scenes, Sec. 6.2 and Tab. comparisons; the
 datasets themselves are not used):
 
 * ``cube_scene``  -- means uniform in [-1,1]^3, scales log-uniform

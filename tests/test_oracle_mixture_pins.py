@@ -1,7 +1,7 @@
 """Pins of the 1D mixture-fitting oracle (oracle/mixture1d.py): the signals' and models' closed
 forms (App. A), the gradient by central differences, the first Adam step in closed form, and the
 study's finding that a GEF mixture fits the square better than a Gaussian mixture with as many
-components (Sec. 3.5, Fig. 1 b-c and the loss-stability figure)."""
+components (Sec. 3.2, Fig. 1 b-c and the loss-stability figure)."""
 import math
 
 import numpy as np
@@ -86,7 +86,7 @@ def test_first_adam_step_and_history():
 
 
 def test_gef_fits_the_square_better_than_gaussians():
-    """Sec. 3.5: a GEF mixture approximates the band-unlimited square with lower loss than a
+    """Sec. 3.2: a GEF mixture approximates the band-unlimited square with lower loss than a
     Gaussian mixture of as many components (here N = 2, 6 seeds, 600 epochs; mean final MSE)."""
     x = np.linspace(-1, 1, 1000)
     y = om.signal("square", x)
