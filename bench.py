@@ -245,7 +245,7 @@ def cpu_baseline(sc, cams, pixels, cores):
                                      "sample": "the 2,000-primitive 128x128 case end to end, brute force fwd + bwd"}}
 
 
-def serving_bench(n_requests, rate_mults, slots, dev, seed=40):
+def serving_bench(n_requests, rate_mults, slots, dev, seed=40, hbm_budget_gib=48):
     """Serving workload: 4 resident scenes (cube generator, SH3: 0.3M/0.8M/1.5M/3M primitives),
     requests at 800x800 / 1245x825 / 1920x1080 from random cameras, Poisson arrivals.  The same
     arrival trace is served (a) by the batched server (continuous batching, captured-graph
@@ -264,8 +264,21 @@ def serving_bench(n_requests, rate_mults, slots, dev, seed=40):
     # (b) per-request path: one frame per resolution (sized for the largest scene), images copied to host
     dev_scenes = [render.scene_tensors(sc, dev) for sc in scs]
     frames = {}
-    host_out = [np.empty((3, c.height, c.width), np.float32) for c in cams]
     n_max = max(sc.n for sc in scs)
+    # host images: a free list per resolution; a buffer goes back once its request has been polled
+    pool = {}
+    pool_lock = threading.Lock()
+
+    def take(c):
+        with pool_lock:
+            free = pool.setdefault((c.width, c.height), [])
+            return free.pop() if free else np.empty((3, c.height, c.width), np.float32)
+
+    def give(a):
+        with pool_lock:
+            pool[(a.shape[2], a.shape[1])].append(a)
+
+    pr_out = {}
 
     def per_request(i):
         w = which[i]
@@ -274,8 +287,9 @@ def serving_bench(n_requests, rate_mults, slots, dev, seed=40):
         fr = frames.get(key)
         if fr is None:
             fr = frames[key] = render.Frame(n_max, c.width, c.height, key_capacity=0, ctx=ctx)
+            pr_out[key] = np.empty((3, c.height, c.width), np.float32)
         img, _, _ = fr.forward(dev_scenes[w], 3, gcams[i])
-        host_out[i][...] = img.cpu().numpy()
+        pr_out[key][...] = img.cpu().numpy()
 
     for i in range(min(12, n_requests)):  # warm-up: frames, capacities
         per_request(i)
@@ -286,16 +300,22 @@ def serving_bench(n_requests, rate_mults, slots, dev, seed=40):
     service = (time.perf_counter() - t0) / n_requests
     capacity = 1.0 / service  # requests/s of back-to-back per-request launches
 
-    srv = ges.ges_serve_create(ctx.handle, ges.params_default(), slots)
+    # the server's own context: its HBM budget bounds the resident scenes and both workspaces
+    budget = hbm_budget_gib << 30
+    sctx = render.Context(dev.index or 0, hbm_budget_bytes=budget)
+    srv = ges.ges_serve_create(sctx.handle, ges.params_default(), slots)
     keep = []
     for sc in scs:
         arrs = [np.ascontiguousarray(a, np.float32) for a in sc.arrays()]
         keep.append(arrs)
         ges.ges_serve_add_scene(srv, ges.make_scene(*arrs, sc.sh_degree))
+    resident = sum(a.nbytes for arrs in keep for a in arrs)
     # warm-up of the server (workspaces, graphs)
     for i in range(min(16, n_requests)):
-        t = ges.ges_serve_submit(srv, int(which[i]), gcams[i], host_out[i])
+        o = take(cams[i])
+        t = ges.ges_serve_submit(srv, int(which[i]), gcams[i], o)
         ges.ges_serve_poll(srv, t, 120_000_000)
+        give(o)
 
     results = []
     for mult in rate_mults:
@@ -303,6 +323,7 @@ def serving_bench(n_requests, rate_mults, slots, dev, seed=40):
         arrivals = np.cumsum(rng.exponential(1.0 / rate, n_requests))
         # (a) server
         tickets = [None] * n_requests
+        bufs = [None] * n_requests
         t_start = time.perf_counter() + 0.01
 
         def submitter():
@@ -310,7 +331,8 @@ def serving_bench(n_requests, rate_mults, slots, dev, seed=40):
                 dt = t_start + arrivals[i] - time.perf_counter()
                 if dt > 0:
                     time.sleep(dt)
-                tickets[i] = ges.ges_serve_submit(srv, int(which[i]), gcams[i], host_out[i])
+                bufs[i] = take(cams[i])
+                tickets[i] = ges.ges_serve_submit(srv, int(which[i]), gcams[i], bufs[i])
 
         th = threading.Thread(target=submitter)
         th.start()
@@ -321,6 +343,8 @@ def serving_bench(n_requests, rate_mults, slots, dev, seed=40):
             st, lat = ges.ges_serve_poll(srv, tickets[i], 120_000_000)
             assert st == ges.GES_OK
             lat_srv.append(lat)
+            give(bufs[i])
+            bufs[i] = None
         th.join()
         t_end_srv = time.perf_counter()
         span_srv = t_end_srv - t_start
@@ -342,11 +366,16 @@ def serving_bench(n_requests, rate_mults, slots, dev, seed=40):
             "per_request": {"p50_ms": float(np.percentile(lat_pr, 50)), "p99_ms": float(np.percentile(lat_pr, 99)),
                             "req_s": n_requests / span_pr, "mpix_s": pix / span_pr / 1e6}})
     ges.ges_serve_destroy(srv)
+    sctx.close()
     for fr in frames.values():
         fr.close()
     return {"workload": "4 resident cube scenes (0.3M/0.8M/1.5M/3M prims, SH3); 800x800/1245x825/1920x1080 "
                         "requests, random cameras at radius 3-5, Poisson arrivals",
-            "requests": n_requests, "slots": slots, "per_request_service_ms": 1e3 * service,
+            "requests": n_requests, "slots": slots, "hbm_budget_bytes": budget, "resident_scene_bytes": resident,
+            "admission": "two workspaces share what the budget leaves after the resident scenes; each batch "
+                         "takes queued requests in order while they fit a workspace's primitive, tile, pixel "
+                         "and slot capacities",
+            "per_request_service_ms": 1e3 * service,
             "per_request_capacity_req_s": capacity, "rates": results}
 
 
@@ -361,7 +390,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=N_PRIMS)
-    ap.add_argument("--serve-requests", type=int, default=100)
+    ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the differentiation and stress legs")
@@ -369,6 +398,7 @@ def main():
                                        "stress_beta2",
                     help="comma-separated extra legs to run (default: all)")
     ap.add_argument("--segment-tiles", type=int, default=16, help="binning granularity (ges_params.segment_tiles)")
+    ap.add_argument("--full-json", default="", help="write every leg in full to this JSON file")
     ap.add_argument("--profile", action="store_true",
                     help="minimal run for ncu: no work counters, e2e or CPU baseline; warmup + steps fwd+bwd")
     args = ap.parse_args()
@@ -552,63 +582,161 @@ def main():
     pre_gbs = pre_bytes / (kernel_ms["k_preprocess"] / 1e3) / 1e9
     hbm = float(peaks.get("hbm_gbs", 6800.0))
 
-    out = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": graph["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "scene-scale: 1.5M clustered GEF primitives (64 clusters + 10% shell), SH3, "
-                                  "beta log-U[0.5,8], 1245x825, 20 orbit cameras; step = fwd+bwd of one view",
-                      "n_prims": sc.n, "width": WIDTH, "height": HEIGHT, "cameras": len(cams),
-                      "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                      "l2": "inputs larger than L2 (scene 360 MB, key lists ~%d MB)" % int(mean_K * 16 / 1e6)},
-           "fwd_mpix_s": fwd_rate, "fwd_ms_per_frame": graph["fwd_ms_per_frame"],
-           "stage_ms": dict(zip(stage_names, [float(x) for x in st_mean])),
-           "dominant_stage": stage_names[dom],
-           "frame_stats": {"K_mean": mean_K, "evaluated_pairs_mean": mean_eval, "in_extent_pairs_mean": mean_inr,
-                           "composited_pairs_mean": mean_comp},
-           "roofline": roofline, "roofline_fwd": roofline_fwd, "sfu_rates": sfu,
-           "preprocess_hbm": {"kernel": "k_preprocess", "achieved_gbs": pre_gbs, "peak_gbs": hbm, "frac": pre_gbs / hbm,
-                              "bytes_per_prim": 328},
-           "kernel_ms": kernel_ms, "graph_replay": graph,
-           "direct_calls": {"mpix_s": direct, "ms_per_step": ms_fb / args.steps, "fwd_mpix_s": fwd_direct,
-                            "fwd_ms_per_frame": ms_f / args.steps,
-                            "what": "the same steps as four C-ABI calls each, traced (the per-kernel times above)"},
-           "gpu_launches": int(launches), "clocks": clocks}
+    full = {}  # every leg in full; written to --full-json
 
+    def leg(name, d, summary=None):
+        """Record a leg and print its line (rank 0): the summary, or the leg itself cut to fit."""
+        full[name] = d
+        if rank == 0:
+            print(json.dumps(_fit(dict({"leg": name}, **(summary if summary is not None else d)))), flush=True)
+
+    roof = {k: roofline[k] for k in ("kernel", "bound", "binding", "achieved", "peak", "unit", "frac", "traffic")}
+    roof["floors_ms"] = {k: v["floor_ms"] for k, v in roofline["resources"].items()}
+    leg("composite_rooflines", {"k_render_bwd": roofline, "k_render_fwd": roofline_fwd, "sfu_rates": sfu,
+                                "preprocess_hbm": {"kernel": "k_preprocess", "achieved_gbs": pre_gbs, "peak_gbs": hbm,
+                                                   "frac": pre_gbs / hbm, "bytes_per_prim": 328}},
+        summary={"k_render_bwd": roof,
+                 "k_render_fwd": {k: roofline_fwd[k] for k in ("binding", "achieved", "peak", "unit", "frac")},
+                 "k_render_fwd_floors_ms": {k: v["floor_ms"] for k, v in roofline_fwd["resources"].items()},
+                 "work_per_frame": roofline["work"],
+                 "rates_per_sm_per_clk": sfu.get("per_sm_per_clk"),
+                 "k_preprocess": {"bound": "hbm", "achieved_gbs": pre_gbs, "peak_gbs": hbm, "frac": pre_gbs / hbm,
+                                  "bytes_per_prim": 328}})
+    leg("kernels", {"kernel_ms": kernel_ms, "stage_ms": dict(zip(stage_names, [float(x) for x in st_mean])),
+                    "dominant_stage": stage_names[dom],
+                    "frame_stats": {"K_mean": mean_K, "evaluated_pairs_mean": mean_eval,
+                                    "in_extent_pairs_mean": mean_inr, "composited_pairs_mean": mean_comp},
+                    "direct_calls": {"mpix_s": direct, "ms_per_step": ms_fb / args.steps, "fwd_mpix_s": fwd_direct,
+                                     "fwd_ms_per_frame": ms_f / args.steps,
+                                     "what": "the same steps as four C-ABI calls each, traced"},
+                    "graph_replay": {k: graph[k] for k in ("mpix_s", "ms_per_step", "fwd_mpix_s", "fwd_ms_per_frame")},
+                    "graph_check": graph["check"]["image"]})
+    leg("graph_replay_check", graph["check"])
+
+    e2e_res = None
     if not args.no_e2e:
-        out["e2e"] = e2e(args, sc, gcam, frame, params, dev, stream, ws, dist)
-        out["e2e_full_transfer"] = e2e(args, sc, gcam, frame, params, dev, stream, ws, dist, full_transfer=True)
+        e2e_res = e2e(args, sc, gcam, frame, params, dev, stream, ws, dist)
+        leg("e2e", e2e_res)
+        leg("e2e_full_transfer", e2e(args, sc, gcam, frame, params, dev, stream, ws, dist, full_transfer=True))
+    cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(sc, cams, args.cpu_pixels, os.cpu_count() or 1)
+        cpu = cpu_baseline(sc, cams, args.cpu_pixels, os.cpu_count() or 1)
+        leg("cpu_baseline", cpu)
     if not args.no_extra:
         legs = set(x for x in args.extra.split(",") if x)
         if "image_loss" in legs:
-            out["image_loss"] = loss_bench(50, 3, dev, img)
+            leg("image_loss", loss_bench(50, 3, dev, img))
         if "differentiation" in legs:
-            out["differentiation"] = differentiation_bench(20, 3, dev)
+            leg("differentiation", differentiation_bench(20, 3, dev))
         if "scale_modification" in legs:
-            out["scale_modification"] = scale_modification_bench(10, 3, dev, sc, t, cams[0], args.segment_tiles,
-                                                                 composite_roofline)
+            r = scale_modification_bench(10, 3, dev, sc, t, cams[0], args.segment_tiles, composite_roofline)
+            leg("scale_modification", r, summary={
+                "workload": r["workload"],
+                "variants": {k: {"fwd_bwd_ms": v["fwd_bwd"]["ms_per_frame"], "fwd_ms": v["fwd"]["ms_per_frame"],
+                                 "K": v["K_entries"], "composited": v["pairs"]["composited_pairs"],
+                                 "bwd_ms": v["k_render_bwd_ms"],
+                                 "bwd_frac": v.get("roofline_bwd", {}).get("frac"),
+                                 "oracle_mpix_s": v["cpu_baseline"]["value"]}
+                             for k, v in r["variants"].items()}})
         torch.cuda.empty_cache()
         if "mixture_study" in legs:
-            out["mixture_study"] = mixture_study_bench(dev)
+            leg("mixture_study", mixture_study_bench(dev))
         if "training" in legs:
-            out["training"] = training_bench(20, 3, dev, sc, cams, args.segment_tiles)
+            leg("training", training_bench(20, 3, dev, sc, cams, args.segment_tiles))
             torch.cuda.empty_cache()
         if "stress" in legs:
-            out["stress"] = stress_bench(5, 3, dev, beta2=False, segment_tiles=256)
+            leg("stress", stress_bench(5, 3, dev, beta2=False, segment_tiles=256))
             torch.cuda.empty_cache()
         if "stress_beta2" in legs:
-            out["stress_beta2"] = stress_bench(5, 3, dev, beta2=True, segment_tiles=args.segment_tiles)
+            leg("stress_beta2", stress_bench(5, 3, dev, beta2=True, segment_tiles=args.segment_tiles))
             torch.cuda.empty_cache()
+    serving = None
     if not args.no_serve:
         del t, grads
         frame.close()
         torch.cuda.empty_cache()
-        out["serving"] = serving_bench(args.serve_requests, (0.5, 1.0, 2.0), args.serve_slots, dev)
+        serving = serving_bench(args.serve_requests, (0.5, 1.0, 2.0), args.serve_slots, dev)
+        leg("serving", serving)
+
+    head = headline(ws, args.steps, args.warmup, value, graph, mean_K, roof, launches, clocks, e2e_res, cpu,
+                    serving)
+    full["headline"] = head
+    if rank == 0 and args.full_json:
+        with open(args.full_json, "w") as f:
+            json.dump(full, f, indent=1)
     if rank == 0:
-        print(json.dumps(out))
+        print(headline_line(head), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def headline(ws, steps, warmup, value, graph, mean_K, roof, launches, clocks, e2e_res, cpu, serving):
+    """The headline record: the fwd+bwd rate of the scene-scale step with the forward rate, the
+    dominant kernel's roofline, the end-to-end rate, the oracle's rate on the host, the serving
+    latencies at each arrival rate and the clocks seen."""
+    head = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": ws, "steps": steps,
+            "warmup": warmup, "ms_per_step": graph["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "scene-scale fwd+bwd: 1.5M clustered GEF primitives, SH3, beta log-U[0.5,8], "
+                                   "1245x825, 20 orbit cameras; one view per step",
+                       "l2": "inputs larger than L2 (scene 360 MB, lists ~%d MB)" % int(mean_K * 16 / 1e6),
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "fwd_mpix_s": graph["fwd_mpix_s"], "fwd_ms_per_frame": graph["fwd_ms_per_frame"],
+            "roofline": roof,
+            "gpu_launches": int(launches), "clocks": clocks}
+    if e2e_res is not None:
+        head["e2e"] = {k: e2e_res[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step",
+                                                "what")}
+    if cpu is not None:
+        head["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if serving is not None:
+        head["serving"] = {"requests_per_rate": serving["requests"],
+                           **{f"x{r['rate_mult']:g}": {m: [r[m]["p50_ms"], r[m]["p99_ms"], r[m]["req_s"]]
+                                                       for m in ("batched", "per_request")}
+                              for r in serving["rates"]},
+                           "fields": "p50 ms, p99 ms, req/s"}
+    return head
+
+
+def headline_line(head, limit=2000):
+    """The headline as one JSON line of at most `limit` characters (floats to 5 significant
+    digits; the serving summary, then the roofline's floors, give way if it is longer)."""
+    head = dict(head)
+    line = json.dumps(_round(head, 5))
+    for drop in ("serving", "floors_ms"):
+        if len(line) <= limit:
+            break
+        if drop == "floors_ms":
+            head["roofline"] = {k: v for k, v in head["roofline"].items() if k != "floors_ms"}
+        else:
+            head.pop(drop, None)
+        line = json.dumps(_round(head, 5))
+    return line
+
+
+def _round(o, sig=4):
+    """Floats rounded to `sig` significant digits, recursively (for short printed lines)."""
+    if isinstance(o, float):
+        return float(f"{o:.{sig}g}") if np.isfinite(o) else None
+    if isinstance(o, dict):
+        return {k: _round(v, sig) for k, v in o.items()}
+    if isinstance(o, (list, tuple)):
+        return [_round(v, sig) for v in o]
+    return o
+
+
+def _fit(d, limit=1900):
+    """A leg's printed form: floats to 4 significant digits; while the line is longer than
+    `limit` characters, the largest top-level entry is replaced by the note that it is only in
+    the full record."""
+    d = _round(d)
+    cut = []
+    while len(json.dumps(d)) > limit:
+        big = max((k for k in d if k != "leg"), key=lambda k: len(json.dumps(d[k])))
+        d.pop(big)
+        cut.append(big)
+        d["omitted"] = cut
+    return d
 
 
 def _ssim(x, y):
@@ -1105,7 +1233,7 @@ def stress_bench(steps, warmup, dev, beta2, segment_tiles):
 
 
 def scale_modification_bench(steps, warmup, dev, sc, t, cam, segment_tiles, roofline_fn=None, cpu_pixels=1000):
-    """The scale-modification variants (Sec. 3.2 and the ablation's shape strengths) on one view of
+    """The scale-modification variants (Sec. 4.2 and the ablation's shape strengths) on one view of
     the scene-scale workload: phi_bar_rho at rho = 0.1 (default), 0 and 10, the exact normalised
     Gamma ratio on the scale vector and on the variance, and the Gaussian-form rasterizer.  The
     exact ratio makes small-beta primitives far larger (240x at beta = 1/2), hence more list entries
@@ -1152,12 +1280,13 @@ def scale_modification_bench(steps, warmup, dev, sc, t, cam, segment_tiles, roof
 
 def e2e(args, sc, gcam, frame, params, dev, stream, ws, dist, full_transfer=False):
     """The fwd+bwd step through the C-ABI with host buffers.  Default: the scene is the model,
-    uploaded once from pinned host memory before the timed region (as weights are), and every step
+    uploaded once from pinned host memory before the timed region (as weights are); every step
     copies its input in (the upstream gradient dL/dI, 12 MB; the camera travels by value) and its
-    result out (the rendered image, 12 MB).  full_transfer: the scene is copied in and all its
-    gradients copied out every step as well (372 MB each way).  The copies are pipelined against
-    the kernels: two slots of device buffers; step i's inputs travel on one copy stream while step
-    i-1 computes, and its results travel back on another while step i+1 computes."""
+    results out: the rendered image (12 MB) and the gradients of every primitive parameter
+    (360 MB at SH3), the step's product.  full_transfer: the scene is copied in every step as well
+    (372 MB in, 372 MB out).  The copies are pipelined against the kernels: two slots of device
+    buffers; step i's inputs travel on one copy stream while step i-1 computes, and its results
+    travel back on another while step i+1 computes."""
     import torch
     from paper_2402_10128_gb300 import ges
     host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in sc.arrays()]
@@ -1171,7 +1300,7 @@ def e2e(args, sc, gcam, frame, params, dev, stream, ws, dist, full_transfer=Fals
         slots.append(dict(dev_in=dev_in, dL=torch.empty_like(dL_h, device=dev), grads=grads,
                           img=torch.empty((3, HEIGHT, WIDTH), device=dev),
                           img_h=torch.empty((3, HEIGHT, WIDTH)).pin_memory(),
-                          grads_h=[torch.empty(h.shape).pin_memory() for h in host] if full_transfer else [],
+                          grads_h=[torch.empty(h.shape).pin_memory() for h in host],
                           scene=ges.make_scene(*dev_in, sc.sh_degree), grads_c=ges.make_grads(*grads),
                           in_ready=torch.cuda.Event(), computed=torch.cuda.Event(), out_done=torch.cuda.Event(),
                           used=False))
@@ -1225,12 +1354,11 @@ def e2e(args, sc, gcam, frame, params, dev, stream, ws, dist, full_transfer=Fals
     s1.record(stream)
     torch.cuda.synchronize()
     ms = max_over_ranks(s0.elapsed_time(s1), dist, dev)
-    what = ("scene and upstream gradient copied in, image and all gradients copied out, every step" if full_transfer
-            else "scene resident (uploaded from pinned host memory before timing); per step the upstream gradient "
-                 "copied in and the rendered image copied out")
+    what = ("per step: scene and dL/dI in; image and all gradients out" if full_transfer
+            else "scene resident (uploaded once, as weights); per step: dL/dI in; image and all gradients out")
     return {"value": aggregate_mpix_s(ws, WIDTH * HEIGHT, args.steps, ms), "unit": "Mpix/s",
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": ms / args.steps,
-            "transfers": what,
+            "what": what,
             "overlap": "copies pipelined against the kernels (two buffer slots, one copy stream per direction)"}
 
 
