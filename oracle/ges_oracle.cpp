@@ -242,10 +242,10 @@ bool row_span(const KeyOut& k, const RowConsts& rc, int ty, int& tx0, int& tx1) 
   const float xl = ((u + rc.sl * dmin) - wl) - k.margin_abs;
   float f0 = std::floor(xl * 0.0625f), f1 = std::floor(xr * 0.0625f);
   const float r0 = (float)k.rect[0], r1 = (float)(k.rect[2] - 1);
-  f0 = std::fmin(std::fmax(f0, r0), r1);
-  f1 = std::fmin(std::fmax(f1, r0), r1);
-  tx0 = (int)f0;
-  tx1 = (int)f1;
+  // the span intersected with the box's columns: empty when it lies wholly to one side
+  if (!(f1 >= r0 && f0 <= r1)) return false;
+  tx0 = (int)std::fmax(f0, r0);
+  tx1 = (int)std::fmin(f1, r1);
   return tx1 >= tx0;
 }
 

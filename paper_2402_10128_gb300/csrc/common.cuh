@@ -145,7 +145,7 @@ __device__ __forceinline__ float ksqrt(float a) { return __fsqrt_rn(a); }
 // band is y in [16 ty, 16 ty + 16); inside it the ellipse's x-extent runs from its leftmost to its
 // rightmost point, x(dy) = (b/c) dy +- sqrt((qlim - dy^2/c) det/c), whose extremes over the whole
 // ellipse lie at dy = +-b sqrt(qlim/a); over the band they lie at that dy clamped into the band.
-// The span, widened by margin_abs, is clipped to the bounding box's columns [r.x, r.z).
+// The span, widened by margin_abs, is intersected with the bounding box's columns [r.x, r.z).
 struct RowSpan {
   float u, v, ql, mabs;  // 2D mean, q limit, absolute margin
   float Y, sl, g, ic, dys;
@@ -183,8 +183,10 @@ __device__ __forceinline__ bool tile_row_span(const RowSpan& s, int ty, int& tx0
   const float xr = kadd(kadd(kadd(s.u, kmul(s.sl, dmax)), wr), s.mabs);
   const float xl = ksub(ksub(kadd(s.u, kmul(s.sl, dmin)), wl), s.mabs);
   float f0 = floorf(kmul(xl, 0.0625f)), f1 = floorf(kmul(xr, 0.0625f));
-  f0 = fminf(fmaxf(f0, s.r0), s.r1);
-  f1 = fminf(fmaxf(f1, s.r0), s.r1);
+  // a span wholly outside the box's columns (the row's part of the ellipse is off the image) is empty
+  if (!(f1 >= s.r0 && f0 <= s.r1)) return false;
+  f0 = fmaxf(f0, s.r0);
+  f1 = fminf(f1, s.r1);
   tx0 = (int)f0;
   tx1 = (int)f1;
   return tx1 >= tx0;

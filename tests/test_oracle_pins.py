@@ -546,3 +546,35 @@ def test_backward_matches_finite_differences_sh3_offaxis():
     sc = _f64(random_small_scene(6, seed=22, beta_range=(1.2, 3.0), degree=3))
     cam = scenes.look_at((0.4, 0.3, -0.5), (0.0, 0.0, 4.5), (0.0, -1.0, 0.0), 32, 28, 70.0)
     _fd_check(sc, cam, None, seed=2)
+
+
+def _geometry_cases():
+    off = scenes.cube_scene(2000, seed=17, beta_range=(0.5, 8.0), beta_log=True, scale_range=(0.02, 0.3))
+    # camera aimed past the cube's edge: many primitives' centres and ellipses lie partly off the image
+    off_cam = scenes.look_at((2.2, 0.8, -3.0), (2.2, 0.8, 0.0), (0.0, -1.0, 0.0), 96, 64, 60.0)
+    return {
+        "tiny": (*scenes.tiny_workload(), None),
+        "wide_beta_ragged": (scenes.cube_scene(300, seed=11, beta_range=(0.3, 16.0), beta_log=True,
+                                               scale_range=(0.02, 0.2)), scenes.tiny_camera(45, 37), None),
+        "exact_phi": (scenes.cube_scene(400, seed=14, beta_range=(0.8, 12.0), beta_log=True,
+                                        scale_range=(0.01, 0.06)), scenes.tiny_camera(70, 50), dict(phi_mode=1)),
+        "paper_form": (*scenes.tiny_workload(), dict(mode=1)),
+        "off_image": (off, off_cam, None),
+    }
+
+
+@pytest.mark.parametrize("which", list(_geometry_cases()))
+def test_tile_lists_against_fp64_geometry(which):
+    """The key module's lists against the extent ellipse in FP64 (oracle.project's conic, q* from
+    libm), with none of the key path's FP32 arithmetic: complete (every tile the ellipse meets is
+    listed) and tight (every listed tile meets the ellipse widened by the stated margins).  The
+    off-image case pins that a row whose part of the ellipse lies wholly off the image lists no
+    tile.  The depth keys against the FP64 camera depth, and each tile's order against it."""
+    from helpers import check_depth_keys_fp64, check_tile_lists_fp64
+    sc, cam, p = _geometry_cases()[which]
+    k = oracle.keys(sc, cam, p)
+    kk, vv = oracle.sorted_keys(sc, cam, p, key_info=k)
+    n, fails = check_tile_lists_fp64(sc, cam, p, kk, vv, oracle)
+    assert n > 1000 and not fails, fails
+    assert not check_depth_keys_fp64(sc, cam, k["depth_key"], oracle, kk, vv)
+
