@@ -41,7 +41,7 @@ DEFAULT_PARAMS = dict(rho=0.1, mode=0, dilation=0.3, alpha_max=0.99, alpha_min=1
 MODE_GEF = 0
 MODE_PAPER_APPROX = 1
 
-# scale modification (Sec. 3.2): phi_bar_rho (Eq. approx); the exact Gamma ratio (Eq. probablity)
+# scale modification (Sec. 4.2): phi_bar_rho (Eq. approx); the exact Gamma ratio (Eq. probablity)
 # normalised to phi_n = 2 Gamma(3/beta)/Gamma(1/beta) on the scale vector; phi_n on the variance
 PHI_APPROX = 0
 PHI_EXACT = 1
@@ -91,7 +91,7 @@ def _load():
     lib.ora_render.argtypes = [i64, P, P, P, P, P, P, i32, P, P, i64, P, P, P, P, P, i32, i32]
     lib.ora_render.restype = i32
     lib.ora_backward.argtypes = [i64, P, P, P, P, P, P, i32, P, P, i64, P, P,
-                                 P, P, P, P, P, P, P, i32]
+                                 P, P, P, P, P, P, P, i32, P]
     lib.ora_backward.restype = i32
     _lib = lib
     return lib
@@ -266,10 +266,13 @@ def render(scene, cam, params=None, pixels=None, tiled=False, nthreads=0):
     return dict(img=img, T=T, ncontrib=nc, flags=fl)
 
 
-def backward(scene, cam, dL_dimg, params=None, pixels=None, nthreads=0):
+def backward(scene, cam, dL_dimg, params=None, pixels=None, nthreads=0, cond=False):
     """Analytic FP64 gradient of sum(dL_dimg * img).  dL_dimg is [3,H,W] (full frame) or
     [3,npix] over ``pixels``.  Returns dict of float64 gradients and ``inter`` [n,10]
-    (mx, my, conic a, b, c, kappa, hb, r, g, b)."""
+    (mx, my, conic a, b, c, kappa, hb, r, g, b).  With cond=True also ``cond``: for every
+    gradient (the same keys and shapes, "inter" included) the scale of its rounding error, the sum
+    over pixels of the absolute per-pixel contributions, carried to the parameters through the
+    absolute values of each primitive's Jacobian."""
     n, m, s, q, b, o, sh = _scene64(scene)
     W, H = cam.width, cam.height
     if pixels is None:
@@ -283,8 +286,13 @@ def backward(scene, cam, dL_dimg, params=None, pixels=None, nthreads=0):
     out = dict(means=np.empty((n, 3)), scales=np.empty((n, 3)), quats=np.empty((n, 4)),
                betas=np.empty(n), opacities=np.empty(n), shs=np.empty((n, nb, 3)),
                inter=np.empty((n, 10)))
+    cbuf = np.empty((n, 22 + 3 * nb)) if cond else None
     _load().ora_backward(n, _p(m), _p(s), _p(q), _p(b), _p(o), _p(sh), int(scene.sh_degree),
                          _p(cam_array(cam)), _p(par_array(params)), npix, _p(pix), _p(g),
                          _p(out["means"]), _p(out["scales"]), _p(out["quats"]), _p(out["betas"]),
-                         _p(out["opacities"]), _p(out["shs"]), _p(out["inter"]), int(nthreads))
+                         _p(out["opacities"]), _p(out["shs"]), _p(out["inter"]), int(nthreads),
+                         _p(cbuf) if cond else None)
+    if cond:
+        out["cond"] = dict(inter=cbuf[:, 0:10], means=cbuf[:, 10:13], scales=cbuf[:, 13:16], quats=cbuf[:, 16:20],
+                           betas=cbuf[:, 20], opacities=cbuf[:, 21], shs=cbuf[:, 22:].reshape(n, nb, 3))
     return out

@@ -7,13 +7,13 @@
 // does.  It shares no code, header or constant table with the CUDA library.
 //
 // What it computes, and which passage each part follows:
-//   * GES kernel  L(x) = exp(-1/2 ((x-mu)^T Sigma^-1 (x-mu))^(beta/2))      Sec. 3.1, Eq. (ges)
-//   * Sigma = R S S^T R^T with S scaled by the shape modification phi(beta)  Sec. 3.1
-//   * phi_bar_rho(beta) = 2 / (1 + exp(-(rho*beta - 2*rho))), rho = 0.1     Sec. 3.2, Eq. (approx); App. B.2
-//     or, as an option, the exact phi_n(beta) = 2 Gamma(3/beta)/Gamma(1/beta) Sec. 3.2, Eq. (probablity)
-//   * EWA projection Sigma' = J W Sigma W^T J^T (Zwicker et al.)             Sec. 3.1
-//   * discrete front-to-back compositing of the volume-rendering integral   Sec. 3.2, Eq. (transmittance)
-//   * view-dependent colour from real spherical harmonics                   Sec. 3.1
+//   * GES kernel  L(x) = exp(-1/2 ((x-mu)^T Sigma^-1 (x-mu))^(beta/2))      Sec. 4.1, Eq. (ges)
+//   * Sigma = R S S^T R^T with S scaled by the shape modification phi(beta)  Sec. 4.1
+//   * phi_bar_rho(beta) = 2 / (1 + exp(-(rho*beta - 2*rho))), rho = 0.1     Sec. 4.2, Eq. (approx); App. B.2
+//     or, as an option, the exact phi_n(beta) = 2 Gamma(3/beta)/Gamma(1/beta) Sec. 4.2, Eq. (probablity)
+//   * EWA projection Sigma' = J W Sigma W^T J^T (Zwicker et al.)             Sec. 4.1
+//   * discrete front-to-back compositing of the volume-rendering integral   Sec. 4.2, Eq. (transmittance)
+//   * view-dependent colour from real spherical harmonics                   Sec. 4.1
 // Readings where the paper is silent (alpha clamp 0.99, skip below 1/255,
 // stop at T < 1e-4, 0.3 px dilation, 16x16 tiles, the beta-dependent extent,
 // SH conventions, FP32 key path) are listed in the design notes and restated
@@ -850,10 +850,15 @@ int ora_render(int64_t n, const double* means, const double* scales, const doubl
 // g_means[n,3], g_scales[n,3], g_quats[n,4], g_betas[n], g_opac[n], g_shs[n,nb,3];
 // inter[n,10] (optional): per-primitive gradients of the 2D quantities
 //   (mx, my, conic a, b, c, kappa, hb, r, g, b) -- the compositing stage's output.
+// cond (optional, [n, 22 + 3 nb]): the scale of each gradient element's rounding error -- for
+// the 2D quantities the sum over pixels of the absolute per-pixel contributions (a sum's
+// floating-point error is bounded by a multiple of it), for the parameters the same sums carried
+// through the absolute values of the per-primitive Jacobian; per primitive in the order
+// inter (10), means (3), scales (3), quats (4), beta, kappa, shs (3 nb).
 int ora_backward(int64_t n, const double* means, const double* scales, const double* quats, const double* betas,
                  const double* opac, const double* shs, int deg, const double* cam_d, const double* par_d, int64_t npix,
                  const int64_t* pix, const double* dL, double* g_means, double* g_scales, double* g_quats,
-                 double* g_betas, double* g_opac, double* g_shs, double* inter, int nthreads) {
+                 double* g_betas, double* g_opac, double* g_shs, double* inter, int nthreads, double* cond) {
   Cam cam = read_cam(cam_d);
   Par par = read_par(par_d);
   SceneIn sc = scene_in(n, means, scales, quats, betas, opac, shs, deg);
@@ -925,11 +930,16 @@ int ora_backward(int64_t n, const double* means, const double* scales, const dou
       recs[tid].push_back(r);
     }
   });
-  std::vector<double> acc((size_t)n * 10, 0.0);
+  std::vector<double> acc((size_t)n * 10, 0.0), acc_abs(cond ? (size_t)n * 10 : 0, 0.0);
   for (auto& v : recs)
     for (auto& r : v)
-      for (int j = 0; j < 10; ++j) acc[(size_t)r.i * 10 + j] += r.g[j];
+      for (int j = 0; j < 10; ++j) {
+        acc[(size_t)r.i * 10 + j] += r.g[j];
+        if (cond) acc_abs[(size_t)r.i * 10 + j] += std::fabs(r.g[j]);
+      }
   if (inter) std::memcpy(inter, acc.data(), sizeof(double) * 10 * n);
+  const int64_t ncond = 22 + 3 * nb;
+  if (cond) std::memset(cond, 0, sizeof(double) * (size_t)ncond * n);
 
   std::memset(g_means, 0, sizeof(double) * 3 * n);
   std::memset(g_scales, 0, sizeof(double) * 3 * n);
@@ -972,6 +982,21 @@ int ora_backward(int64_t n, const double* means, const double* scales, const dou
     g_opac[i] = gp[11];
     for (int k = 0; k < nb; ++k)
       for (int ch = 0; ch < 3; ++ch) g_shs[(size_t)3 * nb * i + 3 * k + ch] = basis[k].v * graw[ch];
+    if (cond) {
+      double* c = cond + (size_t)ncond * i;
+      const double* ga = &acc_abs[(size_t)i * 10];
+      double gin_abs[10];
+      for (int j = 0; j < 7; ++j) gin_abs[j] = ga[j];
+      for (int ch = 0; ch < 3; ++ch) gin_abs[7 + ch] = (pr.raw[ch].v > 0.0) ? ga[7 + ch] : 0.0;
+      for (int j = 0; j < 10; ++j) c[j] = ga[j];
+      for (int k = 0; k < ND; ++k) {
+        double t = 0.0;
+        for (int o = 0; o < 10; ++o) t += gin_abs[o] * std::fabs(outs[o]->d[k]);
+        c[10 + k] = t;
+      }
+      for (int k = 0; k < nb; ++k)
+        for (int ch = 0; ch < 3; ++ch) c[22 + 3 * k + ch] = std::fabs(basis[k].v) * gin_abs[7 + ch];
+    }
   });
   return 0;
 }

@@ -6,6 +6,9 @@
   primitives;
 * gradients: the upstream gradient is non-zero on a random sample of pixels only, so the oracle's
   exact FP64 backward over those pixels is the full answer; the GPU runs its complete backward.
+  Bar per parameter tensor: 1e-3 relative L2 error, and element by element
+  |g - g_ref| <= 1e-3 (|g_ref| + 1e-3 max|g_ref|) + 1e-5 c, c the oracle's sum of the element's
+  absolute per-pixel contributions (the rounding scale of a sum whose terms cancel).
 """
 import numpy as np
 import pytest
@@ -17,7 +20,6 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 IMG_TOL = 1e-4
-GRAD_TOL = 1e-3
 
 
 @pytest.fixture(scope="module")
@@ -69,7 +71,7 @@ def test_fullsize_sampled_pixels(lib, workload):
 
 
 def test_fullsize_sparse_gradient(lib, workload):
-    from gpu_helpers import NAMES, gpu_run
+    from gpu_helpers import grad_failures, gpu_run
     name, sc, cam = workload
     rng = np.random.default_rng(12)
     pix = rng.choice(cam.width * cam.height, 256, replace=False)
@@ -79,9 +81,6 @@ def test_fullsize_sparse_gradient(lib, workload):
     g = np.zeros((3, cam.height * cam.width))
     g[:, pix] = gs
     got = gpu_run(sc, cam, backward_grad=g.reshape(3, cam.height, cam.width), keys=False)
-    ref = oracle.backward(sc, cam, gs, pixels=pix)
-    for k in NAMES:
-        a = got["grads"][k].reshape(-1)
-        b = ref[k].reshape(-1)
-        err = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
-        assert err <= GRAD_TOL, (k, err)
+    ref = oracle.backward(sc, cam, gs, pixels=pix, cond=True)
+    bad = grad_failures(got["grads"], ref, cond=ref["cond"])
+    assert not bad, "; ".join(bad)

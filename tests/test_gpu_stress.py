@@ -13,7 +13,9 @@ listed once per tile row: segment_tiles = 256):
 
 Both forms: a random sample of pixels against the oracle's brute force over all 6M primitives,
 and the backward with an upstream gradient on a random sample of pixels only, against the
-oracle's exact FP64 gradient over those pixels.
+oracle's exact FP64 gradient over those pixels (1e-3 relative L2 per tensor, and element by
+element |g - g_ref| <= 1e-3 (|g_ref| + 1e-3 max|g_ref|) + 1e-5 c, c the oracle's sum of the
+element's absolute per-pixel contributions).
 """
 import numpy as np
 import pytest
@@ -25,7 +27,6 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 IMG_TOL = 1e-4
-GRAD_TOL = 1e-3
 NAMES = ["means", "scales", "quats", "betas", "opacities", "shs"]
 
 
@@ -116,12 +117,10 @@ def _sampled_pixels(run, seed):
 
 def _sparse_gradient(run):
     sc, cam = run["scene"], run["cam"]
-    ref = oracle.backward(sc, cam, run["grad_up"], pixels=run["grad_pix"])
-    for k in NAMES:
-        a = run["grads"][k].reshape(-1)
-        b = ref[k].reshape(-1)
-        err = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
-        assert err <= GRAD_TOL, (k, err)
+    ref = oracle.backward(sc, cam, run["grad_up"], pixels=run["grad_pix"], cond=True)
+    from gpu_helpers import grad_failures
+    bad = grad_failures(run["grads"], ref, cond=ref["cond"])
+    assert not bad, "; ".join(bad)
 
 
 def test_beta2_sampled_pixels_match_the_oracle(beta2):

@@ -48,7 +48,7 @@ def test_key_exp2_log2_match_libm_within_ulps():
 # ---------------------------------------------------------------- shape modification
 def test_phi_bar_fixed_points_and_symmetry():
     g = _golden()
-    assert oracle.phi_bar(2.0, rho=g["rho"])[0] == g["phi_bar_at_beta_2"]      # Sec. 3.2: exactly 1 at beta=2
+    assert oracle.phi_bar(2.0, rho=g["rho"])[0] == g["phi_bar_at_beta_2"]      # Sec. 4.2: exactly 1 at beta=2
     x = np.linspace(0.0, 30.0, 301)
     s = oracle.phi_bar(2.0 + x) + oracle.phi_bar(2.0 - x)                       # sigmoid identity
     assert np.max(np.abs(s - 2.0)) < 1e-15
@@ -65,7 +65,7 @@ def test_phi_exact_closed_forms():
 
 
 def _phi_ref(beta, phi_mode, rho=RHO32):
-    """The scale modification written from Sec. 3.2 with the standard library's Gamma function:
+    """The scale modification written from Sec. 4.2 with the standard library's Gamma function:
     phi_bar_rho (Eq. approx); 2 Gamma(3/b)/Gamma(1/b) (Eq. probablity, normalised to 1 at b = 2);
     its square root (the ratio read as one of variances, Eq. effective)."""
     if phi_mode == oracle.PHI_APPROX:
@@ -100,7 +100,7 @@ def test_key_lgamma_matches_the_library():
 
 @pytest.mark.parametrize("phi_mode", [0, 1, 2])
 def test_key_phi_matches_the_gamma_ratio(phi_mode):
-    """The key path's FP32 scale modification against Sec. 3.2 written with math.gamma."""
+    """The key path's FP32 scale modification against Sec. 4.2 written with math.gamma."""
     for b in np.exp(np.linspace(math.log(0.4), math.log(32.0), 300)).astype(np.float32):
         got, ref = oracle.key_phi(float(b), RHO32, phi_mode), _phi_ref(float(b), phi_mode)
         assert abs(got - ref) <= 4e-6 * ref, (b, got, ref)
@@ -111,7 +111,7 @@ def test_phi_exact_normalised_closed_forms():
     P1 = dict(phi_mode=oracle.PHI_EXACT)
     P2 = dict(phi_mode=oracle.PHI_EXACT_VARIANCE)
     phi = lambda b, p: oracle.phi_mod(b, p)[0][0]
-    # 1 at beta = 2 (Sec. 3.2, after Eq. approx; Fig. approximation caption), in both readings
+    # 1 at beta = 2 (Sec. 4.2, after Eq. approx; Fig. approximation caption), in both readings
     assert abs(phi(2.0, P1) - g["phi_bar_at_beta_2"]) < 1e-15 and abs(phi(2.0, P2) - 1.0) < 1e-15
     assert abs(phi(1.0, P1) - 4.0) < 1e-14            # 2 Gamma(3) / Gamma(1)
     assert abs(phi(0.5, P1) - 240.0) < 1e-11          # 2 Gamma(6) / Gamma(2) = 2 * 5!
@@ -352,7 +352,7 @@ def test_beta2_equals_independent_gaussian_renderer():
 
 
 def test_beta2_scale_modifications_agree():
-    """At beta = 2 every form of the modification is 1 (Sec. 3.2), so the images agree."""
+    """At beta = 2 every form of the modification is 1 (Sec. 4.2), so the images agree."""
     sc = random_small_scene(25, seed=4, beta_range=(2.0, 2.0))
     cam = axis_camera(48, 40)
     ref = oracle.render(sc, cam)["img"]
@@ -578,3 +578,36 @@ def test_tile_lists_against_fp64_geometry(which):
     assert n > 1000 and not fails, fails
     assert not check_depth_keys_fp64(sc, cam, k["depth_key"], oracle, kk, vv)
 
+
+def test_gradient_rounding_scale():
+    """The oracle's per-element rounding scale (``cond``): for the 2D gradients the sum over pixels
+    of the absolute per-pixel contributions, for the parameters those sums carried through the
+    absolute Jacobian.  Pinned by: a single pixel, where it equals the absolute 2D gradient and
+    bounds the parameter gradients; the triangle inequality (cond >= |g| everywhere); additivity
+    over disjoint pixel sets; and an exact cancellation, two pixels symmetric about a lone
+    isotropic splat's centre, whose x-mean gradients cancel while their magnitudes add."""
+    sc, cam = scenes.tiny_workload()
+    ref = oracle.render(sc, cam)
+    rng = np.random.default_rng(3)
+    ok = np.nonzero(ref["flags"].reshape(-1) == 0)[0]
+    pix = rng.choice(ok, 40, replace=False)
+    g = rng.standard_normal((3, pix.size))
+    full = oracle.backward(sc, cam, g, pixels=pix, cond=True)
+    for k in ("means", "scales", "quats", "betas", "opacities", "shs", "inter"):
+        assert np.all(full["cond"][k] >= np.abs(full[k]) * (1 - 1e-12)), k
+    a = oracle.backward(sc, cam, g[:, :17], pixels=pix[:17], cond=True)
+    b = oracle.backward(sc, cam, g[:, 17:], pixels=pix[17:], cond=True)
+    np.testing.assert_allclose(a["cond"]["inter"] + b["cond"]["inter"], full["cond"]["inter"], rtol=1e-12, atol=0)
+    one = oracle.backward(sc, cam, g[:, :1], pixels=pix[:1], cond=True)
+    np.testing.assert_allclose(one["cond"]["inter"], np.abs(one["inter"]), rtol=1e-15, atol=0)
+    for k in ("means", "scales", "quats", "opacities"):
+        assert np.all(one["cond"][k] >= np.abs(one[k]) * (1 - 1e-12))
+    # exact cancellation: an isotropic splat on the axis of a 64x64 camera projects to (32, 32);
+    # pixels (31, 32) and (32, 32) sit at dx = -0.5 and +0.5, dy = +0.5
+    lone = make_scene([[0.0, 0.0, 4.0]], [0.2, 0.2, 0.2], [1.0, 0.0, 0.0, 0.0], [2.0], [0.8], rgb=[[0.6, 0.3, 0.2]])
+    cam2 = axis_camera(64, 64)
+    two = np.array([32 * 64 + 31, 32 * 64 + 32])
+    r = oracle.backward(lone, cam2, np.ones((3, 2)), pixels=two, cond=True)
+    s1 = oracle.backward(lone, cam2, np.ones((3, 1)), pixels=two[:1], cond=True)
+    assert abs(r["inter"][0, 0]) <= 1e-12 * abs(s1["inter"][0, 0])
+    np.testing.assert_allclose(r["cond"]["inter"][0, 0], 2 * abs(s1["inter"][0, 0]), rtol=1e-12)
