@@ -434,7 +434,7 @@ ges_status ges_frame_create(ges_ctx* ctx, int64_t n_capacity, int32_t width, int
   }
   A((void**)&f->rect, sizeof(ushort4) * N);
   A((void**)&f->rec, sizeof(Rec) * N);
-  A((void**)&f->ext, sizeof(float4) * N);
+  A((void**)&f->ks, sizeof(KeyShape) * N);
   A((void**)&f->tprim, 4 * N);
   A((void**)&f->touched, 4 * N);
   A((void**)&f->offsets, 8 * N);
@@ -476,7 +476,7 @@ void ges_frame_destroy(ges_frame* f) {
   }
   ctx_free(c, f->rect, sizeof(ushort4) * N);
   ctx_free(c, f->rec, sizeof(Rec) * N);
-  ctx_free(c, f->ext, sizeof(float4) * N);
+  ctx_free(c, f->ks, sizeof(KeyShape) * N);
   ctx_free(c, f->tprim, 4 * N);
   ctx_free(c, f->touched, 4 * N);
   ctx_free(c, f->offsets, 8 * N);
@@ -518,7 +518,7 @@ ges_status ges_preprocess(ges_frame* f, const ges_scene* scene, const ges_camera
   f->sh_degree = scene->sh_degree;
   {
     TraceScope tr(f->ctx, "k_preprocess", s);
-    launch_preprocess<FrameViews>(f->vt, f->n, f->P, f->depth_key, f->dk[0], f->pv[0], f->rect, f->rec, f->ext,
+    launch_preprocess<FrameViews>(f->vt, f->n, f->P, f->depth_key, f->dk[0], f->pv[0], f->rect, f->rec, f->ks,
                                   f->tprim, f->ctx->num_sms, s);
   }
   cudaError_t e = cudaGetLastError();
@@ -568,20 +568,22 @@ ges_status ges_bin_sort(ges_frame* f, void* stream) {
   }
   {
     TraceScope tr(f->ctx, "k_keygen", s);
-    launch_keygen<FrameViews>(f->vt, f->offsets, f->touched, f->d_K, f->n, f->sorted_prims, f->rect, f->ext, f->rec,
+    launch_keygen<FrameViews>(f->vt, f->offsets, f->touched, f->d_K, f->n, f->sorted_prims, f->ks,
                               f->P, f->key_cap, f->tk[0], f->tv[0], f->d_flags, s);
   }
   int tcur = 0;
+  bool ranges_done = false;
   {
     TraceScope tr(f->ctx, "list_sort", s);
+    // a single-pass list sort also gives every segment's range, from its histogram
     if (!radix_sort_pairs(f->tk, f->tv, tcur, 0, f->d_K, f->key_cap, f->P.seg_bits, f->hist, f->hist_cap, f->scan, s,
-                          f->d_flags))
+                          f->d_flags, f->ranges, f->n_segs, &ranges_done))
       return fail(GES_ERR_CUDA, "internal: list-sort histogram exceeds its buffer");
   }
   f->tile_keys = f->tk[tcur];
   f->tile_vals = f->tv[tcur];
-  if ((e = cudaMemsetAsync(f->ranges, 0, sizeof(uint2) * f->n_segs, s)) != cudaSuccess) return cuda_fail(e, "memset ranges");
-  {
+  if (!ranges_done) {
+    if ((e = cudaMemsetAsync(f->ranges, 0, sizeof(uint2) * f->n_segs, s)) != cudaSuccess) return cuda_fail(e, "memset ranges");
     TraceScope tr(f->ctx, "k_ranges", s);
     launch_ranges(f->tile_keys, f->d_K, f->key_cap, (uint32_t)((1ull << f->P.seg_bits) - 1), f->ranges, f->ctx->num_sms,
                   s);

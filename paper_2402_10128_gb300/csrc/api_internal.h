@@ -47,7 +47,7 @@ struct ges_frame {
   uint32_t* pv[2] = {nullptr, nullptr};
   ushort4* rect = nullptr;
   ges::Rec* rec = nullptr;
-  float4* ext = nullptr;           // extent shape: 2D covariance and q limit
+  ges::KeyShape* ks = nullptr;     // what the key generation reads: extent shape, 2D mean, box
   uint32_t* tprim = nullptr;       // tiles met per primitive
   uint32_t* touched = nullptr;     // the same, in depth order
   unsigned long long* offsets = nullptr;

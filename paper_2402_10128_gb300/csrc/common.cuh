@@ -128,6 +128,14 @@ struct __align__(16) Rec {
   float4 a, b, c;
 };
 
+// What the key generation reads of a primitive, in one 32-byte sector: the extent's shape (2D
+// covariance with dilation, and the q limit), the 2D mean, and the bounding box in tiles.
+struct __align__(32) KeyShape {
+  float4 ext;    // a, b, c, q limit
+  float2 mean;   // u, v
+  ushort4 box;   // x0, y0, x1, y1 (end-exclusive)
+};
+
 // ------------------------------------------------------------------------------------------
 // Key path: FP32 with every operation rounded separately (no contraction), in a fixed order.
 // These values decide integers (visibility, depth order, tile rectangles), so the oracle

@@ -15,7 +15,7 @@ void count_launches(int n);
 // extent in tiles, record, extent shape (2D covariance and q limit), tiles met (row spans)
 template <class VS>
 void launch_preprocess(const VS& vs, int64_t grid_total, const Params& P, uint32_t* depth_key, uint32_t* sort_keys,
-                       uint32_t* sort_vals, ushort4* rect, Rec* rec, float4* ext, uint32_t* tprim, int num_sms,
+                       uint32_t* sort_vals, ushort4* rect, Rec* rec, KeyShape* ks, uint32_t* tprim, int num_sms,
                        cudaStream_t s);
 template <class VS>
 void launch_preprocess_bwd(const VS& vs, int64_t grid_total, const Params& P, const uint32_t* depth_key,
@@ -56,17 +56,21 @@ void launch_gather_touched(const uint32_t* sorted_vals, const uint32_t* tprim, i
 // (digit counts in one read, one kernel per pass with a bounded decoupled look-back; a look-back
 // that gives up sets kFlagSortWait in *flags when flags is given), else as hist / scan / scatter
 // per pass.
+// bin_ranges (optional, n_ranges entries): when the sort takes a single pass over all total_bits, the
+// [start, end) range of every key value in the sorted output is written there from the pass's
+// scanned histogram, and *ranges_done is set (else it is cleared and bin_ranges left alone)
 bool radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_host, const unsigned long long* n_dev,
                       int64_t n_cap, int total_bits, uint32_t* hist, int64_t hist_cap, ScanScratch& sc, cudaStream_t s,
-                      uint32_t* flags = nullptr);
+                      uint32_t* flags = nullptr, uint2* bin_ranges = nullptr, int64_t n_ranges = 0,
+                      bool* ranges_done = nullptr);
 int64_t radix_hist_entries(int64_t n_cap, int max_bits);
 
 // n: primitives (the capacity when n_dev gives the count on the device); touched: tiles per
 // primitive in depth order (the scan's input)
 template <class VS>
 void launch_keygen(const VS& vs, const unsigned long long* offsets, const uint32_t* touched,
-                   const unsigned long long* K_dev, int64_t n, const uint32_t* sorted_vals, const ushort4* rect,
-                   const float4* ext, const Rec* rec, const Params& P, int64_t cap,
+                   const unsigned long long* K_dev, int64_t n, const uint32_t* sorted_vals, const KeyShape* ks,
+                   const Params& P, int64_t cap,
                    uint32_t* tile_keys, uint32_t* tile_vals, uint32_t* flags, cudaStream_t s,
                    const unsigned long long* n_dev = nullptr);
 // [start, end) per segment of the sorted list (segment id = key & seg_mask); ranges of empty

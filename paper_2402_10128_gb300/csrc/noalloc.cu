@@ -32,7 +32,7 @@ constexpr int64_t kNaScanBytes = 4096;     // multi-level scan scratch for <= 2^
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t depth_key, dk0, dk1, pv0, pv1, rect, rec, ext, tprim, touched, offsets;
+  size_t depth_key, dk0, dk1, pv0, pv1, rect, rec, ks, tprim, touched, offsets;
   size_t tk0, tk1, tv0, tv1, hist, scan, ranges, K, flags, total;
 };
 
@@ -51,7 +51,7 @@ constexpr Layout make_layout() {
   L.pv1 = take(4 * kNaMaxPrims);
   L.rect = take(8 * kNaMaxPrims);
   L.rec = take(sizeof(Rec) * kNaMaxPrims);
-  L.ext = take(sizeof(float4) * kNaMaxPrims);
+  L.ks = take(sizeof(KeyShape) * kNaMaxPrims);
   L.tprim = take(4 * kNaMaxPrims);
   L.touched = take(4 * kNaMaxPrims);
   L.offsets = take(8 * kNaMaxPrims);
@@ -170,15 +170,15 @@ extern "C" ges_status ges_render_fwd_noalloc(const ges_scene* scene, const ges_c
   // segments are never written by the ranges kernel)
   if ((e = cudaMemsetAsync(flags, 0, 4, s)) != cudaSuccess) return cuda_fail(e, "clear flags");
   if ((e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * segs, s)) != cudaSuccess) return cuda_fail(e, "clear ranges");
-  float4* ext = at<float4>(b, kL.ext);
+  KeyShape* ks = at<KeyShape>(b, kL.ks);
   uint32_t* tprim = at<uint32_t>(b, kL.tprim);
-  launch_preprocess<FrameViews>(vt, n, P, depth_key, dk[0], pv[0], rect, rec, ext, tprim, ds->num_sms, s);
+  launch_preprocess<FrameViews>(vt, n, P, depth_key, dk[0], pv[0], rect, rec, ks, tprim, ds->num_sms, s);
   int cur = 0;
   if (!radix_sort_pairs(dk, pv, cur, n, nullptr, n, 32, hist, kNaHistEntries, scan, s, flags))
     return fail(GES_ERR_CUDA, "internal: depth-sort histogram exceeds its buffer");
   launch_gather_touched(pv[cur], tprim, n, touched, s);
   scan_exclusive_onepass(touched, offsets, n, dK, scan, flags, s);
-  launch_keygen<FrameViews>(vt, offsets, touched, dK, n, pv[cur], rect, ext, rec, P, kNaMaxKeys,
+  launch_keygen<FrameViews>(vt, offsets, touched, dK, n, pv[cur], ks, P, kNaMaxKeys,
                             tk[0], tv[0], flags, s);
   int tcur = 0;
   if (!radix_sort_pairs(tk, tv, tcur, 0, dK, kNaMaxKeys, P.seg_bits, hist, kNaHistEntries, scan, s, flags))

@@ -1,12 +1,12 @@
 // Per-primitive kernels: projection (forward) and its chain rule (backward).
 //
-// Forward, per primitive (Sec. 3.1, Sec. 3.2):
+// Forward, per primitive (Sec. 4.1, Sec. 4.2):
 //   phi_bar_rho(beta) = 2 / (1 + exp(-rho (beta - 2)))            Eq. approx (App. B.2: rho = 0.1)
 //   or phi_n(beta) = 2 Gamma(3/beta) / Gamma(1/beta) (or its root)   Eq. probablity, normalised
-//   Sigma = R diag(phi_bar s)^2 R^T                                  Sec. 3.1 (scale vector modified by phi)
-//   Sigma' = J W Sigma W^T J^T + dilation I, conic = Sigma'^-1       Sec. 3.1 (EWA, Zwicker et al.)
+//   Sigma = R diag(phi_bar s)^2 R^T                                  Sec. 4.1 (scale vector modified by phi)
+//   Sigma' = J W Sigma W^T J^T + dilation I, conic = Sigma'^-1       Sec. 4.1 (EWA, Zwicker et al.)
 //   extent: alpha = kappa exp(-1/2 q^(beta/2)) >= alpha_min  <=>  q <= q* = (2 ln(kappa/alpha_min))^(2/beta)
-//   colour = max(0, sum_lm c_lm Y_lm(dir) + 1/2)                     Sec. 3.1 (SH as in Gaussian splatting)
+//   colour = max(0, sum_lm c_lm Y_lm(dir) + 1/2)                     Sec. 4.1 (SH as in Gaussian splatting)
 // Everything that decides an integer (visibility, depth key, tile rectangle) runs on the
 // fixed-order FP32 key path of common.cuh; the SH colour uses ordinary FP32 arithmetic.
 #include "common.cuh"
@@ -182,7 +182,7 @@ template <class VS>
 __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ VS vs, const Params P, uint32_t* __restrict__ depth_key,
                                                     uint32_t* __restrict__ sort_keys,
                                                     uint32_t* __restrict__ sort_vals, ushort4* __restrict__ rect,
-                                                    Rec* __restrict__ rec, float4* __restrict__ ext,
+                                                    Rec* __restrict__ rec, KeyShape* __restrict__ ks,
                                                     uint32_t* __restrict__ tprim) {
   const auto& vt = vs.get();
   const int64_t total = (int64_t)vt.total_prims;
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ VS v
     rect[g] = touched ? box : make_ushort4(0, 0, 0, 0);
     tprim[g] = nentries;
     if (!touched) continue;
-    ext[g] = e4;
+    ks[g] = KeyShape{e4, make_float2(u, v), box};
 
     // SH colour (ordinary FP32)
     float dvx = mx - vd.campos[0], dvy = my - vd.campos[1], dvz = mz - vd.campos[2];
@@ -555,10 +555,10 @@ static int grid_for(int64_t total, int num_sms) {
 
 template <class VS>
 void launch_preprocess(const VS& vs, int64_t grid_total, const Params& P, uint32_t* depth_key, uint32_t* sort_keys,
-                       uint32_t* sort_vals, ushort4* rect, Rec* rec, float4* ext, uint32_t* tprim, int num_sms,
+                       uint32_t* sort_vals, ushort4* rect, Rec* rec, KeyShape* ks, uint32_t* tprim, int num_sms,
                        cudaStream_t s) {
   if (grid_total <= 0) return;
-  k_preprocess<VS><<<grid_for(grid_total, num_sms), 256, 0, s>>>(vs, P, depth_key, sort_keys, sort_vals, rect, rec, ext,
+  k_preprocess<VS><<<grid_for(grid_total, num_sms), 256, 0, s>>>(vs, P, depth_key, sort_keys, sort_vals, rect, rec, ks,
                                                                   tprim);
   count_launches(1);
 }
@@ -584,9 +584,9 @@ void set_key_constants(cudaStream_t s) {
 }
 
 template void launch_preprocess<FrameViews>(const FrameViews&, int64_t, const Params&, uint32_t*, uint32_t*, uint32_t*,
-                                            ushort4*, Rec*, float4*, uint32_t*, int, cudaStream_t);
+                                            ushort4*, Rec*, KeyShape*, uint32_t*, int, cudaStream_t);
 template void launch_preprocess<BatchViews>(const BatchViews&, int64_t, const Params&, uint32_t*, uint32_t*, uint32_t*,
-                                            ushort4*, Rec*, float4*, uint32_t*, int, cudaStream_t);
+                                            ushort4*, Rec*, KeyShape*, uint32_t*, int, cudaStream_t);
 template void launch_preprocess_bwd<FrameViews>(const FrameViews&, int64_t, const Params&, const uint32_t*,
                                                 const float4*, int, cudaStream_t);
 

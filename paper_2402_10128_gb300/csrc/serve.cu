@@ -68,7 +68,7 @@ struct Workspace {
   uint32_t* pv[2] = {nullptr, nullptr};
   ushort4* rect = nullptr;
   Rec* rec = nullptr;
-  float4* ext = nullptr;
+  KeyShape* ks = nullptr;
   uint32_t* tprim = nullptr;
   uint32_t* touched = nullptr;
   unsigned long long* offsets = nullptr;
@@ -149,7 +149,7 @@ ges_status ws_alloc(ges_server* S, Workspace& w, int64_t P_cap, int64_t T_cap, i
   }
   A((void**)&w.rect, sizeof(ushort4) * P_cap);
   A((void**)&w.rec, sizeof(Rec) * P_cap);
-  A((void**)&w.ext, sizeof(float4) * P_cap);
+  A((void**)&w.ks, sizeof(KeyShape) * P_cap);
   A((void**)&w.tprim, 4 * P_cap);
   A((void**)&w.touched, 4 * P_cap);
   A((void**)&w.offsets, 8 * P_cap);
@@ -183,13 +183,13 @@ ges_status ws_alloc(ges_server* S, Workspace& w, int64_t P_cap, int64_t T_cap, i
   cudaMemcpyAsync(w.d_vt, w.h_vt, sizeof(Table), cudaMemcpyHostToDevice, s);
   cudaMemsetAsync(w.stat + 1, 0, 16, s);
   cudaMemsetAsync(w.ranges, 0, sizeof(uint2) * T_cap, s);
-  launch_preprocess<BatchViews>(vs, P_cap, S->P, w.depth_key, w.dk[0], w.pv[0], w.rect, w.rec, w.ext, w.tprim, S->num_sms,
+  launch_preprocess<BatchViews>(vs, P_cap, S->P, w.depth_key, w.dk[0], w.pv[0], w.rect, w.rec, w.ks, w.tprim, S->num_sms,
                                 s);
   int cur = 0;
   bool fits = radix_sort_pairs(w.dk, w.pv, cur, 0, n_dev, P_cap, 32, w.hist, w.hist_cap, w.scan, s, flags);
   launch_gather_touched(w.pv[cur], w.tprim, P_cap, w.touched, s, n_dev);
   scan_exclusive_onepass(w.touched, w.offsets, P_cap, dK, w.scan, flags, s, n_dev);
-  launch_keygen<BatchViews>(vs, w.offsets, w.touched, dK, P_cap, w.pv[cur], w.rect, w.ext, w.rec, S->P, K_cap,
+  launch_keygen<BatchViews>(vs, w.offsets, w.touched, dK, P_cap, w.pv[cur], w.ks, S->P, K_cap,
                             w.tk[0], w.tv[0], flags, s, n_dev);
   int tcur = 0;
   fits = radix_sort_pairs(w.tk, w.tv, tcur, 0, dK, K_cap, tile_bits, w.hist, w.hist_cap, w.scan, s, flags) && fits;
@@ -243,13 +243,13 @@ ges_status setup_workspaces(ges_server* S) {
   const int64_t X_cap = slots * kMaxPixelsPerView;
   const int64_t T_cap = X_cap / 256 + slots * 256;
   int64_t P_cap = slots * n_max;
-  // per primitive 108 B, per pixel 20 B (+ 12 B pinned), per tile 8 B; duplicates take the rest
+  // per primitive 124 B, per pixel 20 B (+ 12 B pinned), per tile 8 B; duplicates take the rest
   const size_t fixed_px = (size_t)X_cap * 20 + (size_t)T_cap * 8;
-  if ((size_t)P_cap * 108 > per_ws / 3) P_cap = (int64_t)(per_ws / 3 / 108);
+  if ((size_t)P_cap * 124 > per_ws / 3) P_cap = (int64_t)(per_ws / 3 / 124);
   if (P_cap < n_max)
     return fail(GES_ERR_OOM, "serving workspace of %zu bytes cannot hold the largest scene (%lld primitives)", per_ws,
                 (long long)n_max);
-  const size_t used = (size_t)P_cap * 108 + fixed_px;
+  const size_t used = (size_t)P_cap * 124 + fixed_px;
   if (used >= per_ws) return fail(GES_ERR_OOM, "serving workspace budget %zu bytes is too small", per_ws);
   int64_t K_cap = (int64_t)((per_ws - used) / 17);
   const int64_t k_limit = ((int64_t)1 << 31) - ((int64_t)1 << 20);

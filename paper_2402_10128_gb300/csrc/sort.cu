@@ -158,6 +158,24 @@ __global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restr
   }
 }
 
+// The [start, end) range of every bin in the output of a single-pass sort, from the pass's scanned
+// histogram ([bin][chunk], exclusive over the whole matrix): bin b starts where its first chunk's
+// entries go and ends where bin b + 1's start (the last bin at the element count).
+__global__ void __launch_bounds__(256) k_ranges_from_hist(const uint32_t* __restrict__ hist, int64_t n_host,
+                                                          const unsigned long long* __restrict__ n_dev, int64_t cap,
+                                                          int nbins, int64_t n_ranges, uint2* __restrict__ ranges) {
+  const int64_t n = element_count(n_host, n_dev, cap);
+  const int64_t nchunks = (n + kChunk - 1) / kChunk;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n_ranges; b += (int64_t)gridDim.x * blockDim.x) {
+    uint2 r = make_uint2(0u, 0u);
+    if (nchunks > 0 && b < nbins) {
+      r.x = hist[b * nchunks];
+      r.y = b + 1 < nbins ? hist[(b + 1) * nchunks] : (uint32_t)n;
+    }
+    ranges[b] = r;
+  }
+}
+
 // Stable scatter.  Warp w of the CTA owns chunk elements [w*256, (w+1)*256) and walks them in
 // order, 32 at a time.  Lanes with equal digits (found with one ballot per digit bit) are ranked
 // by lane order; the group's first lane adds the group size to the warp's running count of that
@@ -538,8 +556,7 @@ __global__ void __launch_bounds__(kKeygenThreads, 4) k_keygen(const __grid_const
                                                            const unsigned long long* __restrict__ n_dev,
                                                            const uint32_t* __restrict__ sorted_vals,
                                                            const uint32_t* __restrict__ touched,
-                                                           const ushort4* __restrict__ rect, const float4* __restrict__ ext,
-                                                           const Rec* __restrict__ rec, const Params P, int64_t cap,
+                                                           const KeyShape* __restrict__ ks, const Params P, int64_t cap,
                                                            uint32_t* __restrict__ tile_keys,
                                                            uint32_t* __restrict__ tile_vals, uint32_t* __restrict__ flags) {
   const auto& vt = vs.get();
@@ -560,9 +577,9 @@ __global__ void __launch_bounds__(kKeygenThreads, 4) k_keygen(const __grid_const
     unsigned g = 0, h = 0, y0 = 0, sb = 0, sx = 0;
     if (t) {
       g = sorted_vals[j];
-      const ushort4 r = rect[g];
-      const float4 ra = rec[g].a;
-      rs = make_row_span(ext[g], ra.x, ra.y, P.margin_abs, r);
+      const KeyShape k = ks[g];  // one 32-byte sector
+      const ushort4 r = k.box;
+      rs = make_row_span(k.ext, k.mean.x, k.mean.y, P.margin_abs, r);
       const ViewDesc& vd = vt.v[view_of_prim(vt, (int64_t)g)];
       h = (unsigned)(r.w - r.y);
       y0 = r.y;
@@ -874,7 +891,8 @@ int64_t radix_hist_entries(int64_t n_cap, int max_bits) {
 
 bool radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_host, const unsigned long long* n_dev,
                       int64_t n_cap, int total_bits, uint32_t* hist, int64_t hist_cap, ScanScratch& sc, cudaStream_t s,
-                      uint32_t* flags) {
+                      uint32_t* flags, uint2* bin_ranges, int64_t n_ranges, bool* ranges_done) {
+  if (ranges_done) *ranges_done = false;
   if (n_cap <= 0 || total_bits <= 0) return true;
   const int passes = (total_bits + 7) / 8;
   const int bits_per = (total_bits + passes - 1) / passes;
@@ -926,6 +944,12 @@ bool radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_
                                                                   n_entries);
     }
     scan_exclusive_onepass(hist, hist, entries, (uint32_t*)nullptr, sc, flags, s, n_entries);
+    if (bin_ranges && passes_c == 1 && bits == total_bits && n_ranges > 0) {
+      k_ranges_from_hist<<<(unsigned)cdiv(n_ranges, 256), 256, 0, s>>>(hist, n_host, n_dev, n_cap, 1 << bits, n_ranges,
+                                                                       bin_ranges);
+      count_launches(1);
+      if (ranges_done) *ranges_done = true;
+    }
     if (wide) {
       k_radix_scatter<512><<<grid_cap(nchunks, 2), kScThreads, sizeof(ScatterSmem<512>), s>>>(
           keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_host, n_dev, n_cap, shift, bits, hist);
@@ -941,13 +965,12 @@ bool radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_
 
 template <class VS>
 void launch_keygen(const VS& vs, const unsigned long long* offsets, const uint32_t* touched,
-                   const unsigned long long* K_dev, int64_t n, const uint32_t* sorted_vals, const ushort4* rect,
-                   const float4* ext, const Rec* rec, const Params& P, int64_t cap,
-                   uint32_t* tile_keys, uint32_t* tile_vals, uint32_t* flags, cudaStream_t s,
-                   const unsigned long long* n_dev) {
+                   const unsigned long long* K_dev, int64_t n, const uint32_t* sorted_vals, const KeyShape* ks,
+                   const Params& P, int64_t cap, uint32_t* tile_keys, uint32_t* tile_vals, uint32_t* flags,
+                   cudaStream_t s, const unsigned long long* n_dev) {
   if (n <= 0 || cap <= 0) return;
   k_keygen<VS><<<grid_cap(cdiv(n, kKeygenThreads), 8), kKeygenThreads, 0, s>>>(
-      vs, offsets, K_dev, n, n_dev, sorted_vals, touched, rect, ext, rec, P, cap, tile_keys, tile_vals, flags);
+      vs, offsets, K_dev, n, n_dev, sorted_vals, touched, ks, P, cap, tile_keys, tile_vals, flags);
   count_launches(1);
 }
 
@@ -961,12 +984,12 @@ void launch_ranges(const uint32_t* tile_keys, const unsigned long long* K_dev, i
 }
 
 template void launch_keygen<FrameViews>(const FrameViews&, const unsigned long long*, const uint32_t*,
-                                        const unsigned long long*, int64_t, const uint32_t*, const ushort4*,
-                                        const float4*, const Rec*, const Params&, int64_t, uint32_t*, uint32_t*,
-                                        uint32_t*, cudaStream_t, const unsigned long long*);
+                                        const unsigned long long*, int64_t, const uint32_t*, const KeyShape*,
+                                        const Params&, int64_t, uint32_t*, uint32_t*, uint32_t*, cudaStream_t,
+                                        const unsigned long long*);
 template void launch_keygen<BatchViews>(const BatchViews&, const unsigned long long*, const uint32_t*,
-                                        const unsigned long long*, int64_t, const uint32_t*, const ushort4*,
-                                        const float4*, const Rec*, const Params&, int64_t, uint32_t*, uint32_t*,
-                                        uint32_t*, cudaStream_t, const unsigned long long*);
+                                        const unsigned long long*, int64_t, const uint32_t*, const KeyShape*,
+                                        const Params&, int64_t, uint32_t*, uint32_t*, uint32_t*, cudaStream_t,
+                                        const unsigned long long*);
 
 }  // namespace ges
