@@ -5,10 +5,10 @@
  *
  * The library renders a set of 3D primitives, each with mean mu, scale s,
  * rotation quaternion q, shape parameter beta, opacity kappa and spherical
- * harmonic (SH) colour coefficients (Sec. 3.1), to an image: projection of the
- * beta-modified covariance to a 2D conic (Sec. 3.1, EWA; Sec. 3.2, Eq. approx),
+ * harmonic (SH) colour coefficients (Sec. 4.1), to an image: projection of the
+ * beta-modified covariance to a 2D conic (Sec. 4.1, EWA; Sec. 4.2, Eq. approx),
  * tile|depth keys and a radix sort, front-to-back compositing with the GEF
- * falloff exp(-1/2 q^(beta/2)) (Sec. 3.1, Eq. ges; Sec. 3.2, Eq. transmittance),
+ * falloff exp(-1/2 q^(beta/2)) (Sec. 4.1, Eq. ges; Sec. 4.2, Eq. transmittance),
  * and the gradients of all primitive parameters (backward pass).
  *
  * Conventions shared by every entry point
@@ -58,7 +58,7 @@ typedef enum ges_falloff {
   /* exp(-1/2 q^(beta/2)) on the phi_bar-scaled covariance (Eq. ges with Eq. approx); default */
   GES_FALLOFF_GEF = 0,
   /* exp(-1/2 q) on the phi_bar-scaled covariance: the paper's Gaussian-form
-     rasterizer that only rescales the splat (Sec. 3.2, "Approximate Rasterization") */
+     rasterizer that only rescales the splat (Sec. 4.2, "Approximate Rasterization") */
   GES_FALLOFF_PAPER_APPROX = 1
 } ges_falloff;
 
@@ -68,7 +68,7 @@ typedef enum ges_phi_mode {
   /* the exact Gamma ratio of Eq. probablity normalised to 1 at beta = 2,
      phi_n(beta) = 2 Gamma(3/beta) / Gamma(1/beta), on the scale vector (the slot phi_bar approximates).
      phi_n is 4 at beta = 1, 240 at beta = 1/2 and over 1e5 below beta = 0.33: primitives of small beta
-     grow accordingly (the instability Sec. 3.2 gives as the reason for phi_bar) */
+     grow accordingly (the instability Sec. 4.2 gives as the reason for phi_bar) */
   GES_PHI_EXACT = 1,
   /* phi_n read as a ratio of variances (Eq. effective): sqrt(phi_n(beta)) on the scale vector */
   GES_PHI_EXACT_VARIANCE = 2
@@ -152,7 +152,7 @@ ges_status ges_frame_create(ges_ctx* ctx, int64_t n_capacity, int32_t width, int
 void ges_frame_destroy(ges_frame* frame);
 
 /* Preprocess (per primitive): scale modification phi_bar (Eq. approx), covariance from
-   scale and quaternion (Sec. 3.1), EWA projection to a 2D conic (Sec. 3.1), opacity-aware
+   scale and quaternion (Sec. 4.1), EWA projection to a 2D conic (Sec. 4.1), opacity-aware
    beta-dependent tile extent, depth key, SH colour.  scene->n <= n_capacity; the camera's
    size must equal the frame's.  The scene arrays must stay valid until ges_render_bwd
    (if used) has been enqueued. */
@@ -174,7 +174,7 @@ ges_status ges_preprocess(ges_frame* frame, const ges_scene* scene, const ges_ca
    calls are fixed in the graph. */
 ges_status ges_bin_sort(ges_frame* frame, void* stream);
 
-/* Forward composite (Sec. 3.2): per pixel, front to back over its tile's list,
+/* Forward composite (Sec. 4.2): per pixel, front to back over its tile's list,
    q = d^T conic d, G = exp(-1/2 q^(beta/2)) (or exp(-1/2 q)), alpha = min(alpha_max, kappa G),
    skip alpha < alpha_min, stop before T drops below t_min.  Outputs (device, caller-owned):
    img [3,H,W] = colour + T * bg, final_T [H,W], n_contrib [H,W] (1-based position, in the
@@ -238,7 +238,7 @@ ges_status ges_trace_enable(ges_ctx* ctx, int on);
 ges_status ges_trace_read(ges_ctx* ctx, int32_t capacity, char* names, int64_t* launches, double* total_ms,
                           int32_t* n_out);
 
-/* Training image loss (Sec. 3.3, Eq. mask, Eq. laplace, Eq. final; no rasterizer state).
+/* Training image loss (Sec. 4.3, Eq. mask, Eq. laplace, Eq. final; no rasterizer state).
 
    ges_freq_mask: the frequency-modulated mask M_omega of a ground-truth image gt [3,H,W] (fp32,
    device): the channel mean of gt, box-downsampled by f = round(1/scale) (the image-frequency
@@ -265,7 +265,7 @@ ges_status ges_image_loss(ges_ctx* ctx, const float* img, const float* gt, const
                           int32_t height, float lambda_ssim, float lambda_omega, float* loss, float* dL_dimg,
                           void* stream);
 
-/* Training-side updates (Sec. 3.4; App. B.2): the optimizer and the density control that consume
+/* Training-side updates (Sec. 4.4; App. B.2): the optimizer and the density control that consume
    ges_render_bwd's gradients, as in Gaussian splatting (whose optimisation the paper keeps) plus
    the paper's shape resets and shape pruning.
 
@@ -367,7 +367,7 @@ ges_status ges_density_control(ges_ctx* ctx, const ges_train_set* in, const floa
 ges_status ges_reset_opacity(ges_ctx* ctx, const ges_train_set* set, float max_opacity, void* stream);
 ges_status ges_reset_shape(ges_ctx* ctx, const ges_train_set* set, float beta, void* stream);
 
-/* The 1D mixture-fitting study (Sec. 3.5; App. A), batched: many independent fits of one model
+/* The 1D mixture-fitting study (Sec. 3.2; App. A), batched: many independent fits of one model
    with N components to 1D signals by full-batch Adam on the mean squared error.
 
    Models (App. A; eps = mix_eps, per component i):
@@ -428,7 +428,9 @@ ges_status ges_fit1d(ges_ctx* ctx, const ges_fit1d_params* p, int32_t runs, int3
    final_T [H,W], n_contrib [H,W] (device, caller-owned); stream as everywhere.
    Errors: GES_ERR_INVALID_ARG for a NULL pointer or a scene/image above the limits (nothing
    enqueued); GES_ERR_CAPACITY when the duplicates exceed their limit (outputs then hold the
-   background only).  The call synchronises `stream` before returning, to read that count.
+   background only); GES_ERR_DEVICE_WAIT when a radix sort's bounded wait on its predecessors
+   gave up (outputs then undefined; a later call starts afresh); GES_ERR_CUDA for a failed launch
+   or copy.  The call synchronises `stream` before returning, to read that count.
    Every intermediate buffer lives in one fixed array of about 24 MB in device global memory,
    which each GPU that loads the library holds until the process exits.  All calls share that
    array and it keeps the last call's contents: calls whose work overlaps on the GPU (other

@@ -81,3 +81,33 @@ def test_noalloc_refuses_sizes_above_its_limits(ges):
     with pytest.raises(ges.GesError) as e:
         ges.ges_render_fwd_noalloc(ges.make_scene(*ts, 0), ges.make_camera(wide), ges.params_default(), *outw)
     assert e.value.status == ges.GES_ERR_INVALID_ARG
+
+
+def test_noalloc_duplicate_overflow_reports_capacity_then_recovers(ges):
+    """Within the primitive and tile limits but above the duplicate limit (6,000 large primitives
+    over a 2048x2048 image list about 1.9M entries, against 1,048,576): the call reports
+    GES_ERR_CAPACITY and its outputs hold the background only; the next call within the limits
+    renders normally from the same array."""
+    from paper_2402_10128_gb300 import render, scenes
+    big = scenes.cube_scene(6000, seed=5, scale_range=(0.3, 0.5))
+    cam = scenes.tiny_camera(2048, 2048, bg=(0.25, 0.5, 0.75))
+    t = render.scene_tensors(big, "cuda")
+    fr = render.Frame(big.n, cam.width, cam.height)
+    fr.forward(t, big.sh_degree, cam)
+    assert fr.status()[1] > (1 << 20)  # the frame path's entry count for the same view
+    fr.close()
+    img = torch.full((3, cam.height, cam.width), -1.0, device="cuda")
+    T = torch.full((cam.height, cam.width), -1.0, device="cuda")
+    nc = torch.full((cam.height, cam.width), 7, dtype=torch.int32, device="cuda")
+    with pytest.raises(ges.GesError) as e:
+        ges.ges_render_fwd_noalloc(ges.make_scene(*t, big.sh_degree), ges.make_camera(cam), ges.params_default(),
+                                   img, T, nc)
+    assert e.value.status == ges.GES_ERR_CAPACITY
+    torch.cuda.synchronize()
+    bg = torch.tensor([0.25, 0.5, 0.75], device="cuda")[:, None, None]
+    assert torch.equal(img, bg.expand_as(img))
+    assert bool((T == 1.0).all()) and bool((nc == 0).all())
+    for scene, cam in _cases():
+        ref = _frame_path(ges, scene, cam)
+        got = _noalloc(ges, scene, cam)
+        assert np.abs(got[0] - ref[0]).max() <= IMG_TOL and np.array_equal(got[2], ref[2])
