@@ -5,14 +5,12 @@
 // with alpha_i = min(alpha_max, kappa_i G_i) and the GES falloff G = exp(-1/2 q^(beta/2))
 // (Sec. 4.1, Eq. ges) or the paper's Gaussian-form rasterizer G = exp(-1/2 q).
 //
-// The forward runs one CTA of 128 threads per 16x16 tile, two pixels per thread, (x, y) and
-// (x, y + 4), so a warp covers an 8x8 block.  The backward runs one CTA of 64 threads per tile,
-// four pixels per thread, (x, y + 4k) for k = 0..3, so a warp covers an 8x16 column and one
-// warp-wide sum of a fragment's gradient terms serves 128 pixels.  Pixels that share x and a
-// fragment run their arithmetic as packed float2 pairs, one instruction for two pixels.  The
-// tile's list is staged in shared memory one record per thread per round.  Both kernels evaluate
-// every (fragment, pixel) pair with eval_pair, so they take the same skip / clamp / stop decisions
-// bit for bit.
+// Both kernels run one CTA of 128 threads per 16x16 tile, two pixels per thread, (x, y) and
+// (x, y + 4), so a warp covers an 8x8 block (and, backward, its per-fragment gradient sum is shared
+// by 64 pixels).  The two pixels share x and every fragment, so their arithmetic runs as packed
+// float2 pairs, one instruction for both.  The tile's list is staged in shared memory one record
+// per thread per round.  Both kernels evaluate every (fragment, pixel) pair with eval_pair, so
+// they take the same skip / clamp / stop decisions bit for bit.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -20,7 +18,8 @@ namespace ges {
 
 namespace {
 
-constexpr int kThreads = 128;  // the backward's tile-order kernels
+constexpr int kThreads = 128;  // backward, per tile
+constexpr int kBatch = kThreads;
 constexpr int kFwdThreads = 128;
 constexpr int kFwdBatch = kFwdThreads;
 
@@ -322,174 +321,145 @@ __device__ __forceinline__ int reduce10_slot(unsigned lane) {
 //   dalpha/dkappa = G, dalpha/dG = kappa (0 where alpha is clamped)
 //   dG/dp = -G/2,  p = q^hb:  dp/dq = hb p / q,  dp/dhb = p ln q  (0 for q < 1e-12)
 //   q = a dx^2 + 2 b dx dy + c dy^2, dx = px - mx
-// Four pixels per thread: two warps per tile, warp w the 8x16 column at x = 8w, a thread's pixels
-// (x, y + 4k), k = 0..3, as two packed pairs (y, y + 4) and (y + 8, y + 12).  The thread adds its
-// four pixels' terms, the warp sums by a reduce-scatter butterfly, and ten lanes add the ten
-// per-primitive sums with one atomic each, so one reduction serves 128 pixels.  The fragment test
-// is eval_pair, as in the forward, so the skip / clamp / stop decisions equal the forward's bit for
-// bit.  Reciprocals use the approximate MUFU instruction (about 1 ulp); they only scale gradients,
-// never decide a branch.  The falloff mode is a template parameter: the Gaussian form has no
-// exponent path.
-constexpr int kQThreads = 64;
-constexpr int kQBatch = kQThreads;
-
-__device__ __forceinline__ WarpBlock quad_block(int lt, int tiles_x) {
-  const int tx = lt % tiles_x, ty = lt / tiles_x;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  WarpBlock b;
-  b.x = tx * kTile + w * 8 + (lane & 7);
-  b.y = ty * kTile + (lane >> 3);
-  return b;
-}
-
-struct PairState {
-  float2 T, U, GC0, GC1, GC2;
-  uint32_t last0, last1;
-};
-
-template <class VD>
-__device__ __forceinline__ void load_pair(PairState& s, const VD& vd, int x, int y, int64_t plane) {
-  float Tk[2] = {0.f, 0.f}, g0[2] = {0.f, 0.f}, g1[2] = {0.f, 0.f}, g2[2] = {0.f, 0.f};
-  uint32_t la[2] = {0u, 0u};
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const int yy = y + 4 * k;
-    if (x < vd.W && yy < vd.H) {
-      const int64_t pix = (int64_t)yy * vd.W + x;
-      Tk[k] = vd.final_T[pix];
-      la[k] = vd.n_contrib[pix];
-      g0[k] = vd.dL_dimg[pix];
-      g1[k] = vd.dL_dimg[plane + pix];
-      g2[k] = vd.dL_dimg[2 * plane + pix];
-    }
-  }
-  s.T = make_float2(Tk[0], Tk[1]);
-  s.GC0 = make_float2(g0[0], g0[1]);
-  s.GC1 = make_float2(g1[0], g1[1]);
-  s.GC2 = make_float2(g2[0], g2[1]);
-  s.U = __fmul2_rn(s.T, __ffma2_rn(s.GC2, make_float2(vd.bg[2], vd.bg[2]),
-                                   __ffma2_rn(s.GC1, make_float2(vd.bg[1], vd.bg[1]),
-                                              __fmul2_rn(s.GC0, make_float2(vd.bg[0], vd.bg[0])))));
-  s.last0 = la[0];
-  s.last1 = la[1];
-}
-
-// One pixel pair's gradient terms of a fragment, added into v (v set when `first`); T and U step
-// back past the fragment.  Constant factors are left out here and applied to the warp's sums
-// (slot_scale): the derivative of G = 2^(-p log2(e)/2) w.r.t. p is taken as G (true: -G/2), the
-// record's conic terms as (a, b, c) (true: -2 (a, b, c)), 2 dx dy as dx dy, and ln q as log2 q.
-template <bool GEF>
-__device__ __forceinline__ void pair_terms(PairState& s, const PairEval& f, bool act0, bool act1, bool cl0, bool cl1,
-                                           float al0, float al1, const RecPairB& r, float (&v)[10], bool first) {
-  const float2 ONE = make_float2(1.0f, 1.0f), NEG1 = make_float2(-1.0f, -1.0f), ZERO = make_float2(0.f, 0.f);
-  const float4 n0 = r.n0, n1 = r.n1, k0 = r.k0, k1 = r.k1, e = r.e, c1 = r.c1;
-  const float q0 = f.q0, q1 = f.q1, hb = e.z;
-  const float2 alpha = make_float2(act0 ? al0 : 0.f, act1 ? al1 : 0.f);
-  const float2 om = __ffma2_rn(alpha, NEG1, ONE);
-  const float2 inv = make_float2(act0 ? rcp_approx(om.x) : 1.0f, act1 ? rcp_approx(om.y) : 1.0f);
-  s.T = __fmul2_rn(s.T, inv);
-  const float2 w = __fmul2_rn(alpha, s.T);
-  const float2 D = __ffma2_rn(s.GC2, lo2(k1), __ffma2_rn(s.GC1, hi2(k0), __fmul2_rn(s.GC0, lo2(k0))));
-  const float2 dLda_all = __ffma2_rn(s.U, make_float2(-inv.x, -inv.y), __fmul2_rn(D, s.T));
-  const float2 dLdaG = sel2(act0 && !cl0, act1 && !cl1, dLda_all, ZERO);
-  s.U = __ffma2_rn(D, w, s.U);
-  const float2 gr = __fmul2_rn(s.GC0, w), gg = __fmul2_rn(s.GC1, w), gbl = __fmul2_rn(s.GC2, w);
-  const float2 gk = __fmul2_rn(dLdaG, f.G);
-  const float2 dp = __fmul2_rn(gk, hi2(c1));  // x (-1/2)
-  float2 dq, gbeta = ZERO;
-  if (GEF) {
-    const bool m0 = act0 && q0 > 1e-12f, m1 = act1 && q1 > 1e-12f;
-    if (hb == 1.0f) {
-      dq = sel2(m0, m1, dp, ZERO);
-      const float2 l2 = make_float2(m0 ? mufu_lg2(q0) : 0.f, m1 ? mufu_lg2(q1) : 0.f);
-      gbeta = __fmul2_rn(__fmul2_rn(dq, make_float2(q0, q1)), l2);  // x (-ln 2 / 2)
-    } else {
-      const float2 rq = make_float2(rcp_approx(q0), rcp_approx(q1));
-      const float2 dpp = __fmul2_rn(dp, f.p);
-      dq = sel2(m0, m1, __fmul2_rn(__fmul2_rn(dpp, hi2(e)), rq), ZERO);
-      gbeta = sel2(m0, m1, __fmul2_rn(dpp, f.lq), ZERO);                // x (-ln 2 / 2)
-    }
-  } else {
-    dq = dp;
-  }
-  const float2 dqdx = __fmul2_rn(dq, f.dx), dqdy = __fmul2_rn(dq, f.dy);
-  const float2 gmx = __ffma2_rn(dqdy, hi2(n0), __fmul2_rn(dqdx, lo2(n0)));
-  const float2 gmy = __ffma2_rn(dqdy, lo2(n1), __fmul2_rn(dqdx, hi2(n0)));
-  const float2 ga = __fmul2_rn(dqdx, f.dx);   // x (-1/2)
-  const float2 gb = __fmul2_rn(dqdx, f.dy);   // x (-1)
-  const float2 gcc = __fmul2_rn(dqdy, f.dy);  // x (-1/2)
-  const float t[10] = {gmx.x + gmx.y, gmy.x + gmy.y, ga.x + ga.y,   gb.x + gb.y,   gcc.x + gcc.y,
-                       gk.x + gk.y,   gbeta.x + gbeta.y, gr.x + gr.y, gg.x + gg.y, gbl.x + gbl.y};
-#pragma unroll
-  for (int k = 0; k < 10; ++k) v[k] = first ? t[k] : v[k] + t[k];
-}
-
+// A thread's two pixels share x and the fragment, so their arithmetic runs as float2 pairs (one
+// packed instruction for both).  The fragment test is eval_pair, as in the forward, so the skip /
+// clamp / stop decisions equal the forward's bit for bit.  A thread sums
+// its two pixels' terms, the warp sums by a reduce-scatter butterfly, and ten lanes add the ten
+// per-primitive sums with one predicated atomic each.  Reciprocals use the approximate MUFU
+// instruction (about 1 ulp); they only scale gradients, never decide a branch.  The falloff mode is
+// a template parameter, so the Gaussian form carries no exponent path and no mode branch.
 template <class VS, bool GEF>
-__global__ void __launch_bounds__(kQThreads) k_render_bwd(const __grid_constant__ VS vs, const uint2* __restrict__ ranges,
-                                                          const uint32_t* __restrict__ keys,
-                                                          const uint32_t* __restrict__ vals, const Rec* __restrict__ rec,
-                                                          const Params P, float4* __restrict__ g2d,
-                                                          const uint32_t* __restrict__ order) {
-  __shared__ Stage<RecPairB, kQBatch> st;
+__global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__ VS vs, const uint2* __restrict__ ranges,
+                                                         const uint32_t* __restrict__ keys,
+                                                         const uint32_t* __restrict__ vals, const Rec* __restrict__ rec,
+                                                         const Params P, float4* __restrict__ g2d,
+                                                         const uint32_t* __restrict__ order) {
+  __shared__ Stage<RecPairB, kBatch> st;
   __shared__ uint32_t s_max_last;
   const auto& vt = vs.get();
   const int64_t tile = order ? (int64_t)order[blockIdx.x] : (int64_t)blockIdx.x;
-  if (tile >= (int64_t)vt.total_tiles) return;
+  if (tile >= (int64_t)vt.total_tiles) return;  // (order is a permutation of the tiles)
   const ViewDesc& vd = vt.v[view_of_tile(vt, tile)];
   const int lt = (int)(tile - vd.tile_base);
   const int tx = lt % vd.tiles_x, ty = lt / vd.tiles_x;
-  const WarpBlock wb = quad_block(lt, vd.tiles_x);
+  const WarpBlock wb = warp_block(lt, vd.tiles_x);
   const uint2 rg = ranges[vd.seg_base + ty * vd.segs_x + (tx >> P.seg_log2)];
   const uint32_t to = (uint32_t)tx & ((1u << P.seg_log2) - 1u);
   const int64_t plane = (int64_t)vd.W * vd.H;
-  PairState A, B;
-  load_pair(A, vd, wb.x, wb.y, plane);
-  load_pair(B, vd, wb.x, wb.y + 8, plane);
+
+  float Tk[2], gc[3][2];
+  uint32_t last[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int y = wb.y + 4 * k;
+    const bool inside = wb.x < vd.W && y < vd.H;
+    Tk[k] = 0.f;
+    gc[0][k] = gc[1][k] = gc[2][k] = 0.f;
+    last[k] = 0;
+    if (inside) {
+      const int64_t pix = (int64_t)y * vd.W + wb.x;
+      Tk[k] = vd.final_T[pix];
+      last[k] = vd.n_contrib[pix];
+      gc[0][k] = vd.dL_dimg[pix];
+      gc[1][k] = vd.dL_dimg[plane + pix];
+      gc[2][k] = vd.dL_dimg[2 * plane + pix];
+    }
+  }
   const float2 PX = make_float2((float)wb.x + 0.5f, (float)wb.x + 0.5f);
-  const float2 PYA = make_float2((float)wb.y + 0.5f, (float)(wb.y + 4) + 0.5f);
-  const float2 PYB = make_float2((float)(wb.y + 8) + 0.5f, (float)(wb.y + 12) + 0.5f);
-  const uint32_t mylast = max(max(A.last0, A.last1), max(B.last0, B.last1));
+  const float2 PY = make_float2((float)wb.y + 0.5f, (float)(wb.y + 4) + 0.5f);
+  const float2 GC0 = make_float2(gc[0][0], gc[0][1]), GC1 = make_float2(gc[1][0], gc[1][1]),
+               GC2 = make_float2(gc[2][0], gc[2][1]);
+  float2 T = make_float2(Tk[0], Tk[1]);
+  // U = sum_c dL/dC_c S_c, S_c the colour composited behind the current fragment (at the start,
+  // T_final bg_c): dL/dalpha_i needs S only through this sum, so one float2 carries it.
+  float2 U = __fmul2_rn(T, __ffma2_rn(GC2, make_float2(vd.bg[2], vd.bg[2]),
+                                      __ffma2_rn(GC1, make_float2(vd.bg[1], vd.bg[1]),
+                                                 __fmul2_rn(GC0, make_float2(vd.bg[0], vd.bg[0])))));
   if (threadIdx.x == 0) s_max_last = 0;
   __syncthreads();
-  atomicMax(&s_max_last, mylast);
+  atomicMax(&s_max_last, max(last[0], last[1]));
   __syncthreads();
   const uint32_t max_last = s_max_last;
-  const uint32_t wlast = __reduce_max_sync(0xffffffffu, mylast);
+  const uint32_t wlast = __reduce_max_sync(0xffffffffu, max(last[0], last[1]));
+  constexpr bool gef = GEF;
   const unsigned lane = threadIdx.x & 31u;
   const int slot = reduce10_slot(lane);
   const bool adder = (lane & 1u) == 0 && slot >= 0;
+  // the constant factor each summed value still lacks (see the loop)
   const float kSlotScale[10] = {1.0f, 1.0f, -0.5f, -1.0f, -0.5f, 1.0f, -0.34657359027997264f, 1.0f, 1.0f, 1.0f};
   float slot_scale = 1.0f;
 #pragma unroll
   for (int k = 0; k < 10; ++k) slot_scale = slot == k ? kSlotScale[k] : slot_scale;
+  const float2 ONE = make_float2(1.0f, 1.0f), NEG1 = make_float2(-1.0f, -1.0f), ZERO = make_float2(0.f, 0.f);
 
   for (uint32_t end = rg.x + max_last; end > rg.x;) {
-    const uint32_t start = (end - rg.x > (uint32_t)kQBatch) ? end - kQBatch : rg.x;
-    __syncthreads();
+    const uint32_t start = (end - rg.x > (uint32_t)kBatch) ? end - kBatch : rg.x;
+    __syncthreads();  // the previous round's readers of the staged list are done
     const uint32_t idx = start + threadIdx.x;
     const bool keep = idx < end && seg_key_covers(keys[idx], to, P);
-    const int cnt = stage_kept<kQBatch>(st, keep, idx, rg.x, vals, [&](RecPairB& d, uint32_t g) {
+    const int cnt = stage_kept<kBatch>(st, keep, idx, rg.x, vals, [&](RecPairB& d, uint32_t g) {
       const Rec r = rec[g];
       stage_pair(d, r);
       d.n0 = make_float4(r.b.x, r.b.x, r.b.y, r.b.y);
       d.n1 = make_float4(r.b.z, r.b.z, 0.f, 0.f);
     });
     for (int j = cnt - 1; j >= 0; --j) {
-      const uint32_t kpos = st.pos[j];
-      if (kpos > wlast) continue;
-      PairEval fa, fb;
-      eval_pair(st.rec[j], PX, PYA, fa);
-      eval_pair(st.rec[j], PX, PYB, fb);
-      const bool cla0 = fa.a.x > P.alpha_max, cla1 = fa.a.y > P.alpha_max;
-      const bool clb0 = fb.a.x > P.alpha_max, clb1 = fb.a.y > P.alpha_max;
-      const float ala0 = cla0 ? P.alpha_max : fa.a.x, ala1 = cla1 ? P.alpha_max : fa.a.y;
-      const float alb0 = clb0 ? P.alpha_max : fb.a.x, alb1 = clb1 ? P.alpha_max : fb.a.y;
-      const bool acta0 = kpos <= A.last0 && ala0 >= P.alpha_min, acta1 = kpos <= A.last1 && ala1 >= P.alpha_min;
-      const bool actb0 = kpos <= B.last0 && alb0 >= P.alpha_min, actb1 = kpos <= B.last1 && alb1 >= P.alpha_min;
-      if (!__any_sync(0xffffffffu, acta0 || acta1 || actb0 || actb1)) continue;
-      float v[10];
-      pair_terms<GEF>(A, fa, acta0, acta1, cla0, cla1, ala0, ala1, st.rec[j], v, true);
-      pair_terms<GEF>(B, fb, actb0, actb1, clb0, clb1, alb0, alb1, st.rec[j], v, false);
+      const uint32_t kpos = st.pos[j];  // 1-based position in the segment's list
+      if (kpos > wlast) continue;       // beyond every pixel of this warp
+      PairEval f;
+      eval_pair(st.rec[j], PX, PY, f);
+      const bool cl0 = f.a.x > P.alpha_max, cl1 = f.a.y > P.alpha_max;
+      const float al0 = cl0 ? P.alpha_max : f.a.x, al1 = cl1 ? P.alpha_max : f.a.y;
+      const bool act0 = kpos <= last[0] && al0 >= P.alpha_min;
+      const bool act1 = kpos <= last[1] && al1 >= P.alpha_min;
+      if (!__any_sync(0xffffffffu, act0 || act1)) continue;
+      // gradient terms of both pixels (zero for an inactive one, whose T and S stay as they are).
+      // Constant factors are left out here and applied to the warp's sums (slot_scale): the
+      // derivative of G = 2^(-p log2(e)/2) w.r.t. p is taken as G (true: -G/2), the record's conic
+      // terms as (a, b, c) (true: -2 (a, b, c)), 2 dx dy as dx dy, and ln q as log2 q.
+      const float4 n0 = st.rec[j].n0, n1 = st.rec[j].n1, k0 = st.rec[j].k0, k1 = st.rec[j].k1;
+      const float4 e = st.rec[j].e, c1 = st.rec[j].c1;
+      const float2 dx = f.dx, dy = f.dy, p = f.p, lq = f.lq, G = f.G;
+      const float q0 = f.q0, q1 = f.q1, hb = e.z;
+      const float2 alpha = make_float2(act0 ? al0 : 0.f, act1 ? al1 : 0.f);
+      const float2 om = __ffma2_rn(alpha, NEG1, ONE);
+      const float2 inv = make_float2(act0 ? rcp_approx(om.x) : 1.0f, act1 ? rcp_approx(om.y) : 1.0f);
+      T = __fmul2_rn(T, inv);
+      const float2 w = __fmul2_rn(alpha, T);
+      // D = sum_c dL/dC_c c_c;  dL/dalpha = D T_i - U / (1 - alpha_i);  U += D alpha_i T_i
+      const float2 D = __ffma2_rn(GC2, lo2(k1), __ffma2_rn(GC1, hi2(k0), __fmul2_rn(GC0, lo2(k0))));
+      const float2 dLda_all = __ffma2_rn(U, make_float2(-inv.x, -inv.y), __fmul2_rn(D, T));
+      // dalpha/dG = kappa and dalpha/dkappa = G, both 0 where alpha is clamped or the pixel inactive
+      const float2 dLdaG = sel2(act0 && !cl0, act1 && !cl1, dLda_all, ZERO);
+      U = __ffma2_rn(D, w, U);
+      const float2 gr = __fmul2_rn(GC0, w), gg = __fmul2_rn(GC1, w), gbl = __fmul2_rn(GC2, w);
+      const float2 gk = __fmul2_rn(dLdaG, G);
+      const float2 dp = __fmul2_rn(gk, hi2(c1));  // x (-1/2)
+      float2 dq, gbeta = ZERO;
+      if (gef) {
+        // only where the pixel takes the fragment (elsewhere p may overflow) and q > 1e-12
+        const bool m0 = act0 && q0 > 1e-12f, m1 = act1 && q1 > 1e-12f;
+        if (hb == 1.0f) {
+          dq = sel2(m0, m1, dp, ZERO);
+          const float2 l2 = make_float2(m0 ? mufu_lg2(q0) : 0.f, m1 ? mufu_lg2(q1) : 0.f);
+          gbeta = __fmul2_rn(__fmul2_rn(dq, make_float2(q0, q1)), l2);  // x (-ln 2 / 2)
+        } else {
+          const float2 rq = make_float2(rcp_approx(q0), rcp_approx(q1));
+          const float2 dpp = __fmul2_rn(dp, p);
+          dq = sel2(m0, m1, __fmul2_rn(__fmul2_rn(dpp, hi2(e)), rq), ZERO);
+          gbeta = sel2(m0, m1, __fmul2_rn(dpp, lq), ZERO);                // x (-ln 2 / 2)
+        }
+      } else {
+        dq = dp;
+      }
+      const float2 dqdx = __fmul2_rn(dq, dx), dqdy = __fmul2_rn(dq, dy);
+      const float2 gmx = __ffma2_rn(dqdy, hi2(n0), __fmul2_rn(dqdx, lo2(n0)));
+      const float2 gmy = __ffma2_rn(dqdy, lo2(n1), __fmul2_rn(dqdx, hi2(n0)));
+      const float2 ga = __fmul2_rn(dqdx, dx);   // x (-1/2)
+      const float2 gb = __fmul2_rn(dqdx, dy);   // x (-1)
+      const float2 gcc = __fmul2_rn(dqdy, dy);  // x (-1/2)
+      float v[10] = {gmx.x + gmx.y, gmy.x + gmy.y, ga.x + ga.y,   gb.x + gb.y,   gcc.x + gcc.y,
+                     gk.x + gk.y,   gbeta.x + gbeta.y, gr.x + gr.y, gg.x + gg.y, gbl.x + gbl.y};
       const float sum = warp_reduce_scatter10(v);
       {  // ten lanes add their sums: a predicated reduction, no divergent branch
         float* dst = reinterpret_cast<float*>(g2d + 3 * (int64_t)st.id[j]) + slot;
@@ -609,9 +579,9 @@ void launch_render_bwd(const VS& vs, int64_t total_tiles, const uint2* ranges, c
                        const uint32_t* order) {
   if (total_tiles <= 0) return;
   if (P.mode == 0)
-    k_render_bwd<VS, true><<<(unsigned)total_tiles, kQThreads, 0, s>>>(vs, ranges, keys, vals, rec, P, g2d, order);
+    k_render_bwd<VS, true><<<(unsigned)total_tiles, kThreads, 0, s>>>(vs, ranges, keys, vals, rec, P, g2d, order);
   else
-    k_render_bwd<VS, false><<<(unsigned)total_tiles, kQThreads, 0, s>>>(vs, ranges, keys, vals, rec, P, g2d, order);
+    k_render_bwd<VS, false><<<(unsigned)total_tiles, kThreads, 0, s>>>(vs, ranges, keys, vals, rec, P, g2d, order);
   count_launches(1);
 }
 
