@@ -417,11 +417,6 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(const __grid_constant__ 
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int b = 0; b < 3; ++b) M[3 * a + b] = R[3 * a + b] * sp[b];
-    float Sg[9];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) Sg[3 * a + b] = M[3 * a] * M[3 * b] + M[3 * a + 1] * M[3 * b + 1] + M[3 * a + 2] * M[3 * b + 2];
     const float limx = P.clamp_fov * 0.5f * (float)vd.W / vd.fx;
     const float limy = P.clamp_fov * 0.5f * (float)vd.H / vd.fy;
     const float rxr = t[0] * iz, ryr = t[1] * iz;
@@ -435,35 +430,40 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(const __grid_constant__ 
       T[b] = J00 * V[b] + J02 * V[8 + b];
       T[3 + b] = J11 * V[4 + b] + J12 * V[8 + b];
     }
-    float TS[6];  // T Sigma
+    // ---- Sigma' = U U^T + dilation, U = T M (2x3): column b is axis b of the scaled rotation,
+    // projected.  The chain below goes through U and W = Q U rather than through the 3x3 gradient
+    // of Sigma: for an elongated splat the latter's entries are orders of magnitude larger than
+    // the scale gradient along the long axis, which FP32 would then form as a difference of large
+    // terms.  With G = [[gA, gB/2], [gB/2, gC]] and dL/dSigma' = -Q G Q:
+    //   dL/dM = -2 T^T (Q G W),  dL/dT = -2 (Q G W) M^T,  dL/dsp_b = -(2/sp_b) W_b^T G W_b
+    float U[6];
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+    for (int r = 0; r < 2; ++r)
 #pragma unroll
-      for (int b = 0; b < 3; ++b) TS[3 * a + b] = T[3 * a] * Sg[b] + T[3 * a + 1] * Sg[3 + b] + T[3 * a + 2] * Sg[6 + b];
-    const float ca = TS[0] * T[0] + TS[1] * T[1] + TS[2] * T[2] + P.dilation;
-    const float cb = TS[0] * T[3] + TS[1] * T[4] + TS[2] * T[5];
-    const float cc = TS[3] * T[3] + TS[4] * T[4] + TS[5] * T[5] + P.dilation;
+      for (int b = 0; b < 3; ++b) U[3 * r + b] = T[3 * r] * M[b] + T[3 * r + 1] * M[3 + b] + T[3 * r + 2] * M[6 + b];
+    const float ca = U[0] * U[0] + U[1] * U[1] + U[2] * U[2] + P.dilation;
+    const float cb = U[0] * U[3] + U[1] * U[4] + U[2] * U[5];
+    const float cc = U[3] * U[3] + U[4] * U[4] + U[5] * U[5] + P.dilation;
     const float idet = 1.0f / (ca * cc - cb * cb);
     const float QA = cc * idet, QB = -cb * idet, QC = ca * idet;
-
-    // ---- conic = inverse(Sigma'):  dL/dSigma' = -Q G_Q Q,  G_Q = [[gA, gB/2], [gB/2, gC]]
     const float h = 0.5f * g_B;
-    const float t00 = QA * g_A + QB * h, t01 = QA * h + QB * g_C;
-    const float t10 = QB * g_A + QC * h, t11 = QB * h + QC * g_C;
-    const float GS00 = -(t00 * QA + t01 * QB), GS01 = -(t00 * QB + t01 * QC), GS11 = -(t10 * QB + t11 * QC);
-    // ---- Sigma' = T Sigma T^T: G_Sigma = T^T GS T,  G_T = 2 GS T Sigma
-    float GT[6];
+    float Wq[6], Vq[6], QV[6];  // W = Q U, V = G W, QV = Q V
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      GT[b] = 2.f * (GS00 * TS[b] + GS01 * TS[3 + b]);
-      GT[3 + b] = 2.f * (GS01 * TS[b] + GS11 * TS[3 + b]);
+      Wq[b] = QA * U[b] + QB * U[3 + b];
+      Wq[3 + b] = QB * U[b] + QC * U[3 + b];
+      Vq[b] = g_A * Wq[b] + h * Wq[3 + b];
+      Vq[3 + b] = h * Wq[b] + g_C * Wq[3 + b];
+      QV[b] = QA * Vq[b] + QB * Vq[3 + b];
+      QV[3 + b] = QB * Vq[b] + QC * Vq[3 + b];
     }
-    float GSig[9];
+    // dL/dT = -2 QV M^T (2x3)
+    float GT[6];
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+    for (int r = 0; r < 2; ++r)
 #pragma unroll
-      for (int b = 0; b < 3; ++b)
-        GSig[3 * a + b] = T[a] * (GS00 * T[b] + GS01 * T[3 + b]) + T[3 + a] * (GS01 * T[b] + GS11 * T[3 + b]);
+      for (int c = 0; c < 3; ++c)
+        GT[3 * r + c] = -2.f * (QV[3 * r] * M[3 * c] + QV[3 * r + 1] * M[3 * c + 1] + QV[3 * r + 2] * M[3 * c + 2]);
     // ---- T = J W: only J00, J02, J11, J12 are non-zero
     float gJ00 = 0.f, gJ02 = 0.f, gJ11 = 0.f, gJ12 = 0.f;
 #pragma unroll
@@ -486,16 +486,21 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(const __grid_constant__ 
     float gmu[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) gmu[a] = V[a] * gt[0] + V[4 + a] * gt[1] + V[8 + a] * gt[2];
-    // ---- Sigma = M M^T: G_M = 2 G_Sigma M;  M = R diag(sp)
-    float gR[9], gsp[3] = {0.f, 0.f, 0.f};
+    // ---- M = R diag(sp): dL/dsp_b from W and V; the rotation through the torques about the body
+    // axes, tau_k = dL/dtheta_k for R -> R Rot_k(theta), which is
+    //   tau_k = -2 (s_i^2 - s_j^2) (W_i/s_i)^T G (W_j/s_j),  (i, j, k) cyclic,
+    // so that a rotation about an axis of equal scales gets an exact zero rather than the
+    // difference of two large terms
+    float gsp[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) gsp[b] = -2.f * (Wq[b] * Vq[b] + Wq[3 + b] * Vq[3 + b]) / sp[b];
+    float tau[3];
 #pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        float gM = 2.f * (GSig[3 * a] * M[b] + GSig[3 * a + 1] * M[3 + b] + GSig[3 * a + 2] * M[6 + b]);
-        gR[3 * a + b] = gM * sp[b];
-        gsp[b] += gM * R[3 * a + b];
-      }
+    for (int k = 0; k < 3; ++k) {
+      const int i = (k + 1) % 3, j = (k + 2) % 3;
+      const float wv = Wq[i] * Vq[j] + Wq[3 + i] * Vq[3 + j];
+      tau[k] = -2.f * ((sp[i] - sp[j]) * (sp[i] + sp[j]) / (sp[i] * sp[j])) * wv;
+    }
     const float gphi = s[0] * gsp[0] + s[1] * gsp[1] + s[2] * gsp[2];
     // d phi / d beta: rho phi (1 - phi/2) for phi_bar; c phi (psi(1/beta) - 3 psi(3/beta)) / beta^2 for
     // phi_n^c (c = 1, or 1/2 for the variance reading)
@@ -508,13 +513,14 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(const __grid_constant__ 
       gbeta = gphi * phi * (P.phi_mode == 2 ? 0.5f * dl : dl);
     }
     if (P.mode == 0) gbeta += 0.5f * g_hb;
-    // ---- rotation from the normalised quaternion
-    float gw = 2.f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
-    float gx = 2.f * (y * gR[1] + z * gR[2] + y * gR[3] - 2.f * x * gR[4] - w * gR[5] + z * gR[6] + w * gR[7] - 2.f * x * gR[8]);
-    float gy = 2.f * (-2.f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] + z * gR[7] - 2.f * y * gR[8]);
-    float gz = 2.f * (-2.f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * z * gR[4] + y * gR[5] + x * gR[6] + y * gR[7]);
-    const float dotq = w * gw + x * gx + y * gy + z * gz;
-    const float4 gq = make_float4((gw - w * dotq) * rn, (gx - x * dotq) * rn, (gy - y * dotq) * rn, (gz - z * dotq) * rn);
+    // ---- quaternion: a body rotation dtheta moves the unit quaternion by q (x) (0, dtheta)/2, whose
+    // directions span the tangent space at q orthonormally, so dL/dq = 2 q (x) (0, tau) / |q|
+    // (with respect to the unnormalised input, orthogonal to q)
+    const float gsc = 2.f * rn;
+    const float4 gq = make_float4(-(x * tau[0] + y * tau[1] + z * tau[2]) * gsc,
+                                  (w * tau[0] + (y * tau[2] - z * tau[1])) * gsc,
+                                  (w * tau[1] + (z * tau[0] - x * tau[2])) * gsc,
+                                  (w * tau[2] + (x * tau[1] - y * tau[0])) * gsc);
 
     // ---- SH colour
     const float dvx = mu[0] - vd.campos[0], dvy = mu[1] - vd.campos[1], dvz = mu[2] - vd.campos[2];
