@@ -226,8 +226,8 @@ uint64_t ges_kernel_launches(void);
    kernel launch or launch group that the frame calls of this context make (ges_preprocess,
    ges_bin_sort, ges_render_fwd, ges_render_bwd) is bracketed by two CUDA events recorded on the
    caller's stream.  The names are the kernel names, or for a group its stage:
-   "k_preprocess", "depth_sort", "gather_touched", "scan_touched", "k_keygen", "list_sort",
-   "k_ranges", "k_render_fwd", "k_render_bwd", "k_preprocess_bwd".
+   "k_preprocess", "depth_sort", "scan_touched", "k_keygen", "list_sort", "k_ranges",
+   "k_render_fwd", "tile_order", "k_render_bwd", "k_preprocess_bwd".
    ges_trace_enable(ctx, 1) starts a new record (0 stops recording and keeps the record).
    ges_trace_read synchronises with the recorded events and writes, per name in first-launch
    order, at most `capacity` entries: names[32*i..] (NUL-terminated), launches[i], total_ms[i]

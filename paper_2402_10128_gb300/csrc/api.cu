@@ -545,14 +545,10 @@ ges_status ges_bin_sort(ges_frame* f, void* stream) {
       return fail(GES_ERR_CUDA, "internal: depth-sort histogram exceeds its buffer");
   }
   f->sorted_prims = f->pv[cur];
-  // tiles touched in depth order, exclusive scan -> offsets, K
-  {
-    TraceScope tr(f->ctx, "gather_touched", s);
-    launch_gather_touched(f->sorted_prims, f->tprim, f->n, f->touched, s);
-  }
+  // list entries per primitive in depth order and their exclusive scan -> offsets, K
   {
     TraceScope tr(f->ctx, "scan_touched", s);
-    scan_exclusive_onepass(f->touched, f->offsets, f->n, f->d_K, f->scan, f->d_flags, s);
+    scan_gather_onepass(f->tprim, f->sorted_prims, f->touched, f->offsets, f->n, f->d_K, f->scan, f->d_flags, s);
   }
   if (f->auto_cap) {
     if ((e = cudaMemcpyAsync(f->h_K, f->d_K, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(e, "read K");

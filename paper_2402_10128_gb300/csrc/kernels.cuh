@@ -43,10 +43,12 @@ void scan_exclusive_onepass(const uint32_t* in, unsigned long long* out, int64_t
 void scan_exclusive_onepass(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total, ScanScratch& sc,
                             uint32_t* flags, cudaStream_t s, const unsigned long long* n_dev = nullptr);
 
-// per-primitive tile counts in depth order: touched[j] = tprim[sorted_vals[j]] for j < count
-// (count = min(*n_dev, n) if n_dev is given, else n)
-void launch_gather_touched(const uint32_t* sorted_vals, const uint32_t* tprim, int64_t n, uint32_t* touched,
-                           cudaStream_t s, const unsigned long long* n_dev = nullptr);
+// the same over counts[ids[j]]: gathered[j] = counts[ids[j]] and out[j] = the sum of gathered[0..j)
+// for j < count (min(*n_dev, n) with n_dev, else n); *total gets the sum.  The list entries of the
+// primitives in depth order and their offsets, in one launch.
+void scan_gather_onepass(const uint32_t* counts, const uint32_t* ids, uint32_t* gathered, unsigned long long* out,
+                         int64_t n, unsigned long long* total, ScanScratch& sc, uint32_t* flags, cudaStream_t s,
+                         const unsigned long long* n_dev = nullptr);
 
 // stable LSD radix sort of (u32 key, u32 value) on the low `total_bits` bits.  The element count is
 // n_dev (device) if non-null, else n_host; buffers hold n_cap elements.  keys[cur]/vals[cur] hold the

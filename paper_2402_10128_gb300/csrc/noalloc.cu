@@ -176,8 +176,7 @@ extern "C" ges_status ges_render_fwd_noalloc(const ges_scene* scene, const ges_c
   int cur = 0;
   if (!radix_sort_pairs(dk, pv, cur, n, nullptr, n, 32, hist, kNaHistEntries, scan, s, flags))
     return fail(GES_ERR_CUDA, "internal: depth-sort histogram exceeds its buffer");
-  launch_gather_touched(pv[cur], tprim, n, touched, s);
-  scan_exclusive_onepass(touched, offsets, n, dK, scan, flags, s);
+  scan_gather_onepass(tprim, pv[cur], touched, offsets, n, dK, scan, flags, s);
   launch_keygen<FrameViews>(vt, offsets, touched, dK, n, pv[cur], ks, P, kNaMaxKeys,
                             tk[0], tv[0], flags, s);
   int tcur = 0;

@@ -187,8 +187,7 @@ ges_status ws_alloc(ges_server* S, Workspace& w, int64_t P_cap, int64_t T_cap, i
                                 s);
   int cur = 0;
   bool fits = radix_sort_pairs(w.dk, w.pv, cur, 0, n_dev, P_cap, 32, w.hist, w.hist_cap, w.scan, s, flags);
-  launch_gather_touched(w.pv[cur], w.tprim, P_cap, w.touched, s, n_dev);
-  scan_exclusive_onepass(w.touched, w.offsets, P_cap, dK, w.scan, flags, s, n_dev);
+  scan_gather_onepass(w.tprim, w.pv[cur], w.touched, w.offsets, P_cap, dK, w.scan, flags, s, n_dev);
   launch_keygen<BatchViews>(vs, w.offsets, w.touched, dK, P_cap, w.pv[cur], w.ks, S->P, K_cap,
                             w.tk[0], w.tv[0], flags, s, n_dev);
   int tcur = 0;

@@ -6,7 +6,8 @@
 // bits, so sorting primitives by depth first and duplicating them in that order gives the
 // same list as sorting the duplicates on the depth digits.  The remaining passes are a
 // stable radix sort of the duplicates on the tile id alone (ceil(log2 tiles) bits).
-//   K2  exclusive scan of tiles touched, in depth order        (u64 offsets, K on the device)
+//   K2  list entries per primitive in depth order (gathered) and their exclusive scan
+//       (u64 offsets, K on the device), one launch
 //   K3  keygen: load-balanced expansion, one thread per output entry
 //   K4  stable LSD radix passes (<= 8-bit digits): per-chunk histogram, scan, stable scatter
 //   K5  per-tile [start, end) from the sorted tile ids
@@ -529,17 +530,6 @@ __global__ void __launch_bounds__(kScThreads) k_os_scatter(const uint32_t* __res
   }
 }
 
-// ---------------------------------------------------------------- K2 input
-// touched[j] for j < count: the tile count of the j-th primitive in depth order (count = the
-// device count n_dev when given, else len)
-__global__ void k_gather_touched(const uint32_t* __restrict__ sorted_vals, const uint32_t* __restrict__ tprim,
-                                 int64_t len, const unsigned long long* __restrict__ n_dev,
-                                 uint32_t* __restrict__ touched) {
-  const int64_t n = n_dev ? (int64_t)min((unsigned long long)len, *n_dev) : len;
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
-    touched[j] = tprim[sorted_vals[j]];
-}
-
 // ---------------------------------------------------------------- K3 keygen
 // Primitive j (depth order) owns entries [offsets[j], offsets[j] + touched[j]): per tile row of
 // its bounding box, one entry per segment that the row's span meets, keyed seg_key(segment,
@@ -756,12 +746,15 @@ __device__ __forceinline__ void st_volatile_u64(unsigned long long* p, unsigned 
 }
 
 // status: [0] the chunk counter (low 32 bits), [1 + c] chunk c's word; all zero at launch.  in may
-// equal out: a CTA writes its chunk only after reading it.
-template <typename TOut>
-__global__ void __launch_bounds__(kThreads) k_scan_onepass(const uint32_t* in, TOut* out, int64_t cap,
-                                                           const unsigned long long* __restrict__ n_dev,
-                                                           unsigned long long* __restrict__ status,
-                                                           TOut* __restrict__ total, uint32_t* __restrict__ flags) {
+// equal out: a CTA writes its chunk only after reading it.  With idx (GATHER), element j is
+// in[idx[j]] and is also written to gathered[j].  Three CTAs per SM hold every chunk of the
+// depth-ordered entry counts of 1.5M primitives (367) at once.
+template <typename TOut, bool GATHER>
+__global__ void __launch_bounds__(kThreads, 3) k_scan_onepass(const uint32_t* in, const uint32_t* __restrict__ idx,
+                                                              uint32_t* __restrict__ gathered, TOut* out, int64_t cap,
+                                                              const unsigned long long* __restrict__ n_dev,
+                                                              unsigned long long* __restrict__ status,
+                                                              TOut* __restrict__ total, uint32_t* __restrict__ flags) {
   const int64_t n = scan_count(cap, n_dev);
   const int64_t nchunks = (n + kChunk - 1) / kChunk;
   __shared__ unsigned long long ws[kThreads / 32 + 1];
@@ -777,11 +770,38 @@ __global__ void __launch_bounds__(kThreads) k_scan_onepass(const uint32_t* in, T
   const int64_t base = c * kChunk + (int64_t)threadIdx.x * kItems;
   uint32_t v[kItems];
   unsigned long long acc = 0;
+  // 16-byte loads of the thread's 16 consecutive elements (or ids) where they are all in range
+  const uint32_t* src = GATHER ? idx : in;
+  const bool full = base + kItems <= n && (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
+  if (full) {
+    const uint4* p = reinterpret_cast<const uint4*>(src + base);
 #pragma unroll
-  for (int k = 0; k < kItems; ++k) {
-    v[k] = (base + k < n) ? in[base + k] : 0u;
-    acc += v[k];
+    for (int q = 0; q < kItems / 4; ++q) {
+      const uint4 x = p[q];
+      v[4 * q] = x.x;
+      v[4 * q + 1] = x.y;
+      v[4 * q + 2] = x.z;
+      v[4 * q + 3] = x.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) v[k] = (base + k < n) ? src[base + k] : 0u;
   }
+  if (GATHER) {
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) v[k] = (base + k < n) ? in[v[k]] : 0u;
+    if (full && (reinterpret_cast<uintptr_t>(gathered) & 15u) == 0) {
+      uint4* p = reinterpret_cast<uint4*>(gathered + base);
+#pragma unroll
+      for (int q = 0; q < kItems / 4; ++q) p[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < kItems; ++k)
+        if (base + k < n) gathered[base + k] = v[k];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kItems; ++k) acc += v[k];
   const unsigned long long inc = warp_inclusive_scan(acc);
   const int w = threadIdx.x >> 5;
   const unsigned lane = threadIdx.x & 31u;
@@ -843,9 +863,10 @@ __global__ void __launch_bounds__(kThreads) k_scan_onepass(const uint32_t* in, T
   }
 }
 
-template <typename TOut>
-static void scan_onepass_launch(const uint32_t* in, TOut* out, int64_t n, TOut* total, ScanScratch& sc,
-                                uint32_t* flags, cudaStream_t s, const unsigned long long* n_dev) {
+template <typename TOut, bool GATHER>
+static void scan_onepass_launch(const uint32_t* in, const uint32_t* idx, uint32_t* gathered, TOut* out, int64_t n,
+                                TOut* total, ScanScratch& sc, uint32_t* flags, cudaStream_t s,
+                                const unsigned long long* n_dev) {
   if (n <= 0) {
     if (total) cudaMemsetAsync(total, 0, sizeof(TOut), s);
     return;
@@ -854,18 +875,25 @@ static void scan_onepass_launch(const uint32_t* in, TOut* out, int64_t n, TOut* 
   unsigned long long* status =
       reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(sc.buf) + ScanScratch::kReserved);
   cudaMemsetAsync(status, 0, (size_t)(nchunks + 1) * sizeof(unsigned long long), s);
-  k_scan_onepass<TOut><<<(unsigned)nchunks, kThreads, 0, s>>>(in, out, n, n_dev, status, total, flags);
+  k_scan_onepass<TOut, GATHER><<<(unsigned)nchunks, kThreads, 0, s>>>(in, idx, gathered, out, n, n_dev, status, total,
+                                                                     flags);
   count_launches(1);
 }
 
 void scan_exclusive_onepass(const uint32_t* in, unsigned long long* out, int64_t n, unsigned long long* total,
                             ScanScratch& sc, uint32_t* flags, cudaStream_t s, const unsigned long long* n_dev) {
-  scan_onepass_launch<unsigned long long>(in, out, n, total, sc, flags, s, n_dev);
+  scan_onepass_launch<unsigned long long, false>(in, nullptr, nullptr, out, n, total, sc, flags, s, n_dev);
 }
 
 void scan_exclusive_onepass(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total, ScanScratch& sc,
                             uint32_t* flags, cudaStream_t s, const unsigned long long* n_dev) {
-  scan_onepass_launch<uint32_t>(in, out, n, total, sc, flags, s, n_dev);
+  scan_onepass_launch<uint32_t, false>(in, nullptr, nullptr, out, n, total, sc, flags, s, n_dev);
+}
+
+void scan_gather_onepass(const uint32_t* counts, const uint32_t* ids, uint32_t* gathered, unsigned long long* out,
+                         int64_t n, unsigned long long* total, ScanScratch& sc, uint32_t* flags, cudaStream_t s,
+                         const unsigned long long* n_dev) {
+  scan_onepass_launch<unsigned long long, true>(counts, ids, gathered, out, n, total, sc, flags, s, n_dev);
 }
 
 template void scan_exclusive<uint32_t, uint32_t>(const uint32_t*, uint32_t*, int64_t, uint32_t*, ScanScratch&, cudaStream_t,
@@ -873,13 +901,6 @@ template void scan_exclusive<uint32_t, uint32_t>(const uint32_t*, uint32_t*, int
 template void scan_exclusive<uint32_t, unsigned long long>(const uint32_t*, unsigned long long*, int64_t,
                                                            unsigned long long*, ScanScratch&, cudaStream_t,
                                                            const unsigned long long*);
-
-void launch_gather_touched(const uint32_t* sorted_vals, const uint32_t* tprim, int64_t n, uint32_t* touched,
-                           cudaStream_t s, const unsigned long long* n_dev) {
-  if (n <= 0) return;
-  k_gather_touched<<<grid_cap(cdiv(n, 256), 8), 256, 0, s>>>(sorted_vals, tprim, n, n_dev, touched);
-  count_launches(1);
-}
 
 // scratch entries (uint32) of a sort of n_cap keys: the one-sweep layout (counters, digit counts,
 // two status regions of 256 per chunk), which also holds the per-pass histogram of the classic

@@ -26,7 +26,7 @@ def test_trace_records_each_stage_once_per_pass():
         ges.ges_trace_enable(ctx.handle, False)
         names = list(got)
         # the single-pass list sort of this view's segment ids also writes the segment ranges
-        assert names == ["k_preprocess", "depth_sort", "gather_touched", "scan_touched", "k_keygen", "list_sort",
+        assert names == ["k_preprocess", "depth_sort", "scan_touched", "k_keygen", "list_sort",
                          "k_render_fwd", "tile_order", "k_render_bwd", "k_preprocess_bwd"]
         assert all(n == 2 for n, _ in got.values())
         assert all(ms > 0.0 for _, ms in got.values())
