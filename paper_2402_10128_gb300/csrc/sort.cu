@@ -8,7 +8,7 @@
 // stable radix sort of the duplicates on the tile id alone (ceil(log2 tiles) bits).
 //   K2  list entries per primitive in depth order (gathered) and their exclusive scan
 //       (u64 offsets, K on the device), one launch
-//   K3  keygen: load-balanced expansion, one thread per output entry
+//   K3  keygen: load-balanced walk of (primitive, row) slots, one lane per slot
 //   K4  stable LSD radix passes (<= 8-bit digits): per-chunk histogram, scan, stable scatter
 //   K5  per-tile [start, end) from the sorted tile ids
 #include <atomic>
@@ -535,8 +535,8 @@ __global__ void __launch_bounds__(kScThreads) k_os_scatter(const uint32_t* __res
 // its bounding box, one entry per segment that the row's span meets, keyed seg_key(segment,
 // span columns inside the segment).  A warp takes 32 consecutive primitives, whose entries are
 // one contiguous range: it walks their (primitive, row) slots 32 at a time (one row span per
-// lane), prefix-sums the entry counts, and writes with consecutive lanes on consecutive entries.
-// Writes stay below K whatever the inputs.
+// lane), prefix-sums the slots' entry counts, and each lane writes its slot's entries (at most the
+// segments of one tile row) at its offset.  Writes stay below K whatever the inputs.
 constexpr int kKeygenThreads = 256;
 
 template <class VS>
@@ -584,12 +584,24 @@ __global__ void __launch_bounds__(kKeygenThreads, 4) k_keygen(const __grid_const
     for (unsigned cb = 0; cb < R; cb += 32) {
       const unsigned s = cb + lane;
       const int ow = warp_last_le(hex, s);
-      const RowSpan q = shfl_row_span(rs, ow);
+      RowSpan q;
+      q.u = __shfl_sync(0xffffffffu, rs.u, ow);
+      q.v = __shfl_sync(0xffffffffu, rs.v, ow);
+      q.ql = __shfl_sync(0xffffffffu, rs.ql, ow);
+      q.mabs = P.margin_abs;  // the same for every primitive
+      q.Y = __shfl_sync(0xffffffffu, rs.Y, ow);
+      q.sl = __shfl_sync(0xffffffffu, rs.sl, ow);
+      q.g = __shfl_sync(0xffffffffu, rs.g, ow);
+      q.ic = __shfl_sync(0xffffffffu, rs.ic, ow);
+      q.dys = __shfl_sync(0xffffffffu, rs.dys, ow);
+      q.r0 = __shfl_sync(0xffffffffu, rs.r0, ow);
+      q.r1 = __shfl_sync(0xffffffffu, rs.r1, ow);
       const unsigned qy0 = __shfl_sync(0xffffffffu, y0, ow);
       const unsigned qhex = __shfl_sync(0xffffffffu, hex, ow);
       const unsigned qg = __shfl_sync(0xffffffffu, g, ow);
-      const unsigned qsb = __shfl_sync(0xffffffffu, sb, ow);
-      const unsigned qsx = __shfl_sync(0xffffffffu, sx, ow);
+      // one view: its segment base and row width are the same for every lane
+      const unsigned qsb = VS::kMax == 1 ? (unsigned)vt.v[0].seg_base : __shfl_sync(0xffffffffu, sb, ow);
+      const unsigned qsx = VS::kMax == 1 ? (unsigned)vt.v[0].segs_x : __shfl_sync(0xffffffffu, sx, ow);
       unsigned w = 0, kb = 0, tt = 0;
       if (s < R) {
         const int ty = (int)(qy0 + (s - qhex));
@@ -602,24 +614,17 @@ __global__ void __launch_bounds__(kKeygenThreads, 4) k_keygen(const __grid_const
       }
       unsigned W;
       const unsigned wex = warp_excl_scan(w, W);
-      for (unsigned x0 = 0; x0 < W; x0 += 32) {
-        const unsigned x = x0 + lane;
-        const int rl = warp_last_le(wex, x);
-        const unsigned rkb = __shfl_sync(0xffffffffu, kb, rl);
-        const unsigned rwex = __shfl_sync(0xffffffffu, wex, rl);
-        const unsigned rg = __shfl_sync(0xffffffffu, qg, rl);
-        const unsigned rtt = __shfl_sync(0xffffffffu, tt, rl);
-        const unsigned long long e = eb + x;
-        if (x < W && e < K) {
-          const unsigned i = x - rwex;                     // segment of the span, counted from its first
-          const unsigned t0 = rtt & 0xffffu, t1 = rtt >> 16;
-          const unsigned lo = ((t0 >> L) + i) << L;        // first tile of that segment
-          const unsigned off0 = (t0 > lo ? t0 : lo) - lo;
-          const unsigned hi = lo + (1u << L) - 1u;
-          const unsigned off1 = (t1 < hi ? t1 : hi) - lo;
-          tile_keys[e] = seg_key(rkb + i, off0, off1, P);
-          tile_vals[e] = rg;
-        }
+      // the lane writes its span's w entries itself (w is at most the segments of a tile row)
+      const unsigned t0 = tt & 0xffffu, t1 = tt >> 16;
+      unsigned long long e = eb + wex;
+      for (unsigned i = 0; i < w; ++i, ++e) {
+        if (e >= K) break;
+        const unsigned lo = ((t0 >> L) + i) << L;          // first tile of the span's i-th segment
+        const unsigned off0 = (t0 > lo ? t0 : lo) - lo;
+        const unsigned hi = lo + (1u << L) - 1u;
+        const unsigned off1 = (t1 < hi ? t1 : hi) - lo;
+        tile_keys[e] = seg_key(kb + i, off0, off1, P);
+        tile_vals[e] = qg;
       }
       eb += W;
     }
@@ -767,41 +772,34 @@ __global__ void __launch_bounds__(kThreads, 3) k_scan_onepass(const uint32_t* in
     if (c == 0 && total && threadIdx.x == 0) *total = TOut(0);  // nothing to scan
     return;
   }
-  const int64_t base = c * kChunk + (int64_t)threadIdx.x * kItems;
+  // coalesced loads (element i of the chunk by thread i mod 256), transposed through shared memory
+  // (one padding word per 16) so that each thread then holds 16 consecutive elements
+  __shared__ TOut sbuf[kChunk + kChunk / 16];
+  const int64_t cb = c * kChunk;
+  const int cnt = (int)min((int64_t)kChunk, n - cb);
+#pragma unroll
+  for (int k = 0; k < kItems; ++k) {
+    const int i = k * kThreads + (int)threadIdx.x;
+    uint32_t x = 0u;
+    if (i < cnt) {
+      if (GATHER) {
+        x = in[idx[cb + i]];
+        gathered[cb + i] = x;
+      } else {
+        x = in[cb + i];
+      }
+    }
+    sbuf[i + (i >> 4)] = (TOut)x;
+  }
+  __syncthreads();
   uint32_t v[kItems];
   unsigned long long acc = 0;
-  // 16-byte loads of the thread's 16 consecutive elements (or ids) where they are all in range
-  const uint32_t* src = GATHER ? idx : in;
-  const bool full = base + kItems <= n && (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
-  if (full) {
-    const uint4* p = reinterpret_cast<const uint4*>(src + base);
 #pragma unroll
-    for (int q = 0; q < kItems / 4; ++q) {
-      const uint4 x = p[q];
-      v[4 * q] = x.x;
-      v[4 * q + 1] = x.y;
-      v[4 * q + 2] = x.z;
-      v[4 * q + 3] = x.w;
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < kItems; ++k) v[k] = (base + k < n) ? src[base + k] : 0u;
+  for (int k = 0; k < kItems; ++k) {
+    const int i = (int)threadIdx.x * kItems + k;
+    v[k] = (uint32_t)sbuf[i + (i >> 4)];
+    acc += v[k];
   }
-  if (GATHER) {
-#pragma unroll
-    for (int k = 0; k < kItems; ++k) v[k] = (base + k < n) ? in[v[k]] : 0u;
-    if (full && (reinterpret_cast<uintptr_t>(gathered) & 15u) == 0) {
-      uint4* p = reinterpret_cast<uint4*>(gathered + base);
-#pragma unroll
-      for (int q = 0; q < kItems / 4; ++q) p[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-    } else {
-#pragma unroll
-      for (int k = 0; k < kItems; ++k)
-        if (base + k < n) gathered[base + k] = v[k];
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < kItems; ++k) acc += v[k];
   const unsigned long long inc = warp_inclusive_scan(acc);
   const int w = threadIdx.x >> 5;
   const unsigned lane = threadIdx.x & 31u;
@@ -854,12 +852,19 @@ __global__ void __launch_bounds__(kThreads, 3) k_scan_onepass(const uint32_t* in
       if (c == nchunks - 1 && total) *total = (TOut)(prefix + agg);
     }
   }
-  __syncthreads();
+  __syncthreads();  // every thread's reads of sbuf happened before the block scan's barrier
   unsigned long long run = inc - acc + ws[w] + s_prefix;
 #pragma unroll
   for (int k = 0; k < kItems; ++k) {
-    if (base + k < n) out[base + k] = (TOut)run;
+    const int i = (int)threadIdx.x * kItems + k;
+    sbuf[i + (i >> 4)] = (TOut)run;
     run += v[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kItems; ++k) {
+    const int i = k * kThreads + (int)threadIdx.x;
+    if (i < cnt) out[cb + i] = sbuf[i + (i >> 4)];
   }
 }
 
