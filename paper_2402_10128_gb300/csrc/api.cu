@@ -89,6 +89,7 @@ Params to_params(const ges_params& p) {
   P.seg_log2 = l;
   P.seg_bits = 0;  // set once the segment count is known
   P.phi_mode = p.phi_mode;
+  P.id_bits = 0;  // set once the primitive and segment counts are known
   return P;
 }
 
@@ -162,6 +163,13 @@ ges_status set_segment_bits(Params& P, int64_t total_segs) {
     return fail(GES_ERR_INVALID_ARG, "%lld segments of %d tiles do not fit a 32-bit list key; use fewer tiles per segment",
                 (long long)total_segs, 1 << P.seg_log2);
   return GES_OK;
+}
+
+// The depth sort's 32-bit value carries a primitive's list entries above its id when both fit: ids
+// below n and entries at most the view's segment count (one entry per segment at most).
+void set_pack_bits(Params& P, int64_t n, int64_t segs_per_view) {
+  const int ib = bits_for(n > 1 ? n : 2);
+  P.id_bits = ib + bits_for(segs_per_view + 1) <= 32 ? ib : 0;
 }
 
 // ---------------------------------------------------------------- frame buffers
@@ -514,6 +522,7 @@ ges_status ges_preprocess(ges_frame* f, const ges_scene* scene, const ges_camera
   f->n_segs = (int64_t)f->vt.t.v[0].segs_x * f->tiles_y;
   f->vt.t.total_segs = f->n_segs;
   if ((st = set_segment_bits(f->P, f->n_segs)) != GES_OK) return st;
+  set_pack_bits(f->P, scene->n, f->n_segs);
   f->n = scene->n;
   f->sh_degree = scene->sh_degree;
   {
@@ -548,7 +557,10 @@ ges_status ges_bin_sort(ges_frame* f, void* stream) {
   // list entries per primitive in depth order and their exclusive scan -> offsets, K
   {
     TraceScope tr(f->ctx, "scan_touched", s);
-    scan_gather_onepass(f->tprim, f->sorted_prims, f->touched, f->offsets, f->n, f->d_K, f->scan, f->d_flags, s);
+    if (f->P.id_bits)
+      scan_unpack_onepass(f->sorted_prims, f->P.id_bits, f->offsets, f->n, f->d_K, f->scan, f->d_flags, s);
+    else
+      scan_gather_onepass(f->tprim, f->sorted_prims, f->touched, f->offsets, f->n, f->d_K, f->scan, f->d_flags, s);
   }
   if (f->auto_cap) {
     if ((e = cudaMemcpyAsync(f->h_K, f->d_K, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(e, "read K");

@@ -94,6 +94,7 @@ ges_status check_scene(const ges_scene* s);
 void fill_view(ViewDesc& v, const ges_camera& c, const ges_scene& s, int64_t prim_base, int32_t tile_base,
                int32_t seg_base, int seg_log2);
 ges_status set_segment_bits(Params& P, int64_t total_segs);
+void set_pack_bits(Params& P, int64_t n, int64_t segs_per_view);
 int bits_for(int64_t count);
 // grow-only device scratch of the context, one buffer per slot; replacing a buffer synchronises the device
 ges_status ctx_scratch(ges_ctx* ctx, int slot, size_t bytes, void** out);

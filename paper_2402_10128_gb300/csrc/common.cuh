@@ -105,6 +105,7 @@ struct Params {
   int32_t seg_log2;            // log2 of the tiles per segment
   int32_t seg_bits;            // bits of a global segment id (the radix sort's key width)
   int32_t phi_mode;            // 0 phi_bar_rho, 1 phi_n on the scale vector, 2 phi_n on the variance
+  int32_t id_bits;             // > 0: the depth sort's values are id | list entries << id_bits
 };
 
 // A list entry's key: the global segment id in the low seg_bits bits, then the first and last

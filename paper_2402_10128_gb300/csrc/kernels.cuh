@@ -43,6 +43,11 @@ void scan_exclusive_onepass(const uint32_t* in, unsigned long long* out, int64_t
 void scan_exclusive_onepass(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total, ScanScratch& sc,
                             uint32_t* flags, cudaStream_t s, const unsigned long long* n_dev = nullptr);
 
+// the same over packed[j] >> shift (the list entries that the depth sort's values carry above the
+// primitive id)
+void scan_unpack_onepass(const uint32_t* packed, int shift, unsigned long long* out, int64_t n,
+                         unsigned long long* total, ScanScratch& sc, uint32_t* flags, cudaStream_t s,
+                         const unsigned long long* n_dev = nullptr);
 // the same over counts[ids[j]]: gathered[j] = counts[ids[j]] and out[j] = the sum of gathered[0..j)
 // for j < count (min(*n_dev, n) with n_dev, else n); *total gets the sum.  The list entries of the
 // primitives in depth order and their offsets, in one launch.
@@ -67,8 +72,9 @@ bool radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_
                       bool* ranges_done = nullptr);
 int64_t radix_hist_entries(int64_t n_cap, int max_bits);
 
-// n: primitives (the capacity when n_dev gives the count on the device); touched: tiles per
-// primitive in depth order (the scan's input)
+// n: primitives (the capacity when n_dev gives the count on the device); touched: list entries per
+// primitive in depth order (the scan's input), not read when P.id_bits > 0 (sorted_vals then
+// carries them above the id)
 template <class VS>
 void launch_keygen(const VS& vs, const unsigned long long* offsets, const uint32_t* touched,
                    const unsigned long long* K_dev, int64_t n, const uint32_t* sorted_vals, const KeyShape* ks,

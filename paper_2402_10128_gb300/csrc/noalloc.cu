@@ -149,6 +149,7 @@ extern "C" ges_status ges_render_fwd_noalloc(const ges_scene* scene, const ges_c
   const int64_t segs = (int64_t)vt.t.v[0].segs_x * vt.t.v[0].tiles_y;
   vt.t.total_segs = segs;
   if ((st = set_segment_bits(P, segs)) != GES_OK) return st;
+  set_pack_bits(P, n, segs);
   uint32_t* dk[2] = {at<uint32_t>(b, kL.dk0), at<uint32_t>(b, kL.dk1)};
   uint32_t* pv[2] = {at<uint32_t>(b, kL.pv0), at<uint32_t>(b, kL.pv1)};
   uint32_t* tk[2] = {at<uint32_t>(b, kL.tk0), at<uint32_t>(b, kL.tk1)};
@@ -176,7 +177,10 @@ extern "C" ges_status ges_render_fwd_noalloc(const ges_scene* scene, const ges_c
   int cur = 0;
   if (!radix_sort_pairs(dk, pv, cur, n, nullptr, n, 32, hist, kNaHistEntries, scan, s, flags))
     return fail(GES_ERR_CUDA, "internal: depth-sort histogram exceeds its buffer");
-  scan_gather_onepass(tprim, pv[cur], touched, offsets, n, dK, scan, flags, s);
+  if (P.id_bits)
+    scan_unpack_onepass(pv[cur], P.id_bits, offsets, n, dK, scan, flags, s);
+  else
+    scan_gather_onepass(tprim, pv[cur], touched, offsets, n, dK, scan, flags, s);
   launch_keygen<FrameViews>(vt, offsets, touched, dK, n, pv[cur], ks, P, kNaMaxKeys,
                             tk[0], tv[0], flags, s);
   int tcur = 0;

@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ VS v
     const uint32_t dkey = touched ? __float_as_uint(tz) : kCulledKey;
     depth_key[g] = dkey;
     sort_keys[g] = dkey;
-    sort_vals[g] = (uint32_t)g;
+    sort_vals[g] = P.id_bits ? ((uint32_t)g | (nentries << P.id_bits)) : (uint32_t)g;
     rect[g] = touched ? box : make_ushort4(0, 0, 0, 0);
     tprim[g] = nentries;
     if (!touched) continue;

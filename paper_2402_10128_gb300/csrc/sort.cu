@@ -562,11 +562,21 @@ __global__ void __launch_bounds__(kKeygenThreads, 4) k_keygen(const __grid_const
   const int64_t stride = (int64_t)gridDim.x * wpb * 32;
   for (int64_t base = ((int64_t)blockIdx.x * wpb + (threadIdx.x >> 5)) * 32; base < n; base += stride) {
     const int64_t j = base + lane;
-    const uint32_t t = j < n ? touched[j] : 0u;
+    uint32_t t = 0;
+    unsigned g = 0;
+    if (j < n) {
+      if (P.id_bits) {  // the sorted value carries the entry count above the id
+        const uint32_t pv = sorted_vals[j];
+        t = pv >> P.id_bits;
+        g = pv & ((1u << P.id_bits) - 1u);
+      } else {
+        t = touched[j];
+        if (t) g = sorted_vals[j];
+      }
+    }
     RowSpan rs{};
-    unsigned g = 0, h = 0, y0 = 0, sb = 0, sx = 0;
+    unsigned h = 0, y0 = 0, sb = 0, sx = 0;
     if (t) {
-      g = sorted_vals[j];
       const KeyShape k = ks[g];  // one 32-byte sector
       const ushort4 r = k.box;
       rs = make_row_span(k.ext, k.mean.x, k.mean.y, P.margin_abs, r);
@@ -752,11 +762,12 @@ __device__ __forceinline__ void st_volatile_u64(unsigned long long* p, unsigned 
 
 // status: [0] the chunk counter (low 32 bits), [1 + c] chunk c's word; all zero at launch.  in may
 // equal out: a CTA writes its chunk only after reading it.  With idx (GATHER), element j is
-// in[idx[j]] and is also written to gathered[j].  Three CTAs per SM hold every chunk of the
+// in[idx[j]] and is also written to gathered[j]; otherwise it is in[j] >> shift.  Three CTAs per SM hold every chunk of the
 // depth-ordered entry counts of 1.5M primitives (367) at once.
 template <typename TOut, bool GATHER>
 __global__ void __launch_bounds__(kThreads, 3) k_scan_onepass(const uint32_t* in, const uint32_t* __restrict__ idx,
-                                                              uint32_t* __restrict__ gathered, TOut* out, int64_t cap,
+                                                              uint32_t* __restrict__ gathered, int shift, TOut* out,
+                                                              int64_t cap,
                                                               const unsigned long long* __restrict__ n_dev,
                                                               unsigned long long* __restrict__ status,
                                                               TOut* __restrict__ total, uint32_t* __restrict__ flags) {
@@ -786,7 +797,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_scan_onepass(const uint32_t* in
         x = in[idx[cb + i]];
         gathered[cb + i] = x;
       } else {
-        x = in[cb + i];
+        x = in[cb + i] >> shift;
       }
     }
     sbuf[i + (i >> 4)] = (TOut)x;
@@ -869,8 +880,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_scan_onepass(const uint32_t* in
 }
 
 template <typename TOut, bool GATHER>
-static void scan_onepass_launch(const uint32_t* in, const uint32_t* idx, uint32_t* gathered, TOut* out, int64_t n,
-                                TOut* total, ScanScratch& sc, uint32_t* flags, cudaStream_t s,
+static void scan_onepass_launch(const uint32_t* in, const uint32_t* idx, uint32_t* gathered, int shift, TOut* out,
+                                int64_t n, TOut* total, ScanScratch& sc, uint32_t* flags, cudaStream_t s,
                                 const unsigned long long* n_dev) {
   if (n <= 0) {
     if (total) cudaMemsetAsync(total, 0, sizeof(TOut), s);
@@ -880,25 +891,31 @@ static void scan_onepass_launch(const uint32_t* in, const uint32_t* idx, uint32_
   unsigned long long* status =
       reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(sc.buf) + ScanScratch::kReserved);
   cudaMemsetAsync(status, 0, (size_t)(nchunks + 1) * sizeof(unsigned long long), s);
-  k_scan_onepass<TOut, GATHER><<<(unsigned)nchunks, kThreads, 0, s>>>(in, idx, gathered, out, n, n_dev, status, total,
-                                                                     flags);
+  k_scan_onepass<TOut, GATHER><<<(unsigned)nchunks, kThreads, 0, s>>>(in, idx, gathered, shift, out, n, n_dev, status,
+                                                                     total, flags);
   count_launches(1);
 }
 
 void scan_exclusive_onepass(const uint32_t* in, unsigned long long* out, int64_t n, unsigned long long* total,
                             ScanScratch& sc, uint32_t* flags, cudaStream_t s, const unsigned long long* n_dev) {
-  scan_onepass_launch<unsigned long long, false>(in, nullptr, nullptr, out, n, total, sc, flags, s, n_dev);
+  scan_onepass_launch<unsigned long long, false>(in, nullptr, nullptr, 0, out, n, total, sc, flags, s, n_dev);
 }
 
 void scan_exclusive_onepass(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total, ScanScratch& sc,
                             uint32_t* flags, cudaStream_t s, const unsigned long long* n_dev) {
-  scan_onepass_launch<uint32_t, false>(in, nullptr, nullptr, out, n, total, sc, flags, s, n_dev);
+  scan_onepass_launch<uint32_t, false>(in, nullptr, nullptr, 0, out, n, total, sc, flags, s, n_dev);
 }
 
 void scan_gather_onepass(const uint32_t* counts, const uint32_t* ids, uint32_t* gathered, unsigned long long* out,
                          int64_t n, unsigned long long* total, ScanScratch& sc, uint32_t* flags, cudaStream_t s,
                          const unsigned long long* n_dev) {
-  scan_onepass_launch<unsigned long long, true>(counts, ids, gathered, out, n, total, sc, flags, s, n_dev);
+  scan_onepass_launch<unsigned long long, true>(counts, ids, gathered, 0, out, n, total, sc, flags, s, n_dev);
+}
+
+void scan_unpack_onepass(const uint32_t* packed, int shift, unsigned long long* out, int64_t n,
+                         unsigned long long* total, ScanScratch& sc, uint32_t* flags, cudaStream_t s,
+                         const unsigned long long* n_dev) {
+  scan_onepass_launch<unsigned long long, false>(packed, nullptr, nullptr, shift, out, n, total, sc, flags, s, n_dev);
 }
 
 template void scan_exclusive<uint32_t, uint32_t>(const uint32_t*, uint32_t*, int64_t, uint32_t*, ScanScratch&, cudaStream_t,
@@ -928,7 +945,8 @@ bool radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_
   if (passes >= 3 && n_cap < (int64_t)kOsValue && hist_cap >= kOsHeader + 2 * 256 * nchunks) {
     // zero the counters, the digit counts and the first status region
     cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)(kOsHeader + 256 * nchunks), s);
-    k_os_counts<<<grid_cap(cdiv(n_cap, kThreads * 4), 8), kThreads, 0, s>>>(keys[cur], n_host, n_dev, n_cap, passes,
+    // two count CTAs per SM: each flushes its four 256-bin histograms with global atomics
+    k_os_counts<<<grid_cap(cdiv(n_cap, kThreads * 4), 2), kThreads, 0, s>>>(keys[cur], n_host, n_dev, n_cap, passes,
                                                                            bits_per, total_bits, hist + 8);
     // CTAs take chunks from a counter, so the grid size does not affect the result: two per SM
     // (the register limit of 512 threads at 64 registers); no device query, as serving captures this
