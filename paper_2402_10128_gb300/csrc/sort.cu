@@ -322,6 +322,10 @@ __global__ void __launch_bounds__(kScThreads) k_radix_scatter(const uint32_t* __
 // kFlagSortWait in the caller's flags (its successors then finish with wrong offsets but every
 // store is bounds-checked).
 constexpr int kOsMaxPasses = 4;
+// keys per thread and per chunk of a one-sweep pass: 1.5M keys make 293 chunks, one wave of two
+// CTAs per SM (4,096-key chunks took two rounds and measured 3% slower)
+constexpr int kOsItems = 10;
+constexpr int kOsChunk = kScThreads * kOsItems;
 constexpr int64_t kOsHeader = 8 + kOsMaxPasses * 256;  // chunk counters per pass, digit counts per pass
 constexpr uint32_t kOsAgg = 1u << 30, kOsPre = 2u << 30, kOsValue = (1u << 30) - 1u;
 constexpr int kOsSpinLimit = 1 << 22;
@@ -371,14 +375,14 @@ __global__ void __launch_bounds__(kScThreads) k_os_scatter(const uint32_t* __res
   __shared__ uint32_t dbase[256];
   __shared__ uint32_t bstart[257];
   __shared__ uint32_t wsum[kWarps];
-  __shared__ uint32_t skeys[kChunk];
-  __shared__ uint32_t svals[kChunk];
+  __shared__ uint32_t skeys[kOsChunk];
+  __shared__ uint32_t svals[kOsChunk];
   __shared__ int64_t s_chunk;
   __shared__ int s_fail;
   const int nbins = 1 << bits;
   const uint32_t mask = (uint32_t)nbins - 1u;
   const int64_t n = element_count(n_host, n_dev, cap);
-  const int64_t nchunks = (n + kChunk - 1) / kChunk;
+  const int64_t nchunks = (n + kOsChunk - 1) / kOsChunk;
   const int w = threadIdx.x >> 5;
   const unsigned lane = lane_id();
   uint32_t* counter = os + pass;
@@ -414,20 +418,20 @@ __global__ void __launch_bounds__(kScThreads) k_os_scatter(const uint32_t* __res
     __syncthreads();
     const int64_t c = s_chunk;
     if (c >= nchunks) break;
-    const int64_t base = c * kChunk;
-    const int count = (int)min((int64_t)kChunk, n - base);
+    const int64_t base = c * kOsChunk;
+    const int count = (int)min((int64_t)kOsChunk, n - base);
     const unsigned lt_mask = (1u << lane) - 1u;
-    uint32_t key[kScItems], val[kScItems], rank[kScItems];
+    uint32_t key[kOsItems], val[kOsItems], rank[kOsItems];
 #pragma unroll
-    for (int r = 0; r < kScItems; ++r) {
-      const int li = w * (kScItems * 32) + r * 32 + (int)lane;
+    for (int r = 0; r < kOsItems; ++r) {
+      const int li = w * (kOsItems * 32) + r * 32 + (int)lane;
       const bool ok = li < count;
       key[r] = ok ? keys_in[base + li] : 0u;
       val[r] = ok ? vals_in[base + li] : 0u;
     }
 #pragma unroll
-    for (int r = 0; r < kScItems; ++r) {
-      const int li = w * (kScItems * 32) + r * 32 + (int)lane;
+    for (int r = 0; r < kOsItems; ++r) {
+      const int li = w * (kOsItems * 32) + r * 32 + (int)lane;
       const bool ok = li < count;
       const uint32_t d = (key[r] >> shift) & mask;
       unsigned peers = __ballot_sync(0xffffffffu, ok);
@@ -504,8 +508,8 @@ __global__ void __launch_bounds__(kScThreads) k_os_scatter(const uint32_t* __res
     if ((int)threadIdx.x < nbins) bstart[threadIdx.x] = wsum[w] + inc - total;
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < kScItems; ++r) {
-      const int li = w * (kScItems * 32) + r * 32 + (int)lane;
+    for (int r = 0; r < kOsItems; ++r) {
+      const int li = w * (kOsItems * 32) + r * 32 + (int)lane;
       if (li < count) {
         const int d = (int)((key[r] >> shift) & mask);
         const uint32_t pos = bstart[d] + wcnt[w][d] + rank[r];
@@ -940,22 +944,23 @@ bool radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_
   const int passes = (total_bits + 7) / 8;
   const int bits_per = (total_bits + passes - 1) / passes;
   const int64_t nchunks = cdiv(n_cap, kChunk);
+  const int64_t os_chunks = cdiv(n_cap, kOsChunk);
   // one sweep for sorts of three or four passes (the depth sort); shorter sorts over many chunks (the
   // list sort) measured faster in the classic form, whose passes have no look-back chain
   if (passes >= 3 && n_cap < (int64_t)kOsValue && hist_cap >= kOsHeader + 2 * 256 * nchunks) {
     // zero the counters, the digit counts and the first status region
-    cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)(kOsHeader + 256 * nchunks), s);
+    cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)(kOsHeader + 256 * os_chunks), s);
     // two count CTAs per SM: each flushes its four 256-bin histograms with global atomics
     k_os_counts<<<grid_cap(cdiv(n_cap, kThreads * 4), 2), kThreads, 0, s>>>(keys[cur], n_host, n_dev, n_cap, passes,
                                                                            bits_per, total_bits, hist + 8);
     // CTAs take chunks from a counter, so the grid size does not affect the result: two per SM
     // (the register limit of 512 threads at 64 registers); no device query, as serving captures this
-    const unsigned grid = grid_cap(nchunks, 2);
+    const unsigned grid = grid_cap(os_chunks, 2);
     for (int p = 0; p < passes; ++p) {
       const int shift = p * bits_per;
       const int bits = (total_bits - shift) < bits_per ? (total_bits - shift) : bits_per;
       k_os_scatter<<<grid, kScThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_host, n_dev,
-                                               n_cap, shift, bits, p, p + 1 < passes ? 1 : 0, hist, nchunks, flags);
+                                               n_cap, shift, bits, p, p + 1 < passes ? 1 : 0, hist, os_chunks, flags);
       cur ^= 1;
     }
     count_launches(1 + passes);
