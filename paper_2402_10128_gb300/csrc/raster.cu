@@ -173,6 +173,9 @@ __device__ __forceinline__ void render_tile_fwd(const ViewTable<MAXV>& vt, int64
     const int cnt = stage_kept<kFwdBatch>(st, keep, idx, rg.x, vals,
                                           [&](RecPair& d, uint32_t g) { stage_pair(d, rec[g]); });
     if (!__all_sync(0xffffffffu, done0 && done1)) {
+      // unrolled: the loop overhead and the staged records' address arithmetic are shared over eight
+      // fragments (0.706 -> 0.645 ms at the scene-scale view, 0.585 -> 0.570 ms at the cube view)
+#pragma unroll 8
       for (int j = 0; j < cnt; ++j) {
         if (done0 && done1) break;
         PairEval f;
