@@ -464,7 +464,8 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
       const float q0 = f.q0, q1 = f.q1, hb = e.z;
       const float2 alpha = make_float2(act0 ? al0 : 0.f, act1 ? al1 : 0.f);
       const float2 om = __ffma2_rn(alpha, NEG1, ONE);
-      const float2 inv = make_float2(act0 ? rcp_approx(om.x) : 1.0f, act1 ? rcp_approx(om.y) : 1.0f);
+      // an inactive pixel has alpha = 0, om = 1 and rcp(1) = 1: its T stays as it is
+      const float2 inv = make_float2(rcp_approx(om.x), rcp_approx(om.y));
       T = __fmul2_rn(T, inv);
       const float2 w = __fmul2_rn(alpha, T);
       // D = sum_c dL/dC_c c_c;  dL/dalpha = D T_i - U / (1 - alpha_i);  U += D alpha_i T_i
