@@ -21,7 +21,7 @@ namespace {
 constexpr int kThreads = 128;  // backward, per tile
 constexpr int kBatch = kThreads;
 constexpr int kFwdThreads = 128;
-constexpr int kFwdBatch = kFwdThreads;
+constexpr int kFwdBatch = 2 * kFwdThreads;  // list positions per round: two per thread
 
 __device__ __forceinline__ float rcp_approx(float x) {
   float y;
@@ -131,6 +131,47 @@ __device__ __forceinline__ int stage_kept(Stage<RecT, N>& st, bool keep, uint32_
   return (int)total;
 }
 
+// The same for two candidates per thread (positions idx0 < idx1 of a round of 2 NT): the round's
+// first half is kept in order, then the second.
+template <int NT, class RecT, class StageFn>
+__device__ __forceinline__ int stage_kept2(Stage<RecT, 2 * NT>& st, bool keep0, uint32_t idx0, bool keep1,
+                                           uint32_t idx1, uint32_t list_start, const uint32_t* __restrict__ vals,
+                                           StageFn stage_rec) {
+  const unsigned lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+  const unsigned m0 = __ballot_sync(0xffffffffu, keep0), m1 = __ballot_sync(0xffffffffu, keep1);
+  if (lane == 0) {
+    st.warp_count[w] = (uint32_t)__popc(m0);
+    st.warp_count[NT / 32 + w] = (uint32_t)__popc(m1);
+  }
+  __syncthreads();
+  uint32_t off0 = 0, off1 = 0, t0 = 0, t1 = 0;
+#pragma unroll
+  for (int k = 0; k < NT / 32; ++k) {
+    const uint32_t c0 = st.warp_count[k], c1 = st.warp_count[NT / 32 + k];
+    off0 += k < (int)w ? c0 : 0u;
+    off1 += k < (int)w ? c1 : 0u;
+    t0 += c0;
+    t1 += c1;
+  }
+  const unsigned lt = (1u << lane) - 1u;
+  if (keep0) {
+    const uint32_t at = off0 + (uint32_t)__popc(m0 & lt);
+    const uint32_t g = vals[idx0];
+    stage_rec(st.rec[at], g);
+    st.pos[at] = idx0 - list_start + 1u;
+    st.id[at] = g;
+  }
+  if (keep1) {
+    const uint32_t at = t0 + off1 + (uint32_t)__popc(m1 & lt);
+    const uint32_t g = vals[idx1];
+    stage_rec(st.rec[at], g);
+    st.pos[at] = idx1 - list_start + 1u;
+    st.id[at] = g;
+  }
+  __syncthreads();
+  return (int)(t0 + t1);
+}
+
 struct WarpBlock {
   int x, y;  // first pixel of this thread (the second is at y + 4)
 };
@@ -168,10 +209,11 @@ __device__ __forceinline__ void render_tile_fwd(const ViewTable<MAXV>& vt, int64
   bool done0 = !inside0, done1 = !inside1;
   for (uint32_t base = rg.x; base < rg.y; base += kFwdBatch) {
     if (__syncthreads_count(done0 && done1) == kFwdThreads) break;
-    const uint32_t idx = base + threadIdx.x;
-    const bool keep = idx < rg.y && seg_key_covers(keys[idx], to, P);
-    const int cnt = stage_kept<kFwdBatch>(st, keep, idx, rg.x, vals,
-                                          [&](RecPair& d, uint32_t g) { stage_pair(d, rec[g]); });
+    const uint32_t idx0 = base + threadIdx.x, idx1 = idx0 + kFwdThreads;
+    const bool keep0 = idx0 < rg.y && seg_key_covers(keys[idx0], to, P);
+    const bool keep1 = idx1 < rg.y && seg_key_covers(keys[idx1], to, P);
+    const int cnt = stage_kept2<kFwdThreads>(st, keep0, idx0, keep1, idx1, rg.x, vals,
+                                             [&](RecPair& d, uint32_t g) { stage_pair(d, rec[g]); });
     if (!__all_sync(0xffffffffu, done0 && done1)) {
       // full groups of eight staged fragments with one done-test each (a pixel finished inside a group
       // composites nothing more: c0/c1 stay false), then the rest one by one.  At the scene-scale
