@@ -56,6 +56,23 @@ def test_fullsize_sorted_keys_bitexact(lib, workload):
     assert np.array_equal(got["inspect"]["ranges"][nonempty], ref_ranges[nonempty])
 
 
+def test_gathered_entry_counts_lists_bitexact(lib):
+    """A primitive id and its list entries (at most the view's segments) fit the depth sort's 32-bit
+    value together at the scene-scale view (21 + 9 bits).  Here they do not: 2.2M primitives (22
+    bits) and one segment per tile at 512x512 (1,024 segments, 11 bits), so the scan gathers the
+    counts through the sorted ids instead of unpacking them.  The lists must be the same."""
+    from gpu_helpers import gpu_run
+    sc = scenes.cube_scene(2_200_000, seed=5)
+    cam = scenes.tiny_camera(512, 512)
+    p = {"segment_tiles": 1}
+    got = gpu_run(sc, cam, p)
+    kk, vv = oracle.sorted_keys(sc, cam, p)
+    assert got["K_tiles"] == kk.size and kk.size > 1_000_000
+    assert np.array_equal(got["keys"], kk)
+    assert np.array_equal(got["vals"], vv)
+    got["frame"].close()
+
+
 def test_fullsize_sampled_pixels(lib, workload):
     from gpu_helpers import gpu_run
     name, sc, cam = workload
