@@ -5,9 +5,9 @@
 // primitives instead of the K duplicates: every duplicate of a primitive shares its depth
 // bits, so sorting primitives by depth first and duplicating them in that order gives the
 // same list as sorting the duplicates on the depth digits.  The remaining passes are a
-// stable radix sort of the duplicates on the tile id alone (ceil(log2 tiles) bits).
-//   K2  list entries per primitive in depth order (gathered) and their exclusive scan
-//       (u64 offsets, K on the device), one launch
+// stable radix sort of the duplicates on their segment id alone (ceil(log2 segments) bits).
+//   K2  list entries per primitive in depth order (unpacked from the sorted values, or gathered
+//       through the sorted ids) and their exclusive scan (u64 offsets, K on the device), one launch
 //   K3  keygen: load-balanced walk of (primitive, row) slots, one lane per slot
 //   K4  stable LSD radix passes (<= 8-bit digits): per-chunk histogram, scan, stable scatter
 //   K5  per-tile [start, end) from the sorted tile ids
@@ -535,7 +535,8 @@ __global__ void __launch_bounds__(kScThreads) k_os_scatter(const uint32_t* __res
 }
 
 // ---------------------------------------------------------------- K3 keygen
-// Primitive j (depth order) owns entries [offsets[j], offsets[j] + touched[j]): per tile row of
+// Primitive j (depth order) owns entries [offsets[j], offsets[j] + t_j), t_j its list entries (packed
+// above the id in the sorted value when P.id_bits > 0, else touched[j]): per tile row of
 // its bounding box, one entry per segment that the row's span meets, keyed seg_key(segment,
 // span columns inside the segment).  A warp takes 32 consecutive primitives, whose entries are
 // one contiguous range: it walks their (primitive, row) slots 32 at a time (one row span per
