@@ -159,24 +159,6 @@ __global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restr
   }
 }
 
-// The [start, end) range of every bin in the output of a single-pass sort, from the pass's scanned
-// histogram ([bin][chunk], exclusive over the whole matrix): bin b starts where its first chunk's
-// entries go and ends where bin b + 1's start (the last bin at the element count).
-__global__ void __launch_bounds__(256) k_ranges_from_hist(const uint32_t* __restrict__ hist, int64_t n_host,
-                                                          const unsigned long long* __restrict__ n_dev, int64_t cap,
-                                                          int nbins, int64_t n_ranges, uint2* __restrict__ ranges) {
-  const int64_t n = element_count(n_host, n_dev, cap);
-  const int64_t nchunks = (n + kChunk - 1) / kChunk;
-  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n_ranges; b += (int64_t)gridDim.x * blockDim.x) {
-    uint2 r = make_uint2(0u, 0u);
-    if (nchunks > 0 && b < nbins) {
-      r.x = hist[b * nchunks];
-      r.y = b + 1 < nbins ? hist[(b + 1) * nchunks] : (uint32_t)n;
-    }
-    ranges[b] = r;
-  }
-}
-
 // Stable scatter.  Warp w of the CTA owns chunk elements [w*256, (w+1)*256) and walks them in
 // order, 32 at a time.  Lanes with equal digits (found with one ballot per digit bit) are ranked
 // by lane order; the group's first lane adds the group size to the warp's running count of that
@@ -203,7 +185,8 @@ __global__ void __launch_bounds__(kScThreads) k_radix_scatter(const uint32_t* __
                                                             uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
                                                             int64_t n_host, const unsigned long long* __restrict__ n_dev,
                                                             int64_t cap, int shift, int bits,
-                                                            const uint32_t* __restrict__ hist_scanned) {
+                                                            const uint32_t* __restrict__ hist_scanned,
+                                                            uint2* __restrict__ ranges, int64_t n_ranges) {
   constexpr int kWarps = kScThreads / 32;
   extern __shared__ __align__(16) unsigned char sc_smem[];
   ScatterSmem<NB>& sm = *reinterpret_cast<ScatterSmem<NB>*>(sc_smem);
@@ -219,6 +202,19 @@ __global__ void __launch_bounds__(kScThreads) k_radix_scatter(const uint32_t* __
   const int64_t nchunks = (n + kChunk - 1) / kChunk;
   const int w = threadIdx.x >> 5;
   const unsigned lane = lane_id();
+  // a single pass over all the key bits: the [start, end) range of every bin in the output comes
+  // from the scanned histogram ([bin][chunk], exclusive over the whole matrix): bin b starts where
+  // its first chunk's entries go and ends where bin b + 1's start (the last bin at the count)
+  if (ranges) {
+    for (int64_t b = (int64_t)blockIdx.x * kScThreads + threadIdx.x; b < n_ranges; b += (int64_t)gridDim.x * kScThreads) {
+      uint2 r = make_uint2(0u, 0u);
+      if (nchunks > 0 && b < nbins) {
+        r.x = hist_scanned[b * nchunks];
+        r.y = b + 1 < nbins ? hist_scanned[(b + 1) * nchunks] : (uint32_t)n;
+      }
+      ranges[b] = r;
+    }
+  }
   for (int64_t c = blockIdx.x; c * kChunk < n; c += gridDim.x) {
   const int64_t base = c * kChunk;
   const int count = (int)min((int64_t)kChunk, n - base);
@@ -994,18 +990,18 @@ bool radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int& cur, int64_t n_
                                                                   n_entries);
     }
     scan_exclusive_onepass(hist, hist, entries, (uint32_t*)nullptr, sc, flags, s, n_entries);
-    if (bin_ranges && passes_c == 1 && bits == total_bits && n_ranges > 0) {
-      k_ranges_from_hist<<<(unsigned)cdiv(n_ranges, 256), 256, 0, s>>>(hist, n_host, n_dev, n_cap, 1 << bits, n_ranges,
-                                                                       bin_ranges);
-      count_launches(1);
-      if (ranges_done) *ranges_done = true;
-    }
+    // a single pass over all the key bits also gives every bin's range (written by the scatter)
+    const bool with_ranges = bin_ranges && passes_c == 1 && bits == total_bits && n_ranges > 0;
+    uint2* rg_out = with_ranges ? bin_ranges : nullptr;
+    if (with_ranges && ranges_done) *ranges_done = true;
     if (wide) {
       k_radix_scatter<512><<<grid_cap(nchunks, 2), kScThreads, sizeof(ScatterSmem<512>), s>>>(
-          keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_host, n_dev, n_cap, shift, bits, hist);
+          keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_host, n_dev, n_cap, shift, bits, hist, rg_out,
+          n_ranges);
     } else {
       k_radix_scatter<256><<<grid_cap(nchunks, 4), kScThreads, sizeof(ScatterSmem<256>), s>>>(
-          keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_host, n_dev, n_cap, shift, bits, hist);
+          keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_host, n_dev, n_cap, shift, bits, hist, rg_out,
+          n_ranges);
     }
     count_launches(2);
     cur ^= 1;
