@@ -30,29 +30,28 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 // A fragment's record as the composite kernels read it: every value the two pixels of a thread
-// share is stored twice, so that one 16-byte shared load gives two ready float2 operands.
+// share is stored twice, so that one 16-byte shared load gives two ready float2 operands.  Five
+// such loads per fragment (the q limit, read only when counting work, comes from the global
+// record); the backward adds the conic's b pair.
 struct RecPair {
   float4 m;    // -mx, -mx, -my, -my
-  float4 e;    // q limit x2, beta/2 x2
   float4 c0;   // conic a x2, 2 conic b x2
   float4 c1;   // conic c x2, kappa x2
   float4 k0;   // r x2, g x2
-  float4 k1;   // b x2, (unused)
+  float4 k1;   // b x2, beta/2 x2
 };
 // the backward's copy adds the conic terms of the mean gradient
 struct RecPairB : RecPair {
-  float4 n0;   // -2 conic a x2, -2 conic b x2
-  float4 n1;   // -2 conic c x2, (unused)
+  float2 nb;   // conic b x2 (the mean gradient's cross term; a and c are in c0 and c1)
 };
 
 __device__ __forceinline__ void stage_pair(RecPair& d, const Rec& r) {
   d.m = make_float4(-r.a.x, -r.a.x, -r.a.y, -r.a.y);
-  d.e = make_float4(r.a.z, r.a.z, r.a.w, r.a.w);
   const float tb = __fmul_rn(2.0f, r.b.y);
   d.c0 = make_float4(r.b.x, r.b.x, tb, tb);
   d.c1 = make_float4(r.b.z, r.b.z, r.b.w, r.b.w);
   d.k0 = make_float4(r.c.x, r.c.x, r.c.y, r.c.y);
-  d.k1 = make_float4(r.c.z, r.c.z, 0.f, 0.f);
+  d.k1 = make_float4(r.c.z, r.c.z, r.a.w, r.a.w);
 }
 
 __device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
@@ -73,7 +72,7 @@ struct PairEval {
   float q0, q1;
 };
 __device__ __forceinline__ void eval_pair(const RecPair& r, float2 PX, float2 PY, PairEval& f) {
-  const float4 m = r.m, e = r.e, c0 = r.c0, c1 = r.c1;
+  const float4 m = r.m, c0 = r.c0, c1 = r.c1, e = r.k1;  // e.z, e.w: beta/2
   f.dx = __fadd2_rn(PX, lo2(m));
   f.dy = __fadd2_rn(PY, hi2(m));
   const float2 t = __ffma2_rn(hi2(c0), f.dy, __fmul2_rn(lo2(c0), f.dx));
@@ -228,7 +227,7 @@ __device__ __forceinline__ void render_tile_fwd(const ViewTable<MAXV>& vt, int64
           PairEval f;
           eval_pair(st.rec[j], PX, PY, f);
           if (STATS) {
-            const float ql = st.rec[j].e.x;
+            const float ql = rec[st.id[j]].a.z;
             n_eval += (done0 ? 0u : 1u) + (done1 ? 0u : 1u);
             n_range += (!done0 && f.q0 <= ql ? 1u : 0u) + (!done1 && f.q1 <= ql ? 1u : 0u);
           }
@@ -261,7 +260,7 @@ __device__ __forceinline__ void render_tile_fwd(const ViewTable<MAXV>& vt, int64
         PairEval f;
         eval_pair(st.rec[j], PX, PY, f);
         if (STATS) {
-          const float ql = st.rec[j].e.x;
+          const float ql = rec[st.id[j]].a.z;
           n_eval += (done0 ? 0u : 1u) + (done1 ? 0u : 1u);
           n_range += (!done0 && f.q0 <= ql ? 1u : 0u) + (!done1 && f.q1 <= ql ? 1u : 0u);
         }
@@ -483,8 +482,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
     const int cnt = stage_kept<kBatch>(st, keep, idx, rg.x, vals, [&](RecPairB& d, uint32_t g) {
       const Rec r = rec[g];
       stage_pair(d, r);
-      d.n0 = make_float4(r.b.x, r.b.x, r.b.y, r.b.y);
-      d.n1 = make_float4(r.b.z, r.b.z, 0.f, 0.f);
+      d.nb = make_float2(r.b.y, r.b.y);
     });
     for (int j = cnt - 1; j >= 0; --j) {
       const uint32_t kpos = st.pos[j];  // 1-based position in the segment's list
@@ -500,8 +498,9 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
       // Constant factors are left out here and applied to the warp's sums (slot_scale): the
       // derivative of G = 2^(-p log2(e)/2) w.r.t. p is taken as G (true: -G/2), the record's conic
       // terms as (a, b, c) (true: -2 (a, b, c)), 2 dx dy as dx dy, and ln q as log2 q.
-      const float4 n0 = st.rec[j].n0, n1 = st.rec[j].n1, k0 = st.rec[j].k0, k1 = st.rec[j].k1;
-      const float4 e = st.rec[j].e, c1 = st.rec[j].c1;
+      const float4 c0 = st.rec[j].c0, k0 = st.rec[j].k0, k1 = st.rec[j].k1;
+      const float2 nb = st.rec[j].nb;
+      const float4 e = st.rec[j].k1, c1 = st.rec[j].c1;  // e.z, e.w: beta/2
       const float2 dx = f.dx, dy = f.dy, p = f.p, lq = f.lq, G = f.G;
       const float q0 = f.q0, q1 = f.q1, hb = e.z;
       const float2 alpha = make_float2(act0 ? al0 : 0.f, act1 ? al1 : 0.f);
@@ -537,8 +536,8 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
         dq = dp;
       }
       const float2 dqdx = __fmul2_rn(dq, dx), dqdy = __fmul2_rn(dq, dy);
-      const float2 gmx = __ffma2_rn(dqdy, hi2(n0), __fmul2_rn(dqdx, lo2(n0)));
-      const float2 gmy = __ffma2_rn(dqdy, lo2(n1), __fmul2_rn(dqdx, hi2(n0)));
+      const float2 gmx = __ffma2_rn(dqdy, nb, __fmul2_rn(dqdx, lo2(c0)));
+      const float2 gmy = __ffma2_rn(dqdy, lo2(c1), __fmul2_rn(dqdx, nb));
       const float2 ga = __fmul2_rn(dqdx, dx);   // x (-1/2)
       const float2 gb = __fmul2_rn(dqdx, dy);   // x (-1)
       const float2 gcc = __fmul2_rn(dqdy, dy);  // x (-1/2)
