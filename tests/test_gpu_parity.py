@@ -33,6 +33,15 @@ def _needles_and_discs(n=300, seed=17):
     return sc
 
 
+def _beta2_mixed(n=400, seed=18):
+    """Half the primitives at beta = 2 exactly (the GEF kernels' exponent-free branch: p = q), the
+    other half spread over [0.5, 8], mixed in depth so that both branches alternate in a tile."""
+    sc = scenes.cube_scene(n, seed=seed, beta_range=(0.5, 8.0), beta_log=True, scale_range=(0.01, 0.07))
+    rng = np.random.default_rng(seed + 1)
+    sc.betas[rng.random(n) < 0.5] = np.float32(2.0)
+    return sc
+
+
 def _cases():
     return {
         "tiny": (*scenes.tiny_workload(), None),
@@ -57,6 +66,7 @@ def _cases():
         "rho0": (scenes.cube_scene(400, seed=16, beta_range=(0.5, 8.0), beta_log=True), scenes.tiny_camera(70, 50),
                  dict(rho=0.0)),
         "needles_and_discs": (_needles_and_discs(), scenes.tiny_camera(96, 80), None),
+        "beta2_mixed": (_beta2_mixed(), scenes.tiny_camera(72, 56), None),
     }
 
 
