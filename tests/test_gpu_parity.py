@@ -35,8 +35,10 @@ def _needles_and_discs(n=300, seed=17):
 
 def _beta2_mixed(n=400, seed=18):
     """Half the primitives at beta = 2 exactly (the GEF kernels' exponent-free branch: p = q), the
-    other half spread over [0.5, 8], mixed in depth so that both branches alternate in a tile."""
-    sc = scenes.cube_scene(n, seed=seed, beta_range=(0.5, 8.0), beta_log=True, scale_range=(0.01, 0.07))
+    other half spread over [0.5, 8], mixed in depth so that both branches alternate in a tile; SH
+    degree 1 (the other degrees have cases of their own)."""
+    sc = scenes.cube_scene(n, seed=seed, sh_degree=1, beta_range=(0.5, 8.0), beta_log=True,
+                           scale_range=(0.01, 0.07))
     rng = np.random.default_rng(seed + 1)
     sc.betas[rng.random(n) < 0.5] = np.float32(2.0)
     return sc
