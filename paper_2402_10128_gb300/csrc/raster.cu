@@ -322,7 +322,9 @@ __device__ __forceinline__ void render_tile_fwd(const ViewTable<MAXV>& vt, int64
 }
 
 template <class VS, bool STATS>
-__global__ void __launch_bounds__(kFwdThreads, 8) k_render_fwd(const __grid_constant__ VS vs, const uint2* __restrict__ ranges,
+// seven CTAs per SM: at 72 registers the forward keeps its values in registers (eight CTAs
+// capped it at 64 with spills: 0.566 against 0.555 ms at the scene-scale view)
+__global__ void __launch_bounds__(kFwdThreads, 7) k_render_fwd(const __grid_constant__ VS vs, const uint2* __restrict__ ranges,
                                                             const uint32_t* __restrict__ keys,
                                                             const uint32_t* __restrict__ vals, const Rec* __restrict__ rec,
                                                             const Params P, unsigned long long* __restrict__ stats) {
@@ -333,7 +335,7 @@ __global__ void __launch_bounds__(kFwdThreads, 8) k_render_fwd(const __grid_cons
 // Persistent form: CTAs take tiles from a work counter until the table's total_tiles are done, so
 // a fixed grid serves batches of any size (the launch can be replayed from a captured graph).
 template <class VS>
-__global__ void __launch_bounds__(kFwdThreads, 8) k_render_fwd_persistent(const __grid_constant__ VS vs,
+__global__ void __launch_bounds__(kFwdThreads, 7) k_render_fwd_persistent(const __grid_constant__ VS vs,
                                                                     const uint2* __restrict__ ranges,
                                                                     const uint32_t* __restrict__ keys,
                                                                     const uint32_t* __restrict__ vals,
